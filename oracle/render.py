@@ -1,0 +1,356 @@
+"""FP64 forward renderer of textured 2D Gaussian splats (TEST INFRASTRUCTURE).
+
+The plain definition, evaluated per pixel and per candidate splat, in float64
+torch CPU ops (no tiling tricks beyond taking each pixel's candidates from its
+tile's sorted list, which the brute-force mode replaces by every visible
+splat):
+
+  ray        o + tau d through the pixel centre (x+0.5, y+0.5),
+             d = R^T K^-1 (x, y, 1) so that tau is the camera depth
+  splat      P_k(u,v) = p_k + s_u t_u u + s_v t_v v, n_k = t_u x t_v  (Sec. 3.1, Eq. 1)
+  hit        tau = (p - o).n / d.n, skip if |d.n| <= 1e-12 |d| or tau <= 0.2
+  (u, v)     u = (X - p).t_u / s_u, v = (X - p).t_v / s_v   (exact ray-splat intersection)
+  support    fragment only if |u| <= 3 and |v| <= 3 (S_sigma = 3, Sec. 3.3)
+  kernel     G = exp(-(u^2+v^2)/2)                         (Eq. 2)
+  opacity    alpha = min(0.99, o G); skip if alpha < 1/255
+  texture    s = (u+3)/6, t = (v+3)/6                      (Eq. 5)
+             a = BilinearFilter(T_k, s, t)                 (Eq. 4, Eq. 6)
+             texel centres at (i+0.5)/T, clamp-to-edge inside the splat's texture
+  normals    n = R_k n^t with R_k = [t_u, t_v, n_k'] and n_k' the splat normal
+             turned to face the camera                    (Eq. 7)
+  blending   X = sum_i x_i alpha_i prod_{j<i}(1 - alpha_j)  (Eq. 3, Eq. 8-9)
+             A = sum_i alpha_i prod_{j<i}(1 - alpha_j); stop after the first
+             fragment that brings the transmittance below 1e-4
+  shading    see shading.py                               (Eq. 10-12)
+
+Products along a pixel's list are cumulative products and sums cumulative sums
+(sequential, in list order), so adding a candidate that does not contribute
+changes no bit of the result: that is what makes the brute-force comparison
+exact.
+
+Parity: pinned by the closed-form single-splat and two-splat tests, the
+texel-centre and affine-texture tests, the constant-texture invariant, the
+90-degree twist invariant and the brute-force comparison
+(tests/test_oracle_render.py).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import keys as K
+from .shading import shade, shading_ambiguity
+
+F64 = torch.float64
+ALPHA_MIN = float(K.ALPHA_MIN)
+ALPHA_MAX = float(np.float32(0.99))
+T_MIN = float(np.float32(1e-4))
+NEAR = float(K.NEAR)
+
+
+def to_params(scene: dict, requires_grad: bool = False) -> dict:
+    """Float64 torch leaves of the splat parameters."""
+    out = {}
+    for k in ("means", "quats", "scales", "opacity", "texels"):
+        t = torch.from_numpy(np.asarray(scene[k], dtype=np.float64).copy())
+        t.requires_grad_(requires_grad)
+        out[k] = t
+    return out
+
+
+def env_params(env: dict, requires_grad: bool = False) -> dict:
+    spec = []
+    for m in env["spec"]:
+        t = torch.from_numpy(np.asarray(m, dtype=np.float64).copy())
+        t.requires_grad_(requires_grad)
+        spec.append(t)
+    irr = torch.from_numpy(np.asarray(env["irr"], dtype=np.float64).copy()).requires_grad_(requires_grad)
+    lut = torch.from_numpy(np.asarray(env["lut"], dtype=np.float64).copy())
+    return dict(spec=spec, irr=irr, lut=lut)
+
+
+def rotation_columns(q: torch.Tensor):
+    """Unit-quaternion rotation matrix columns (t_u, t_v, n) in float64."""
+    qn = q / torch.linalg.vector_norm(q, dim=-1, keepdim=True)
+    w, x, y, z = qn.unbind(-1)
+    tu = torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)], -1)
+    tv = torch.stack([2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)], -1)
+    n = torch.stack([2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)], -1)
+    return tu, tv, n
+
+
+def camera_tensors(cam: dict):
+    R = torch.tensor(np.asarray(cam["R"], dtype=np.float64))
+    t = torch.tensor(np.asarray(cam["t"], dtype=np.float64))
+    origin = -(R.T @ t)
+    return R, t, origin
+
+
+def pixel_rays(cam: dict, px: np.ndarray, py: np.ndarray) -> torch.Tensor:
+    """World-space ray directions through pixel centres; camera-z component 1."""
+    R, _, _ = camera_tensors(cam)
+    xc = (torch.tensor(px, dtype=F64) + 0.5 - float(cam["cx"])) / float(cam["fx"])
+    yc = (torch.tensor(py, dtype=F64) + 0.5 - float(cam["cy"])) / float(cam["fy"])
+    dc = torch.stack([xc, yc, torch.ones_like(xc)], -1)
+    return dc @ R  # R^T dc, row-vector form
+
+
+def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None):
+    """All per-fragment quantities for pixels (px, py) [P] and candidate splat
+    indices cand [P, L] (-1 = padding), in list order.
+
+    Returns a dict with alpha-validity masks, the blended weights, the
+    per-fragment attribute vectors and the composited G-buffer.
+    """
+    P, L = cand.shape
+    _, _, origin = camera_tensors(cam)
+    d = pixel_rays(cam, px, py)  # [P,3]
+    pad = cand < 0
+    ci = cand.clamp_min(0)
+    T = params["texels"].shape[1]
+
+    tu_all, tv_all, n_all = rotation_columns(params["quats"])
+    p = params["means"][ci]          # [P,L,3]
+    tu, tv, n = tu_all[ci], tv_all[ci], n_all[ci]
+    su = params["scales"][ci][..., 0]
+    sv = params["scales"][ci][..., 1]
+    op = params["opacity"][ci]
+
+    dd = d[:, None, :]
+    den = (dd * n).sum(-1)                       # d.n
+    po = p - origin                              # p - o
+    num = (po * n).sum(-1)                       # (p - o).n
+    dnorm = torch.linalg.vector_norm(d, dim=-1)[:, None]
+    hit = (den.abs() > 1e-12 * dnorm) & ~pad
+    den_s = torch.where(hit, den, torch.ones_like(den))
+    tau = num / den_s
+    hit = hit & (tau > NEAR)
+    rel = tau[..., None] * dd - po               # X - p
+    u = (rel * tu).sum(-1) / su
+    v = (rel * tv).sum(-1) / sv
+    inside = hit & (u.abs() <= 3.0) & (v.abs() <= 3.0)
+    u_s = torch.where(inside, u, torch.zeros_like(u))
+    v_s = torch.where(inside, v, torch.zeros_like(v))
+    G = torch.exp(-(u_s * u_s + v_s * v_s) / 2.0)
+    oG = op * G
+    alpha = torch.clamp(oG, max=ALPHA_MAX)
+    valid = inside & (alpha >= ALPHA_MIN)
+
+    # texture lookup (Eq. 5-6)
+    s = (u_s + 3.0) / 6.0
+    t = (v_s + 3.0) / 6.0
+    from .shading import bilinear_2d
+    tex = bilinear_2d(params["texels"], s * T - 0.5, t * T - 0.5, lead_index=ci)  # [P,L,8]
+
+    # normal mapping (Eq. 7): columns t_u, t_v and the camera-facing normal
+    flip = num > 0.0
+    n_face = torch.where(flip[..., None], -n, n)
+    nt = tex[..., 5:8]
+    n_w = nt[..., 0:1] * tu + nt[..., 1:2] * tv + nt[..., 2:3] * n_face
+    x = torch.cat([tex[..., 0:5], n_w], -1)  # [P,L,8]
+
+    # compositing (Eq. 3, Eq. 8): sequential products / sums along the list
+    a = torch.where(valid, alpha, torch.zeros_like(alpha))
+    trans = torch.cumprod(1.0 - a, dim=1)
+    T_before = torch.cat([torch.ones_like(trans[:, :1]), trans[:, :-1]], 1)
+    blended = valid & (T_before >= T_MIN)
+    w = torch.where(blended, a * T_before, torch.zeros_like(a))
+    X = torch.cumsum(w[..., None] * x, dim=1)[:, -1, :] if L > 0 else torch.zeros(P, 8, dtype=F64)
+    A = torch.cumsum(w, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
+    ab = torch.where(blended, a, torch.zeros_like(a))
+    T_final = torch.cumprod(1.0 - ab, dim=1)[:, -1] if L > 0 else torch.ones(P, dtype=F64)
+
+    out = dict(X=X, A=A, T=T_final, ray_d=d, blended=blended, valid=valid, T_before=T_before)
+    with torch.no_grad():
+        evaluated = (T_before >= T_MIN) & ~pad
+        out["n_eval"] = evaluated.sum(1)
+        out["n_contrib"] = blended.sum(1)
+        # index (within the list) of the last blended fragment, -1 if none
+        idx = torch.arange(L).expand(P, L)
+        out["last"] = torch.where(blended, idx, torch.full_like(idx, -1)).max(1).values if L > 0 \
+            else torch.full((P,), -1, dtype=torch.long)
+        if margins is not None:
+            m_uv, m_a, m_t, m_f = margins
+            maybe_eval = (T_before >= T_MIN * (1.0 - m_t)) & hit
+            oG_full = op * torch.exp(-(u * u + v * v).clamp(max=1e4) / 2.0)
+            near_edge = (((u.abs() - 3.0).abs() <= m_uv) & (v.abs() <= 3.0 + m_uv)) | \
+                        (((v.abs() - 3.0).abs() <= m_uv) & (u.abs() <= 3.0 + m_uv))
+            amb = near_edge & (oG_full >= ALPHA_MIN * (1.0 - m_a))
+            amb |= inside & ((oG - ALPHA_MIN).abs() <= m_a * ALPHA_MIN)
+            T_after = T_before * (1.0 - a)
+            amb |= valid & ((T_after / T_MIN - 1.0).abs() <= m_t)
+            amb |= inside & (num.abs() <= m_f * torch.linalg.vector_norm(po, dim=-1))
+            out["ambiguous"] = (amb & maybe_eval).any(1)
+    return out
+
+
+def tile_candidates(keylist: dict, tile: int) -> np.ndarray:
+    s, e = keylist["tile_ranges"][tile]
+    return keylist["ids"][s:e].astype(np.int64)
+
+
+def brute_candidates(view: dict) -> np.ndarray:
+    """Every visible splat, ordered by (depth bits, id): the tile-free list."""
+    vis = np.nonzero(view["visible"])[0]
+    order = np.lexsort((vis, view["depth_bits"][vis]))
+    return vis[order].astype(np.int64)
+
+
+DEFAULT_MARGINS = (1e-4, 1e-4, 1e-3, 1e-6)
+
+
+def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=False,
+           tiles=None, margins=DEFAULT_MARGINS, max_entries=4_000_000, keylist=None) -> dict:
+    """Render the view (or the listed ``tiles``) in float64.
+
+    Returns rgba [H,W,4], the G-buffer X [H,W,8], A, T_final, the ambiguity
+    mask, fragment counts (evaluated / contributing), the last contributor
+    index and the key list.  With ``params``/``envp`` (torch leaves) the
+    images are differentiable.
+    """
+    W, H = int(cam["W"]), int(cam["H"])
+    if params is None:
+        params = to_params(scene)
+    if envp is None:
+        envp = env_params(env)
+    kl = keylist if keylist is not None else K.build_keys(scene, cam)
+    tiles_x, tiles_y = kl["view"]["tiles_x"], kl["view"]["tiles_y"]
+    tile_list = list(range(tiles_x * tiles_y)) if tiles is None else list(tiles)
+    brute_list = brute_candidates(kl["view"]) if brute else None
+
+    rgba = torch.zeros(H, W, 4, dtype=F64)
+    Xb = torch.zeros(H, W, 8, dtype=F64)
+    Ab = torch.zeros(H, W, dtype=F64)
+    Tb = torch.ones(H, W, dtype=F64)
+    amb = torch.zeros(H, W, dtype=torch.bool)
+    n_eval = torch.zeros(H, W, dtype=torch.long)
+    n_con = torch.zeros(H, W, dtype=torch.long)
+    last = torch.full((H, W), -1, dtype=torch.long)
+    covered = torch.zeros(H, W, dtype=torch.bool)
+
+    def run_chunk(chunk):
+        pxs, pys, cands = [], [], []
+        for tl in chunk:
+            tx, ty = tl % tiles_x, tl // tiles_x
+            xs = np.arange(tx * K.TILE, min(W, (tx + 1) * K.TILE))
+            ys = np.arange(ty * K.TILE, min(H, (ty + 1) * K.TILE))
+            gy, gx = np.meshgrid(ys, xs, indexing="ij")
+            c = brute_list if brute else tile_candidates(kl, tl)
+            pxs.append(gx.ravel())
+            pys.append(gy.ravel())
+            cands.append(np.broadcast_to(c, (gx.size, c.size)))
+        Lm = max(c.shape[1] for c in cands)
+        Pn = sum(c.shape[0] for c in cands)
+        cm = np.full((Pn, Lm), -1, dtype=np.int64)
+        r = 0
+        for c in cands:
+            cm[r:r + c.shape[0], :c.shape[1]] = c
+            r += c.shape[0]
+        px = np.concatenate(pxs)
+        py = np.concatenate(pys)
+        fr = fragments(params, cam, px, py, torch.from_numpy(cm), margins)
+        col = shade(fr["X"], fr["A"], fr["ray_d"], envp)
+        pyt, pxt = torch.from_numpy(py), torch.from_numpy(px)
+        rgba.index_put_((pyt, pxt), col)
+        Xb.index_put_((pyt, pxt), fr["X"])
+        Ab.index_put_((pyt, pxt), fr["A"])
+        Tb.index_put_((pyt, pxt), fr["T"])
+        n_eval[pyt, pxt] = fr["n_eval"]
+        n_con[pyt, pxt] = fr["n_contrib"]
+        last[pyt, pxt] = fr["last"]
+        covered[pyt, pxt] = True
+        if margins is not None:
+            a2 = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
+            amb[pyt, pxt] = a2
+
+    chunk, size = [], 0
+    for tl in tile_list:
+        L = brute_list.size if brute else int(kl["tile_ranges"][tl][1] - kl["tile_ranges"][tl][0])
+        ent = K.TILE * K.TILE * max(L, 1)
+        if chunk and size + ent > max_entries:
+            run_chunk(chunk)
+            chunk, size = [], 0
+        chunk.append(tl)
+        size += ent
+    if chunk:
+        run_chunk(chunk)
+    return dict(rgba=rgba, X=Xb, A=Ab, T=Tb, ambiguous=amb, n_eval=n_eval, n_contrib=n_con,
+                last=last, covered=covered, keys=kl)
+
+
+def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, params=None,
+                  envp=None, margins=DEFAULT_MARGINS) -> dict:
+    """Render individual pixels (px, py) from their tiles' lists: the sampled
+    check used at sizes where a whole image would take too long."""
+    kl = keylist if keylist is not None else K.build_keys(scene, cam)
+    params = params if params is not None else to_params(scene)
+    envp = envp if envp is not None else env_params(env)
+    tiles_x = kl["view"]["tiles_x"]
+    px = np.asarray(px, dtype=np.int64)
+    py = np.asarray(py, dtype=np.int64)
+    cands = [tile_candidates(kl, (y // K.TILE) * tiles_x + (x // K.TILE)) for x, y in zip(px, py)]
+    Lm = max(1, max(c.size for c in cands))
+    cm = np.full((px.size, Lm), -1, dtype=np.int64)
+    for i, c in enumerate(cands):
+        cm[i, :c.size] = c
+    fr = fragments(params, cam, px, py, torch.from_numpy(cm), margins)
+    col = shade(fr["X"], fr["A"], fr["ray_d"], envp)
+    amb = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
+    return dict(rgba=col, X=fr["X"], A=fr["A"], T=fr["T"], ambiguous=amb, n_eval=fr["n_eval"],
+                n_contrib=fr["n_contrib"], last=fr["last"])
+
+
+def render_attributes_2dgs(scene: dict, cam: dict, env: dict, attrs: np.ndarray, **kw) -> dict:
+    """Per-primitive-attribute 2DGS branch (one 8-vector per splat, no texture):
+    the texture lookup is replaced by the splat's constant attribute.  Written
+    separately from the texture path so that the 'constant texture equals
+    per-splat attribute' invariant (Sec. 3.2, Sec. 4.1 two-stage training)
+    compares two independent code paths."""
+    W, H = int(cam["W"]), int(cam["H"])
+    params = to_params(dict(scene, texels=np.zeros((len(scene["opacity"]), 1, 1, 8))))
+    envp = env_params(env)
+    kl = K.build_keys(scene, cam)
+    tiles_x = kl["view"]["tiles_x"]
+    attr = torch.from_numpy(np.asarray(attrs, dtype=np.float64))
+    _, _, origin = camera_tensors(cam)
+    tu_all, tv_all, n_all = rotation_columns(params["quats"])
+    out = torch.zeros(H, W, 4, dtype=F64)
+    for y in range(H):
+        xs = np.arange(W)
+        ys = np.full(W, y)
+        d = pixel_rays(cam, xs, ys)
+        for xi in range(W):
+            tl = (y // K.TILE) * tiles_x + (xi // K.TILE)
+            Tt = 1.0
+            Xp = torch.zeros(8, dtype=F64)
+            Ap = 0.0
+            for k in tile_candidates(kl, tl):
+                p, n = params["means"][k], n_all[k]
+                den = float(d[xi] @ n)
+                if abs(den) <= 1e-12 * float(torch.linalg.vector_norm(d[xi])):
+                    continue
+                num = float((p - origin) @ n)
+                tau = num / den
+                if tau <= NEAR:
+                    continue
+                rel = tau * d[xi] - (p - origin)
+                u = float(rel @ tu_all[k]) / float(params["scales"][k, 0])
+                v = float(rel @ tv_all[k]) / float(params["scales"][k, 1])
+                if not (abs(u) <= 3.0 and abs(v) <= 3.0):
+                    continue
+                al = min(ALPHA_MAX, float(params["opacity"][k]) * math.exp(-(u * u + v * v) / 2.0))
+                if al < ALPHA_MIN:
+                    continue
+                nf = -n if num > 0 else n
+                nt = attr[k, 5:8]
+                nw = nt[0] * tu_all[k] + nt[1] * tv_all[k] + nt[2] * nf
+                xv = torch.cat([attr[k, 0:5], nw])
+                Xp = Xp + al * Tt * xv
+                Ap = Ap + al * Tt
+                Tt = Tt * (1.0 - al)
+                if Tt < T_MIN:
+                    break
+            out[y, xi, :] = shade(Xp[None], torch.tensor([Ap], dtype=F64), d[xi:xi + 1], envp)[0]
+    return dict(rgba=out)

@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: differentiable textured-2DGS training step (forward + L1 loss +
+backward) on 200k textured splats at 800x800, reported as Mpix/s.
+
+Workload (synthetic, seeded; stands in for the paper's Shiny Blender
+object captures): 160k splats on a unit sphere + 40k in a [-1,1]^3 box,
+8x8 texels x 8 channels, 100 cameras on a radius-4 Fibonacci sphere, 800x800,
+L1 loss to seeded U[0,1] targets, 32x32 cube + 8x8 irradiance + 128x128 BRDF
+table.  One step = one view: render (with saved state), loss, backward.
+Gradients accumulate over the steps (a multi-view gradient accumulation), so
+every step does the full forward and backward.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank renders its own views (replicas, no collective on
+the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s fwd+bwd at 200k splats 800²; served-view p50/p99 latency vs plain"
+UNIT = "Mpix/s"
+N_SPLATS, T_TEX, RES, N_CAMS = 200_000, 8, 800, 100
+FP32_LANES_PER_SM, N_SM = 128, 148
+
+# FP32 operations per fragment of the algorithm ("roofline"):
+# every evaluated (pixel, splat) pair costs the homography and the support cut;
+# every blended fragment adds kernel/alpha, texel setup, 8-channel bilinear,
+# normal mapping and blending; the backward recomputes that and adds the adjoint.
+FLOP_EVAL = 15
+FLOP_BLEND_FWD = 124
+FLOP_BLEND_BWD = 124 + 260
+FLOP_SHADE_FWD = 150
+FLOP_SHADE_BWD = 400
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-tiles", type=int, default=6, help="tiles of the oracle CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(seed_cams=0):
+    import scenegen as sg
+    scene = sg.make_scene(1)
+    env = sg.make_env(1, cube_res=32, levels=1, irr_res=8, lut_res=128)
+    cams = sg.fibonacci_cameras(N_CAMS, 4.0, RES, RES)
+    return scene, env, cams
+
+
+# ----------------------------------------------------------------------------
+def cpu_oracle_sample(scene, env, cam, n_tiles: int, seed: int = 0):
+    """Times the FP64 oracle (forward + autograd backward) on the n_tiles
+    seeded random non-empty tiles of one view.  Returns (Mpix/s, seconds, threads, pixels)."""
+    import numpy as np
+    import torch
+
+    import scenegen as sg
+    from oracle import grad as G
+    from oracle import keys as K
+
+    kl = K.build_keys(scene, cam)
+    lens = kl["tile_ranges"][:, 1] - kl["tile_ranges"][:, 0]
+    rng = np.random.default_rng(seed)
+    busy = np.nonzero(lens > 0)[0]
+    tiles = sorted(rng.choice(busy, size=min(n_tiles, busy.size), replace=False).tolist())
+    tgt = sg.make_target(seed, RES, RES)
+    dL = np.sign(rng.normal(size=tgt.shape)) / (3.0 * RES * RES)
+    t0 = time.perf_counter()
+    G.render_grads(scene, cam, env, dL, tiles=tiles, keylist=kl)
+    dt = time.perf_counter() - t0
+    px = 256 * len(tiles)
+    return px / dt / 1e6, dt, torch.get_num_threads(), px
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    scene, env, cams = build_workload()
+    vals, secs = [], []
+    for i in range(args.warmup + args.steps):
+        v, dt, thr, px = cpu_oracle_sample(scene, env, cams[i % N_CAMS], max(1, args.cpu_tiles // 3), seed=i)
+        if i >= args.warmup:
+            vals.append(v)
+            secs.append(dt)
+    total_px = 256 * max(1, args.cpu_tiles // 3) * args.steps
+    value = total_px / sum(secs) / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "cfg1: 200k textured splats (8x8x8 texels), 800x800, fwd+L1+bwd",
+                       "sample": f"{max(1, args.cpu_tiles // 3)} random non-empty 16x16 tiles per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{max(1, args.cpu_tiles // 3)} random non-empty tiles of each view, fwd+autograd bwd, FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2506_13348_b300 as P
+    from paper_2506_13348_b300 import _lib
+    import scenegen as sg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    scene, env, cams = build_workload()
+    sc = P.Scene.from_arrays(scene, env, device=local)
+    n_needed = min(N_CAMS, args.warmup + args.steps)
+    my_cams = [cams[(rank * 7 + i) % N_CAMS] for i in range(n_needed)]
+    targets = [torch.from_numpy(sg.make_target((rank * 7 + i) % N_CAMS, RES, RES)).to(dev)
+               for i in range(n_needed)]
+    out = torch.empty(RES, RES, 4, dtype=torch.float32, device=dev)
+    dl = torch.empty_like(out)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    grads = P.zero_grads(sc)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        _, saved = P.render(sc, my_cams[i % n_needed], out=out, save=True)
+        P.l1_loss(out, targets[i % n_needed], loss, dl)
+        P.render_backward(saved, dl, grads)
+        saved.release()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler = ClockSampler(local)
+    _lib.profile_enable(True)
+    _lib.profile_report()
+    l0 = _lib.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.launch_count() - l0
+    stages = _lib.profile_report()
+    _lib.profile_enable(False)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev)
+    if pg:
+        pg.barrier()
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    ms_max = float(t.item())
+    mpix = RES * RES / 1e6
+    value = world * args.steps * mpix / (ms_max / 1e3)
+
+    # fragment statistics of a few of the timed views (untimed pass)
+    fr = {"n_pairs": 0, "n_evaluated": 0, "n_blended": 0, "n_visible": 0}
+    nstat = 4
+    for i in range(nstat):
+        _, saved = P.render(sc, my_cams[(args.warmup + i) % n_needed], out=out, save=True)
+        s = saved.frag_stats()
+        saved.release()
+        for k in fr:
+            fr[k] += s[k] / nstat
+    npix = RES * RES
+    flops_fwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_FWD * fr["n_blended"] + FLOP_SHADE_FWD * npix
+    flops_bwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_BWD * fr["n_blended"] + FLOP_SHADE_BWD * npix
+    peaks, peak_kind = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    stage_ms = {k: v[1] / max(1, v[0]) for k, v in stages.items()}
+    dom = max(("raster_fwd", "raster_bwd"), key=lambda k: stages.get(k, (0, 0.0))[1])
+    dom_ms = stage_ms.get(dom, float("nan"))
+    dom_flops = flops_bwd if dom == "raster_bwd" else flops_fwd
+    achieved = dom_flops / (dom_ms / 1e3) / 1e12
+    traffic = read_traffic(dom)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cfg1: 200k textured splats (160k sphere + 40k box), 8x8 texels x 8 ch, "
+                                   "800x800, forward + L1 loss + backward per view",
+                       "splats": N_SPLATS, "texels": f"{T_TEX}x{T_TEX}x8 f32", "resolution": f"{RES}x{RES}",
+                       "views_per_step": 1, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (texel atlas 410 MB, records+pairs ~90 MB per view)"},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                         "peak_note": f"FP32 FMA peak {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                                      f"(clock from {peak_kind} peaks)",
+                         "flops_per_launch": dom_flops, "ms_per_launch": dom_ms},
+            "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "fragments_per_view": {k: int(v) for k, v in fr.items()},
+            "gpu_launches": int(launches),
+            "clocks": clocks}
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(P, sc, my_cams, n_needed, args, dev, pg, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, thr, px = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "sample": f"{args.cpu_tiles} random non-empty 16x16 tiles ({px} px) of one 800x800 view, "
+                                          f"FP64 forward + autograd backward, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
+    """Same step through the public API with host buffers: the target image
+    goes host->device from pinned memory and the loss comes back each step."""
+    import numpy as np
+    import torch
+
+    import scenegen as sg
+    host_t = [torch.from_numpy(sg.make_target(i, RES, RES)).pin_memory() for i in range(min(8, n_needed))]
+    dev_t = torch.empty(RES, RES, 4, dtype=torch.float32, device=dev)
+    out = torch.empty_like(dev_t)
+    dl = torch.empty_like(dev_t)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    loss_h = torch.zeros(1, dtype=torch.float32).pin_memory()
+    grads = P.zero_grads(sc)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        dev_t.copy_(host_t[i % len(host_t)], non_blocking=True)
+        _, saved = P.render(sc, cams[i % n_needed], out=out, save=True)
+        P.l1_loss(out, dev_t, loss, dl)
+        P.render_backward(saved, dl, grads)
+        saved.release()
+        loss_h.copy_(loss, non_blocking=True)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = torch.tensor([e0.elapsed_time(e1)], device=dev)
+    if pg:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    ms = float(t.item())
+    return {"value": world * args.steps * RES * RES / 1e6 / (ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": RES * RES * 4 * 4, "d2h_bytes_per_step": 4}
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    ent = rec.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2506_13348_b300", "csrc")
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(src)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(src, fn), "rb") as f:
+                h.update(f.read())
+    if ent.get("source_sha256") != h.hexdigest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * texsplat.h -- C ABI of the B300 textured 2D-Gaussian-splat renderer.
+ *
+ * The library renders planar (2DGS) Gaussian splats that each carry a T x T
+ * texture of 8 material channels, composites the texture lookups into a
+ * G-buffer and shades it against a cube-map environment (TextureSplat,
+ * Sec. 3), and differentiates all of it.  Every entry point takes plain
+ * pointers and sizes; no C++ or framework type crosses this boundary.
+ *
+ * Conventions shared by all entry points
+ *   - Every call returns a ts_status; TS_OK is 0.  On failure the call has
+ *     no partial effect on caller buffers unless stated, and
+ *     ts_last_error() returns a message (thread-local, valid until the next
+ *     call on that thread).  No exception or abort crosses the ABI.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued in stream order.  Device pointers must
+ *     belong to the scene's device.
+ *   - Arrays are dense, row-major, float32 unless stated.
+ *   - Channel order of a texel (8 channels): 0..2 albedo RGB, 3 metallic,
+ *     4 roughness, 5..7 tangent-space normal (x, y, z) (Sec. 3.5.1).
+ *   - Texture layout [n][T][T][8]: row index along the splat's v axis
+ *     (texture t), column along u (texture s) (Eq. 5).
+ *   - Cube maps [6][R][R][3]: faces +x,-x,+y,-y,+z,-z, row t, column s, in
+ *     the OpenGL/CUDA cube-face convention.
+ */
+#ifndef TEXSPLAT_H
+#define TEXSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ts_status;
+#define TS_OK 0
+#define TS_ERR_ARG 1      /* invalid argument (null pointer, bad size, bad enum) */
+#define TS_ERR_OOM 2      /* device or host allocation failed */
+#define TS_ERR_CAPACITY 3 /* a fixed-capacity buffer would overflow */
+#define TS_ERR_CUDA 4     /* a CUDA runtime call failed (message has the CUDA error) */
+#define TS_ERR_TIMEOUT 5  /* a host-side wait ran out of time */
+#define TS_ERR_STATE 6    /* call out of order (e.g. render before upload) */
+
+typedef enum ts_dtype { TS_F32 = 0, TS_BF16 = 1, TS_F16 = 2 } ts_dtype;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  R is the
+ * world->camera rotation (row-major), t the world->camera translation, so a
+ * world point X maps to R X + t.  Pixel centres are at (i + 0.5, j + 0.5).
+ * width, height >= 1. */
+typedef struct ts_camera {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} ts_camera;
+
+typedef struct ts_scene ts_scene;  /* library-owned splats, texels, environment */
+typedef struct ts_saved ts_saved;  /* library-owned forward state for the backward */
+
+/* Caller-owned device buffers receiving gradients.  The backward ACCUMULATES
+ * (+=) into every non-NULL pointer; NULL skips that group.  Shapes follow
+ * the uploads: means [n][3], quats [n][4] (w,x,y,z; gradient w.r.t. the
+ * uploaded, unnormalised quaternion), scales [n][2] (linear), opacity [n]
+ * (linear), texels [n][T][T][8] (float32 whatever the stored dtype), spec
+ * (all mip levels concatenated, [6][R_l][R_l][3] each), irr [6][R][R][3]. */
+typedef struct ts_grads {
+  float* means;
+  float* quats;
+  float* scales;
+  float* opacity;
+  float* texels;
+  float* spec;
+  float* irr;
+} ts_grads;
+
+/* Fragment statistics of one forward (for roofline accounting). */
+typedef struct ts_frag_stats {
+  int64_t n_pairs;      /* (tile, splat) pairs after binning */
+  int64_t n_evaluated;  /* (pixel, splat) fragments tested before each pixel terminated */
+  int64_t n_blended;    /* fragments that passed the support and alpha tests and were blended */
+  int64_t n_visible;    /* splats that survived culling */
+} ts_frag_stats;
+
+/* ---- scenes --------------------------------------------------------------- */
+
+/* Creates an empty scene on CUDA device `device`. *out owns device memory
+ * until ts_destroy_scene. */
+ts_status ts_create_scene(ts_scene** out, int device);
+ts_status ts_destroy_scene(ts_scene* scene);
+
+/* Splat geometry of Sec. 3.1 (Eq. 1): means p [n][3], quaternions [n][4]
+ * (w,x,y,z, normalised inside), linear scales (s_u, s_v) [n][2] > 0 and
+ * linear opacities o [n] in [0,1].  Copies into library memory (from device
+ * memory if src_on_device, else host memory; the call then returns after
+ * the host buffers may be reused).  n >= 0 (0 renders an empty image).
+ * Replaces previous geometry; the atlas must be re-uploaded if n changed. */
+ts_status ts_upload_gaussians(ts_scene* scene, int64_t n, const float* means, const float* quats,
+                              const float* scales, const float* opacity, int src_on_device,
+                              void* stream);
+
+/* Per-primitive textures (Sec. 3.2-3.3; packed as in the supplementary's
+ * atlas construction, one contiguous T x T chart per splat).  texels
+ * [n][T][T][C] float32 with C == 8 and 1 <= T <= 32; `store` selects the
+ * stored precision (float32, or bfloat16 / float16 rounded to nearest
+ * even).  Lookups always widen to float32. */
+ts_status ts_upload_atlas(ts_scene* scene, int T, int C, ts_dtype store, const float* texels,
+                          int src_on_device, void* stream);
+
+/* Environment light of Sec. 3.5.4 (Eq. 11-12): `levels` specular mips, level l
+ * of resolution max(1, base_res >> l), concatenated [6][R_l][R_l][3]; the
+ * irradiance cube [6][irr_res][irr_res][3]; the split-sum BRDF table
+ * [lut_res][lut_res][2] (row = roughness, column = N.w_o; channels scale,
+ * bias).  `store` F32 or F16 for the cube maps (the table stays float32).
+ * 1 <= levels <= 12. */
+ts_status ts_upload_envmap(ts_scene* scene, int levels, int base_res, const float* spec, int irr_res,
+                           const float* irr, int lut_res, const float* lut, ts_dtype store,
+                           int src_on_device, void* stream);
+
+/* ---- rendering -------------------------------------------------------------- */
+
+/* Renders one view: cull and bin the splats into 16x16 tiles, sort each
+ * tile's list by depth (keys bit-exact with the FP32 binning specification),
+ * intersect each pixel ray with each listed splat in closed form to get its
+ * local (u, v) (Sec. 3.1, Eq. 2), fetch the bilinear texel (Eq. 5-6),
+ * rotate the tangent normal to world space (Eq. 7), composite front to back
+ * into the G-buffer (Eq. 3, Eq. 8-9) and shade it (Eq. 10-12).
+ * out_rgba: caller-owned device buffer [H][W][4] (RGB colour, alpha = 1 - T).
+ * saved: NULL for inference; otherwise receives a handle holding what the
+ * backward needs (release with ts_release_saved).  Synchronises the stream
+ * once to size the pair buffer (see ts_render_views for the batched form). */
+ts_status ts_render(ts_scene* scene, const ts_camera* cam, float* out_rgba, ts_saved** saved,
+                    void* stream);
+
+/* Batched form: n_views views, view i of scenes[i] with cams[i] into
+ * out_rgba[i].  All views share one binning/sort/raster launch sequence.
+ * saved may be NULL.  1 <= n_views <= 32. */
+ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_views,
+                          float* const* out_rgba, ts_saved** saved, void* stream);
+
+/* Backward of ts_render / ts_render_views through shading, compositing,
+ * texel fetch and intersection (Sec. 3.6 optimises all of these).
+ * dL_drgba: device [H][W][4] per view (array of n_views pointers for the
+ * batched form, in view order).  Gradients are accumulated into `grads`
+ * (one set per scene; for the batched form all views must share one scene).
+ * The saved handle stays valid (backward may be repeated). */
+ts_status ts_render_backward(const ts_saved* saved, const float* const* dL_drgba,
+                             const ts_grads* grads, void* stream);
+
+ts_status ts_release_saved(ts_saved* saved);
+
+/* ---- inspection of a saved forward (tests and accounting) ------------------ */
+
+/* Number of pairs and tiles (global, over all views) of a saved forward.
+ * Synchronises the saved forward's stream. */
+ts_status ts_saved_sizes(const ts_saved* saved, int64_t* n_pairs, int64_t* n_tiles);
+
+/* Copies the sorted per-tile lists to caller device buffers:
+ * item_ids [n_pairs] (splat id + the view's item offset), tile_ranges
+ * [n_tiles][2] (start, end), depth_bits [n_items] (float bits of each
+ * splat's camera depth, 0xFFFFFFFF when culled).  Any pointer may be NULL. */
+ts_status ts_saved_copy_lists(const ts_saved* saved, uint32_t* item_ids, uint32_t* tile_ranges,
+                              uint32_t* depth_bits, void* stream);
+
+/* Copies view v's per-pixel forward state: gbuf [H][W][8] (blended X of
+ * Eq. 9), trans [H][W] (final transmittance T), last [H][W] (index in the
+ * pair list of the last blended fragment, -1 if none).  NULL skips. */
+ts_status ts_saved_copy_pixels(const ts_saved* saved, int view, float* gbuf, float* trans,
+                               int32_t* last, void* stream);
+
+/* Fragment counts of a saved forward (counted by a separate, untimed pass
+ * over the same lists).  Synchronises the stream. */
+ts_status ts_saved_frag_stats(const ts_saved* saved, ts_frag_stats* out, void* stream);
+
+/* ---- training helpers --------------------------------------------------------- */
+
+/* L1 image loss over the RGB channels: loss_out[0] = mean |rgba - target|
+ * (device scalar, written, not accumulated), dL_drgba = sign(rgba - target) /
+ * (3 H W) for RGB and 0 for alpha (written).  n_pixels = H * W. */
+ts_status ts_l1_loss(const float* rgba, const float* target, int64_t n_pixels, float* loss_out,
+                     float* dL_drgba, void* stream);
+
+/* ---- accounting and stage timing ------------------------------------------- */
+
+/* Number of kernels this library has launched since it was loaded (all
+ * threads, all devices). */
+int64_t ts_launch_count(void);
+
+/* Turns per-stage CUDA-event timing on (1) or off (0).  While on, each
+ * pipeline stage (preprocess, sort_splats, scan_counts, emit_pairs,
+ * sort_pairs, tile_ranges, raster_fwd, raster_bwd, preprocess_bwd, l1_loss)
+ * records an event pair on the stream it runs on. */
+ts_status ts_profile_enable(int on);
+
+/* Waits for the recorded events, writes one line per stage
+ * "name launches total_ms\n" into buf (NUL-terminated, truncated to buflen)
+ * and clears the records. */
+ts_status ts_profile_report(char* buf, size_t buflen);
+
+/* ---- errors ---------------------------------------------------------------- */
+
+const char* ts_last_error(void);
+const char* ts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TEXSPLAT_H */

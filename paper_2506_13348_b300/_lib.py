@@ -1,0 +1,111 @@
+"""ctypes declarations of libtexsplat.so (include/texsplat.h).
+
+Loading fails loudly when the library has not been built: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtexsplat.so")
+
+TS_F32, TS_BF16, TS_F16 = 0, 1, 2
+STATUS = {0: "TS_OK", 1: "TS_ERR_ARG", 2: "TS_ERR_OOM", 3: "TS_ERR_CAPACITY", 4: "TS_ERR_CUDA",
+          5: "TS_ERR_TIMEOUT", 6: "TS_ERR_STATE"}
+
+EXPORTED = [
+    "ts_create_scene", "ts_destroy_scene", "ts_upload_gaussians", "ts_upload_atlas", "ts_upload_envmap",
+    "ts_render", "ts_render_views", "ts_render_backward", "ts_release_saved", "ts_saved_sizes",
+    "ts_saved_copy_lists", "ts_saved_copy_pixels", "ts_saved_frag_stats", "ts_l1_loss",
+    "ts_launch_count", "ts_profile_enable", "ts_profile_report", "ts_last_error", "ts_version",
+]
+
+
+class TsCamera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class TsGrads(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("means", "quats", "scales", "opacity", "texels", "spec", "irr")]
+
+
+class TsFragStats(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("n_evaluated", C.c_int64), ("n_blended", C.c_int64),
+                ("n_visible", C.c_int64)]
+
+
+class TexSplatError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise TexSplatError(f"{LIB_PATH} is missing: build it with `python -m paper_2506_13348_b300.build` "
+                            "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64 = C.c_void_p, C.c_int, C.c_int64
+    sig = {
+        "ts_create_scene": [C.POINTER(vp), i32],
+        "ts_destroy_scene": [vp],
+        "ts_upload_gaussians": [vp, i64, vp, vp, vp, vp, i32, vp],
+        "ts_upload_atlas": [vp, i32, i32, i32, vp, i32, vp],
+        "ts_upload_envmap": [vp, i32, i32, vp, i32, vp, i32, vp, i32, i32, vp],
+        "ts_render": [vp, C.POINTER(TsCamera), vp, C.POINTER(vp), vp],
+        "ts_render_views": [C.POINTER(vp), C.POINTER(TsCamera), i32, C.POINTER(vp), C.POINTER(vp), vp],
+        "ts_render_backward": [vp, C.POINTER(vp), C.POINTER(TsGrads), vp],
+        "ts_release_saved": [vp],
+        "ts_saved_sizes": [vp, C.POINTER(i64), C.POINTER(i64)],
+        "ts_saved_copy_lists": [vp, vp, vp, vp, vp],
+        "ts_saved_copy_pixels": [vp, i32, vp, vp, vp, vp],
+        "ts_saved_frag_stats": [vp, C.POINTER(TsFragStats), vp],
+        "ts_l1_loss": [vp, vp, i64, vp, vp, vp],
+        "ts_profile_enable": [i32],
+        "ts_profile_report": [C.c_char_p, C.c_size_t],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.ts_last_error.restype = C.c_char_p
+    L.ts_last_error.argtypes = []
+    L.ts_version.restype = C.c_char_p
+    L.ts_version.argtypes = []
+    L.ts_launch_count.restype = C.c_int64
+    L.ts_launch_count.argtypes = []
+    _lib = L
+    return L
+
+
+def check(status: int, what: str = ""):
+    if status != 0:
+        msg = lib().ts_last_error().decode(errors="replace")
+        raise TexSplatError(f"{what}: {STATUS.get(status, status)}: {msg}")
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far."""
+    return int(lib().ts_launch_count())
+
+
+def profile_enable(on: bool = True):
+    check(lib().ts_profile_enable(1 if on else 0), "ts_profile_enable")
+
+
+def profile_report() -> dict:
+    """{stage: (launches, total_ms)} of the stages timed since the last report."""
+    buf = C.create_string_buffer(1 << 16)
+    check(lib().ts_profile_report(buf, len(buf)), "ts_profile_report")
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.split()
+        out[name] = (int(n), float(ms))
+    return out

@@ -1,0 +1,254 @@
+"""Python binding of the renderer: argument marshalling around the C ABI.
+
+Torch provides device memory and streams; every step of rendering and its
+backward runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from ._lib import TS_BF16, TS_F16, TS_F32, TsCamera, TsFragStats, TsGrads, check, lib
+
+DTYPES = {"f32": TS_F32, "bf16": TS_BF16, "f16": TS_F16, torch.float32: TS_F32, torch.bfloat16: TS_BF16,
+          torch.float16: TS_F16}
+
+
+def _ptr(t) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(0)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_camera(cam: dict) -> TsCamera:
+    c = TsCamera()
+    R = np.asarray(cam["R"], dtype=np.float32).reshape(9)
+    t = np.asarray(cam["t"], dtype=np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = (float(np.float32(cam[k])) for k in ("fx", "fy", "cx", "cy"))
+    c.width, c.height = int(cam["W"]), int(cam["H"])
+    return c
+
+
+def _dev_f32(a, device) -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        return a.detach().to(device=device, dtype=torch.float32).contiguous()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
+
+
+class Scene:
+    """Library-owned splats, texel atlas and environment light on one GPU."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = C.c_void_p()
+        check(lib().ts_create_scene(C.byref(h), device), "ts_create_scene")
+        self.handle = h
+        self.n = 0
+        self.T = 0
+        self.levels = 0
+        self.spec_sizes = []
+        self.irr_size = 0
+
+    def close(self):
+        if self.handle:
+            lib().ts_destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def upload_gaussians(self, means, quats, scales, opacity, stream=None):
+        dev = torch.device("cuda", self.device)
+        m, q, s, o = (_dev_f32(a, dev) for a in (means, quats, scales, opacity))
+        n = m.shape[0]
+        check(lib().ts_upload_gaussians(self.handle, n, _ptr(m), _ptr(q), _ptr(s), _ptr(o), 1, _stream(stream)),
+              "ts_upload_gaussians")
+        self.n = n
+
+    def upload_atlas(self, texels, store="f32", stream=None):
+        dev = torch.device("cuda", self.device)
+        t = _dev_f32(texels, dev)
+        T = t.shape[1]
+        check(lib().ts_upload_atlas(self.handle, T, 8, DTYPES[store], _ptr(t), 1, _stream(stream)),
+              "ts_upload_atlas")
+        self.T = T
+
+    def upload_envmap(self, env: dict, store="f32", stream=None):
+        dev = torch.device("cuda", self.device)
+        spec = [_dev_f32(m, dev) for m in env["spec"]]
+        flat = torch.cat([x.reshape(-1) for x in spec])
+        irr = _dev_f32(env["irr"], dev)
+        lut = _dev_f32(env["lut"], dev)
+        check(lib().ts_upload_envmap(self.handle, len(spec), spec[0].shape[1], _ptr(flat), irr.shape[1], _ptr(irr),
+                                     lut.shape[0], _ptr(lut), DTYPES[store], 1, _stream(stream)),
+              "ts_upload_envmap")
+        self.levels = len(spec)
+        self.spec_sizes = [x.numel() for x in spec]
+        self.irr_size = irr.numel()
+
+    @classmethod
+    def from_arrays(cls, scene: dict, env: dict, device: int = 0, store="f32", env_store="f32"):
+        s = cls(device)
+        s.upload_gaussians(scene["means"], scene["quats"], scene["scales"], scene["opacity"])
+        s.upload_atlas(scene["texels"], store)
+        s.upload_envmap(env, env_store)
+        return s
+
+
+class Saved:
+    """Forward state kept for the backward (library-owned)."""
+
+    def __init__(self, handle, views):
+        self.handle = handle
+        self.views = views  # list of (W, H)
+
+    def release(self):
+        if self.handle:
+            lib().ts_release_saved(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+    def sizes(self):
+        k, t = C.c_int64(), C.c_int64()
+        check(lib().ts_saved_sizes(self.handle, C.byref(k), C.byref(t)), "ts_saved_sizes")
+        return k.value, t.value
+
+    def lists(self, n_items: int, stream=None):
+        K, ntiles = self.sizes()
+        ids = torch.empty(max(K, 1), dtype=torch.int32, device="cuda")
+        rng = torch.empty(ntiles, 2, dtype=torch.int32, device="cuda")
+        db = torch.empty(max(n_items, 1), dtype=torch.int32, device="cuda")
+        check(lib().ts_saved_copy_lists(self.handle, _ptr(ids), _ptr(rng), _ptr(db), _stream(stream)),
+              "ts_saved_copy_lists")
+        torch.cuda.synchronize()
+        u32 = lambda t: t.cpu().numpy().view(np.uint32)  # noqa: E731
+        return u32(ids)[:K], u32(rng).astype(np.int64), u32(db)[:n_items]
+
+    def pixels(self, view: int = 0, stream=None):
+        W, H = self.views[view]
+        g = torch.empty(H, W, 8, dtype=torch.float32, device="cuda")
+        tr = torch.empty(H, W, dtype=torch.float32, device="cuda")
+        last = torch.empty(H, W, dtype=torch.int32, device="cuda")
+        check(lib().ts_saved_copy_pixels(self.handle, view, _ptr(g), _ptr(tr), _ptr(last), _stream(stream)),
+              "ts_saved_copy_pixels")
+        return g, tr, last
+
+    def frag_stats(self, stream=None) -> dict:
+        st = TsFragStats()
+        check(lib().ts_saved_frag_stats(self.handle, C.byref(st), _stream(stream)), "ts_saved_frag_stats")
+        return dict(n_pairs=st.n_pairs, n_evaluated=st.n_evaluated, n_blended=st.n_blended,
+                    n_visible=st.n_visible)
+
+
+def render(scene: Scene, cam: dict, out: torch.Tensor | None = None, save: bool = False, stream=None):
+    """Render one view into ``out`` ([H,W,4] float32 CUDA).  Returns (out, Saved|None)."""
+    W, H = int(cam["W"]), int(cam["H"])
+    if out is None:
+        out = torch.empty(H, W, 4, dtype=torch.float32, device=torch.device("cuda", scene.device))
+    c = make_camera(cam)
+    h = C.c_void_p()
+    check(lib().ts_render(scene.handle, C.byref(c), _ptr(out), C.byref(h) if save else None, _stream(stream)),
+          "ts_render")
+    return out, (Saved(h, [(W, H)]) if save else None)
+
+
+def render_views(scenes: Sequence[Scene], cams: Sequence[dict], outs=None, save: bool = False, stream=None):
+    """Render a batch of views (one launch sequence).  Returns (outs, Saved|None)."""
+    n = len(cams)
+    if outs is None:
+        outs = [torch.empty(int(c["H"]), int(c["W"]), 4, dtype=torch.float32,
+                            device=torch.device("cuda", scenes[i].device)) for i, c in enumerate(cams)]
+    carr = (TsCamera * n)(*[make_camera(c) for c in cams])
+    sarr = (C.c_void_p * n)(*[s.handle for s in scenes])
+    oarr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    h = C.c_void_p()
+    check(lib().ts_render_views(sarr, carr, n, oarr, C.byref(h) if save else None, _stream(stream)),
+          "ts_render_views")
+    return outs, (Saved(h, [(int(c["W"]), int(c["H"])) for c in cams]) if save else None)
+
+
+def zero_grads(scene: Scene, device=None) -> dict:
+    dev = device or torch.device("cuda", scene.device)
+    z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=dev)  # noqa: E731
+    return dict(means=z(scene.n, 3), quats=z(scene.n, 4), scales=z(scene.n, 2), opacity=z(scene.n),
+                texels=z(scene.n, scene.T, scene.T, 8), spec=z(sum(scene.spec_sizes)), irr=z(scene.irr_size))
+
+
+def render_backward(saved: Saved, dL_drgba, grads: dict, stream=None):
+    """Accumulate gradients of the saved forward into ``grads`` (dict of
+    CUDA float32 tensors as from :func:`zero_grads`)."""
+    dls = dL_drgba if isinstance(dL_drgba, (list, tuple)) else [dL_drgba]
+    dls = [d.contiguous() for d in dls]
+    arr = (C.c_void_p * len(dls))(*[d.data_ptr() for d in dls])
+    g = TsGrads(*[grads.get(k).data_ptr() if grads.get(k) is not None else None
+                  for k in ("means", "quats", "scales", "opacity", "texels", "spec", "irr")])
+    check(lib().ts_render_backward(saved.handle, arr, C.byref(g), _stream(stream)), "ts_render_backward")
+
+
+def l1_loss(rgba: torch.Tensor, target: torch.Tensor, loss: torch.Tensor, grad: torch.Tensor, stream=None):
+    n = rgba.shape[0] * rgba.shape[1]
+    check(lib().ts_l1_loss(_ptr(rgba), _ptr(target), n, _ptr(loss), _ptr(grad), _stream(stream)), "ts_l1_loss")
+
+
+def split_spec(scene: Scene, flat: torch.Tensor):
+    """Split a concatenated specular-mip gradient into per-level tensors."""
+    out, o = [], 0
+    for sz in scene.spec_sizes:
+        out.append(flat[o:o + sz])
+        o += sz
+    return out
+
+
+class TexSplatRender(torch.autograd.Function):
+    """Differentiable render of one view of a scene whose parameters are
+    held by the caller as torch tensors (means, quats, scales, opacity,
+    texels, spec (flat), irr).  Parameters are uploaded into ``scene`` on
+    each forward (device-to-device copies); the backward calls the
+    library's hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, scene: Scene, cam: dict, env_lut, means, quats, scales, opacity, texels, spec_flat, irr):
+        scene.upload_gaussians(means, quats, scales, opacity)
+        scene.upload_atlas(texels, "f32")
+        levels = scene.levels or 1
+        base = int(round((spec_flat.numel() / 18 / sum(4.0 ** -l for l in range(levels))) ** 0.5))
+        res = [max(1, base >> l) for l in range(levels)]
+        spec, o = [], 0
+        for r in res:
+            n = 6 * r * r * 3
+            spec.append(spec_flat[o:o + n].reshape(6, r, r, 3))
+            o += n
+        scene.upload_envmap(dict(spec=spec, irr=irr, lut=env_lut))
+        out, saved = render(scene, cam, save=True)
+        ctx.scene = scene
+        ctx.saved = saved
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        scene = ctx.scene
+        grads = zero_grads(scene)
+        render_backward(ctx.saved, g.contiguous(), grads)
+        ctx.saved.release()
+        return (None, None, None, grads["means"], grads["quats"], grads["scales"], grads["opacity"],
+                grads["texels"], grads["spec"], grads["irr"].reshape(6, *([int((scene.irr_size / 18) ** 0.5)] * 2), 3))

@@ -1,0 +1,634 @@
+// C ABI of the textured 2DGS renderer: scene memory, the render / backward
+// launch sequences and inspection helpers.  See include/texsplat.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "prof.h"
+#include "../../include/texsplat.h"
+
+using namespace ts;
+
+namespace {
+
+thread_local std::string g_err;
+
+ts_status fail(ts_status code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define TS_CUDA(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      return fail(e_ == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,                      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+    }                                                                                              \
+  } while (0)
+
+#define TS_CHECK_LAUNCH()                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                                           \
+    if (e_ != cudaSuccess) return fail(TS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+std::mutex g_pool_mu;
+bool g_pool_set[64] = {false};
+
+ts_status prepare_device(int device) {
+  TS_CUDA(cudaSetDevice(device));
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (device >= 0 && device < 64 && !g_pool_set[device]) {
+    cudaMemPool_t pool;
+    TS_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t thr = UINT64_MAX;
+    TS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    g_pool_set[device] = true;
+  }
+  return TS_OK;
+}
+
+// Stream-ordered scratch allocations released together.
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  cudaError_t alloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+    ptrs.clear();
+  }
+  ~Scratch() { release(); }
+};
+
+int bits_for(long long n) {
+  int b = 0;
+  while ((1ll << b) < n) ++b;
+  return b;
+}
+
+}  // namespace
+
+struct ts_scene {
+  int device = 0;
+  int64_t n = 0;
+  float4* means = nullptr;
+  float4* quats = nullptr;
+  float2* scales = nullptr;
+  float* opacity = nullptr;
+  void* texels = nullptr;
+  int T = 0;
+  int tex_dtype = 0;
+  int64_t tex_n = -1;
+  void* spec = nullptr;  // all levels, concatenated
+  size_t spec_off[MAX_LEVELS] = {0};
+  int spec_res[MAX_LEVELS] = {0};
+  int levels = 0;
+  void* irr = nullptr;
+  int irr_res = 0;
+  int cube_dtype = 0;
+  float* lut = nullptr;
+  int lut_res = 0;
+};
+
+struct ts_saved {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ViewTable vt;
+  std::vector<ts_scene*> scenes;
+  Record* rec = nullptr;
+  uint32_t* pair_items = nullptr;
+  uint32_t* tile_keys = nullptr;
+  uint2* ranges = nullptr;
+  uint32_t* depth_bits = nullptr;
+  std::vector<void*> bufs;  // owned, cudaMallocAsync'ed on `stream`
+  int64_t K = 0;
+};
+
+static void free_scene_buffers(ts_scene* s) {
+  void* ptrs[] = {s->means, s->quats, s->scales, s->opacity, s->texels, s->spec, s->irr, s->lut};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+extern "C" {
+
+const char* ts_last_error(void) { return g_err.c_str(); }
+const char* ts_version(void) { return "texsplat-b300 0.1 (sm_103a)"; }
+
+ts_status ts_create_scene(ts_scene** out, int device) {
+  if (!out) return fail(TS_ERR_ARG, "ts_create_scene: out is NULL");
+  int count = 0;
+  TS_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fail(TS_ERR_ARG, "ts_create_scene: bad device index");
+  ts_status st = prepare_device(device);
+  if (st != TS_OK) return st;
+  ts_scene* s = new (std::nothrow) ts_scene();
+  if (!s) return fail(TS_ERR_OOM, "ts_create_scene: host allocation failed");
+  s->device = device;
+  *out = s;
+  return TS_OK;
+}
+
+ts_status ts_destroy_scene(ts_scene* s) {
+  if (!s) return TS_OK;
+  cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  free_scene_buffers(s);
+  delete s;
+  return TS_OK;
+}
+
+static ts_status copy_in(void* dst, const void* src, size_t bytes, int src_on_device, cudaStream_t st) {
+  if (bytes == 0) return TS_OK;
+  TS_CUDA(cudaMemcpyAsync(dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  return TS_OK;
+}
+
+ts_status ts_upload_gaussians(ts_scene* s, int64_t n, const float* means, const float* quats, const float* scales,
+                              const float* opacity, int src_on_device, void* stream) {
+  if (!s) return fail(TS_ERR_ARG, "ts_upload_gaussians: scene is NULL");
+  if (n < 0 || n > (int64_t)INT32_MAX / 64) return fail(TS_ERR_ARG, "ts_upload_gaussians: bad n");
+  if (n > 0 && (!means || !quats || !scales || !opacity))
+    return fail(TS_ERR_ARG, "ts_upload_gaussians: NULL array");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(s->device));
+  TS_CUDA(cudaStreamSynchronize(st));
+  for (void** p : {(void**)&s->means, (void**)&s->quats, (void**)&s->scales, (void**)&s->opacity}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  s->n = n;
+  size_t nn = (size_t)std::max<int64_t>(n, 1);
+  TS_CUDA(cudaMalloc(&s->means, nn * sizeof(float4)));
+  TS_CUDA(cudaMalloc(&s->quats, nn * sizeof(float4)));
+  TS_CUDA(cudaMalloc(&s->scales, nn * sizeof(float2)));
+  TS_CUDA(cudaMalloc(&s->opacity, nn * sizeof(float)));
+  if (n > 0) {
+    float* staging = nullptr;
+    TS_CUDA(cudaMallocAsync(&staging, nn * 3 * sizeof(float), st));
+    ts_status r = copy_in(staging, means, (size_t)n * 3 * sizeof(float), src_on_device, st);
+    if (r != TS_OK) return r;
+    launch_pad4(staging, 3, s->means, n, st);
+    TS_CHECK_LAUNCH();
+    TS_CUDA(cudaFreeAsync(staging, st));
+    if ((r = copy_in(s->quats, quats, (size_t)n * 4 * sizeof(float), src_on_device, st)) != TS_OK) return r;
+    if ((r = copy_in(s->scales, scales, (size_t)n * 2 * sizeof(float), src_on_device, st)) != TS_OK) return r;
+    if ((r = copy_in(s->opacity, opacity, (size_t)n * sizeof(float), src_on_device, st)) != TS_OK) return r;
+  }
+  TS_CUDA(cudaStreamSynchronize(st));
+  return TS_OK;
+}
+
+ts_status ts_upload_atlas(ts_scene* s, int T, int C, ts_dtype store, const float* texels, int src_on_device,
+                          void* stream) {
+  if (!s) return fail(TS_ERR_ARG, "ts_upload_atlas: scene is NULL");
+  if (C != 8) return fail(TS_ERR_ARG, "ts_upload_atlas: C must be 8");
+  if (T < 1 || T > 32) return fail(TS_ERR_ARG, "ts_upload_atlas: T must be in [1, 32]");
+  if (store != TS_F32 && store != TS_BF16 && store != TS_F16) return fail(TS_ERR_ARG, "ts_upload_atlas: bad dtype");
+  if (s->n > 0 && !texels) return fail(TS_ERR_ARG, "ts_upload_atlas: texels is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(s->device));
+  TS_CUDA(cudaStreamSynchronize(st));
+  if (s->texels) cudaFree(s->texels);
+  s->texels = nullptr;
+  const long long count = (long long)s->n * T * T * 8;
+  const size_t esz = store == TS_F32 ? 4 : 2;
+  TS_CUDA(cudaMalloc(&s->texels, std::max<size_t>((size_t)count * esz, 16)));
+  s->T = T;
+  s->tex_dtype = (int)store;
+  s->tex_n = s->n;
+  if (count > 0) {
+    if (store == TS_F32) {
+      ts_status r = copy_in(s->texels, texels, (size_t)count * 4, src_on_device, st);
+      if (r != TS_OK) return r;
+    } else {
+      const float* src = texels;
+      float* staging = nullptr;
+      if (!src_on_device) {
+        TS_CUDA(cudaMallocAsync(&staging, (size_t)count * 4, st));
+        TS_CUDA(cudaMemcpyAsync(staging, texels, (size_t)count * 4, cudaMemcpyHostToDevice, st));
+        src = staging;
+      }
+      launch_pack_texels(src, s->texels, count, (int)store, st);
+      TS_CHECK_LAUNCH();
+      if (staging) TS_CUDA(cudaFreeAsync(staging, st));
+    }
+  }
+  TS_CUDA(cudaStreamSynchronize(st));
+  return TS_OK;
+}
+
+ts_status ts_upload_envmap(ts_scene* s, int levels, int base_res, const float* spec, int irr_res, const float* irr,
+                           int lut_res, const float* lut, ts_dtype store, int src_on_device, void* stream) {
+  if (!s) return fail(TS_ERR_ARG, "ts_upload_envmap: scene is NULL");
+  if (levels < 1 || levels > MAX_LEVELS || base_res < 1 || irr_res < 1 || lut_res < 1)
+    return fail(TS_ERR_ARG, "ts_upload_envmap: bad sizes");
+  if (!spec || !irr || !lut) return fail(TS_ERR_ARG, "ts_upload_envmap: NULL array");
+  if (store != TS_F32 && store != TS_F16) return fail(TS_ERR_ARG, "ts_upload_envmap: store must be F32 or F16");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(s->device));
+  TS_CUDA(cudaStreamSynchronize(st));
+  for (void** p : {(void**)&s->spec, (void**)&s->irr, (void**)&s->lut}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  size_t total = 0;
+  for (int l = 0; l < levels; ++l) {
+    int r = std::max(1, base_res >> l);
+    s->spec_res[l] = r;
+    s->spec_off[l] = total;
+    total += (size_t)6 * r * r * 3;
+  }
+  s->levels = levels;
+  s->irr_res = irr_res;
+  s->lut_res = lut_res;
+  s->cube_dtype = (int)store;
+  const size_t esz = store == TS_F32 ? 4 : 2;
+  const size_t irr_n = (size_t)6 * irr_res * irr_res * 3;
+  TS_CUDA(cudaMalloc(&s->spec, total * esz));
+  TS_CUDA(cudaMalloc(&s->irr, irr_n * esz));
+  TS_CUDA(cudaMalloc((void**)&s->lut, (size_t)lut_res * lut_res * 2 * sizeof(float)));
+  ts_status r = copy_in(s->lut, lut, (size_t)lut_res * lut_res * 2 * sizeof(float), src_on_device, st);
+  if (r != TS_OK) return r;
+  if (store == TS_F32) {
+    if ((r = copy_in(s->spec, spec, total * 4, src_on_device, st)) != TS_OK) return r;
+    if ((r = copy_in(s->irr, irr, irr_n * 4, src_on_device, st)) != TS_OK) return r;
+  } else {
+    float* staging = nullptr;
+    TS_CUDA(cudaMallocAsync(&staging, (total + irr_n) * 4, st));
+    if ((r = copy_in(staging, spec, total * 4, src_on_device, st)) != TS_OK) return r;
+    if ((r = copy_in(staging + total, irr, irr_n * 4, src_on_device, st)) != TS_OK) return r;
+    launch_pack_texels(staging, s->spec, (long long)total, DT_F16, st);
+    launch_pack_texels(staging + total, s->irr, (long long)irr_n, DT_F16, st);
+    TS_CHECK_LAUNCH();
+    TS_CUDA(cudaFreeAsync(staging, st));
+  }
+  TS_CUDA(cudaStreamSynchronize(st));
+  return TS_OK;
+}
+
+static void fill_env(const ts_scene* s, EnvDesc& E) {
+  const size_t esz = s->cube_dtype == DT_F32 ? 4 : 2;
+  memset(&E, 0, sizeof(E));
+  for (int l = 0; l < s->levels; ++l) {
+    E.spec[l] = reinterpret_cast<const char*>(s->spec) + s->spec_off[l] * esz;
+    E.spec_res[l] = s->spec_res[l];
+  }
+  E.levels = s->levels;
+  E.irr = s->irr;
+  E.irr_res = s->irr_res;
+  E.cube_dtype = s->cube_dtype;
+  E.lut = s->lut;
+  E.lut_res = s->lut_res;
+}
+
+static ts_status check_scene(const ts_scene* s) {
+  if (!s) return fail(TS_ERR_ARG, "scene is NULL");
+  if (!s->means) return fail(TS_ERR_STATE, "geometry not uploaded");
+  if (!s->texels || s->tex_n != s->n) return fail(TS_ERR_STATE, "atlas missing or stale (re-upload after geometry)");
+  if (!s->spec) return fail(TS_ERR_STATE, "environment not uploaded");
+  return TS_OK;
+}
+
+static ts_status check_cam(const ts_camera* c) {
+  if (!c) return fail(TS_ERR_ARG, "camera is NULL");
+  if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384)
+    return fail(TS_ERR_ARG, "camera resolution out of range");
+  if (!(c->fx > 0.f) || !(c->fy > 0.f)) return fail(TS_ERR_ARG, "camera focal length must be > 0");
+  return TS_OK;
+}
+
+ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_views, float* const* out_rgba,
+                          ts_saved** saved_out, void* stream) {
+  if (!scenes || !cams || !out_rgba) return fail(TS_ERR_ARG, "ts_render_views: NULL argument");
+  if (n_views < 1 || n_views > MAX_VIEWS) return fail(TS_ERR_ARG, "ts_render_views: n_views out of [1, 32]");
+  const int device = scenes[0] ? scenes[0]->device : 0;
+  for (int i = 0; i < n_views; ++i) {
+    ts_status r = check_scene(scenes[i]);
+    if (r != TS_OK) return r;
+    if ((r = check_cam(&cams[i])) != TS_OK) return r;
+    if (!out_rgba[i]) return fail(TS_ERR_ARG, "ts_render_views: NULL output");
+    if (scenes[i]->device != device) return fail(TS_ERR_ARG, "ts_render_views: scenes on different devices");
+    if (scenes[i]->tex_dtype != scenes[0]->tex_dtype)
+      return fail(TS_ERR_ARG, "ts_render_views: views of one batch must share the atlas dtype");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(device));
+
+  ViewTable vt;
+  memset(&vt, 0, sizeof(vt));
+  vt.n_views = n_views;
+  long long tiles = 0, items = 0;
+  for (int i = 0; i < n_views; ++i) {
+    const ts_camera& c = cams[i];
+    const ts_scene* s = scenes[i];
+    ViewDesc& V = vt.v[i];
+    memcpy(V.R, c.R, sizeof(V.R));
+    memcpy(V.t, c.t, sizeof(V.t));
+    V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy;
+    V.W = c.width; V.H = c.height;
+    V.tiles_x = (c.width + TILE - 1) / TILE;
+    V.tiles_y = (c.height + TILE - 1) / TILE;
+    V.tile_off = (int)tiles;
+    V.item_off = (int)items;
+    V.n_splats = (int)s->n;
+    V.means = s->means; V.quats = s->quats; V.scales = s->scales; V.opacity = s->opacity;
+    V.texels = s->texels; V.T = s->T; V.tex_dtype = s->tex_dtype;
+    fill_env(s, V.env);
+    V.rgba = reinterpret_cast<float4*>(out_rgba[i]);
+    tiles += (long long)V.tiles_x * V.tiles_y;
+    items += s->n;
+  }
+  if (items > INT32_MAX / 2 || tiles > INT32_MAX / 2) return fail(TS_ERR_CAPACITY, "ts_render_views: batch too large");
+  vt.n_tiles = (int)tiles;
+  vt.n_items = (int)items;
+  const int n_items = vt.n_items;
+
+  Scratch tmp(st);
+  ts_saved* sv = nullptr;
+  std::vector<void*> keep;  // buffers that move into the saved handle
+  auto salloc = [&](void** p, size_t bytes) -> cudaError_t {
+    if (saved_out) {
+      cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+      if (e == cudaSuccess) keep.push_back(*p);
+      return e;
+    }
+    return tmp.alloc(p, bytes);
+  };
+  auto cleanup_keep = [&]() {
+    for (void* p : keep) cudaFreeAsync(p, st);
+    keep.clear();
+  };
+#define TS_CUDA_K(call)                                                                        \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      cleanup_keep();                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,                  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+    }                                                                                          \
+  } while (0)
+
+  // ---- per-item preprocess --------------------------------------------------
+  Record* rec = nullptr;
+  uint32_t *counts = nullptr, *ids0 = nullptr, *ids1 = nullptr, *cs = nullptr, *offs = nullptr, *dbits = nullptr;
+  uint64_t *dk0 = nullptr, *dk1 = nullptr;
+  int4* rects = nullptr;
+  const size_t ni = (size_t)std::max(n_items, 1);
+  TS_CUDA_K(salloc((void**)&rec, ni * sizeof(Record)));
+  TS_CUDA_K(tmp.alloc((void**)&counts, ni * 4));
+  TS_CUDA_K(tmp.alloc((void**)&ids0, ni * 4));
+  TS_CUDA_K(tmp.alloc((void**)&ids1, ni * 4));
+  TS_CUDA_K(tmp.alloc((void**)&cs, ni * 4));
+  TS_CUDA_K(tmp.alloc((void**)&offs, ni * 4));
+  TS_CUDA_K(tmp.alloc((void**)&dk0, ni * 8));
+  TS_CUDA_K(tmp.alloc((void**)&dk1, ni * 8));
+  TS_CUDA_K(tmp.alloc((void**)&rects, ni * sizeof(int4)));
+  if (saved_out) TS_CUDA_K(salloc((void**)&dbits, ni * 4));
+  void* rtemp = nullptr;
+  size_t rt_bytes = std::max(radix_temp_bytes(n_items), scan_temp_bytes(n_items));
+  TS_CUDA_K(tmp.alloc(&rtemp, rt_bytes));
+
+  {
+    ProfScope p(st, "preprocess");
+    launch_preprocess(vt, rec, counts, dk0, ids0, rects, st);
+    if (dbits) launch_depth_bits(dk0, dbits, n_items, st);
+  }
+  const int view_bits = bits_for(n_views);
+  int which = 0;
+  {
+    ProfScope p(st, "sort_splats");
+    which = radix_sort_u64(dk0, ids0, dk1, ids1, n_items, 0, 32 + view_bits, rtemp, st);
+  }
+  uint32_t* order = which ? ids1 : ids0;
+  {
+    ProfScope p(st, "scan_counts");
+    launch_gather_counts(order, counts, cs, n_items, st);
+    launch_exclusive_scan(cs, offs, n_items, rtemp, st);
+  }
+  TS_CHECK_LAUNCH();
+
+  // total pair count -> host (one synchronisation per batch)
+  static thread_local uint32_t* h_tail = nullptr;
+  if (!h_tail) TS_CUDA_K(cudaHostAlloc((void**)&h_tail, 2 * sizeof(uint32_t), cudaHostAllocDefault));
+  h_tail[0] = h_tail[1] = 0;
+  if (n_items > 0) {
+    TS_CUDA_K(cudaMemcpyAsync(&h_tail[0], offs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
+    TS_CUDA_K(cudaMemcpyAsync(&h_tail[1], cs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
+  }
+  TS_CUDA_K(cudaStreamSynchronize(st));
+  const long long K = (long long)h_tail[0] + h_tail[1];
+  if (K > INT32_MAX / 2) {
+    cleanup_keep();
+    return fail(TS_ERR_CAPACITY, "ts_render_views: too many (tile, splat) pairs");
+  }
+
+  // ---- pairs: emit in depth order, stable sort by tile --------------------------
+  uint32_t *tk0 = nullptr, *tk1 = nullptr, *pi0 = nullptr, *pi1 = nullptr;
+  uint2* ranges = nullptr;
+  const size_t nk = (size_t)std::max<long long>(K, 1);
+  TS_CUDA_K(salloc((void**)&tk0, nk * 4));
+  TS_CUDA_K(salloc((void**)&pi0, nk * 4));
+  TS_CUDA_K(salloc((void**)&tk1, nk * 4));
+  TS_CUDA_K(salloc((void**)&pi1, nk * 4));
+  TS_CUDA_K(salloc((void**)&ranges, (size_t)vt.n_tiles * sizeof(uint2)));
+  void* rtemp2 = nullptr;
+  TS_CUDA_K(tmp.alloc(&rtemp2, radix_temp_bytes((int)K)));
+  {
+    ProfScope p(st, "emit_pairs");
+    launch_emit_pairs(vt, order, offs, cs, rects, tk0, pi0, n_items, st);
+  }
+  int w2 = 0;
+  {
+    ProfScope p(st, "sort_pairs");
+    w2 = radix_sort_u32(tk0, pi0, tk1, pi1, (int)K, 0, std::max(1, bits_for(vt.n_tiles)), rtemp2, st);
+  }
+  uint32_t* tkeys = w2 ? tk1 : tk0;
+  uint32_t* pitems = w2 ? pi1 : pi0;
+  {
+    ProfScope p(st, "tile_ranges");
+    TS_CUDA_K(cudaMemsetAsync(ranges, 0, (size_t)vt.n_tiles * sizeof(uint2), st));
+    launch_tile_ranges(tkeys, (int)K, ranges, st);
+  }
+  TS_CHECK_LAUNCH();
+
+  // ---- per-pixel state for the backward ------------------------------------------
+  if (saved_out) {
+    for (int i = 0; i < n_views; ++i) {
+      ViewDesc& V = vt.v[i];
+      const size_t np = (size_t)V.W * V.H;
+      TS_CUDA_K(salloc((void**)&V.gbuf, np * 2 * sizeof(float4)));
+      TS_CUDA_K(salloc((void**)&V.trans, np * sizeof(float)));
+      TS_CUDA_K(salloc((void**)&V.last, np * sizeof(int)));
+    }
+  }
+  {
+    ProfScope p(st, "raster_fwd");
+    launch_raster_fwd(vt, rec, pitems, ranges, scenes[0]->tex_dtype, saved_out != nullptr, nullptr, st);
+  }
+  TS_CHECK_LAUNCH();
+
+  if (saved_out) {
+    sv = new (std::nothrow) ts_saved();
+    if (!sv) {
+      cleanup_keep();
+      return fail(TS_ERR_OOM, "ts_render_views: host allocation failed");
+    }
+    sv->device = device;
+    sv->stream = st;
+    sv->vt = vt;
+    sv->scenes.assign(scenes, scenes + n_views);
+    sv->rec = rec;
+    sv->pair_items = pitems;
+    sv->tile_keys = tkeys;
+    sv->ranges = ranges;
+    sv->depth_bits = dbits;
+    sv->K = K;
+    sv->bufs = keep;
+    *saved_out = sv;
+  }
+  return TS_OK;
+#undef TS_CUDA_K
+}
+
+ts_status ts_render(ts_scene* scene, const ts_camera* cam, float* out_rgba, ts_saved** saved, void* stream) {
+  ts_scene* sc[1] = {scene};
+  float* outs[1] = {out_rgba};
+  return ts_render_views(sc, cam, 1, outs, saved, stream);
+}
+
+ts_status ts_release_saved(ts_saved* sv) {
+  if (!sv) return TS_OK;
+  cudaSetDevice(sv->device);
+  for (void* p : sv->bufs) cudaFreeAsync(p, sv->stream);
+  delete sv;
+  return TS_OK;
+}
+
+ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, const ts_grads* grads, void* stream) {
+  if (!sv || !dL_drgba || !grads) return fail(TS_ERR_ARG, "ts_render_backward: NULL argument");
+  const ts_scene* s = sv->scenes[0];
+  for (ts_scene* o : sv->scenes)
+    if (o != s) return fail(TS_ERR_ARG, "ts_render_backward: views of one backward must share one scene");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(sv->device));
+  ViewTable vt = sv->vt;
+  for (int i = 0; i < vt.n_views; ++i) {
+    if (!dL_drgba[i]) return fail(TS_ERR_ARG, "ts_render_backward: NULL dL/drgba");
+    vt.v[i].dl = reinterpret_cast<const float4*>(dL_drgba[i]);
+  }
+  GradTable g;
+  memset(&g, 0, sizeof(g));
+  g.means = grads->means;
+  g.quats = grads->quats;
+  g.scales = grads->scales;
+  g.opacity = grads->opacity;
+  g.texels = grads->texels;
+  g.irr = grads->irr;
+  if (grads->spec) {
+    for (int l = 0; l < s->levels; ++l) g.spec[l] = grads->spec + s->spec_off[l];
+  }
+  Scratch tmp(st);
+  float* g_items = nullptr;
+  TS_CUDA(tmp.alloc((void**)&g_items, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(float)));
+  TS_CUDA(cudaMemsetAsync(g_items, 0, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(float), st));
+  {
+    ProfScope p(st, "raster_bwd");
+    launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, g_items, g, st);
+  }
+  {
+    ProfScope p(st, "preprocess_bwd");
+    launch_preprocess_bwd(vt, g_items, g, st);
+  }
+  TS_CHECK_LAUNCH();
+  return TS_OK;
+}
+
+ts_status ts_saved_sizes(const ts_saved* sv, int64_t* n_pairs, int64_t* n_tiles) {
+  if (!sv) return fail(TS_ERR_ARG, "ts_saved_sizes: NULL saved");
+  if (n_pairs) *n_pairs = sv->K;
+  if (n_tiles) *n_tiles = sv->vt.n_tiles;
+  return TS_OK;
+}
+
+ts_status ts_saved_copy_lists(const ts_saved* sv, uint32_t* item_ids, uint32_t* tile_ranges, uint32_t* depth_bits,
+                              void* stream) {
+  if (!sv) return fail(TS_ERR_ARG, "ts_saved_copy_lists: NULL saved");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(sv->device));
+  if (item_ids && sv->K > 0)
+    TS_CUDA(cudaMemcpyAsync(item_ids, sv->pair_items, (size_t)sv->K * 4, cudaMemcpyDeviceToDevice, st));
+  if (tile_ranges)
+    TS_CUDA(cudaMemcpyAsync(tile_ranges, sv->ranges, (size_t)sv->vt.n_tiles * 8, cudaMemcpyDeviceToDevice, st));
+  if (depth_bits && sv->vt.n_items > 0)
+    TS_CUDA(cudaMemcpyAsync(depth_bits, sv->depth_bits, (size_t)sv->vt.n_items * 4, cudaMemcpyDeviceToDevice, st));
+  return TS_OK;
+}
+
+ts_status ts_saved_copy_pixels(const ts_saved* sv, int view, float* gbuf, float* trans, int32_t* last, void* stream) {
+  if (!sv) return fail(TS_ERR_ARG, "ts_saved_copy_pixels: NULL saved");
+  if (view < 0 || view >= sv->vt.n_views) return fail(TS_ERR_ARG, "ts_saved_copy_pixels: bad view");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(sv->device));
+  const ViewDesc& V = sv->vt.v[view];
+  const size_t np = (size_t)V.W * V.H;
+  if (gbuf) TS_CUDA(cudaMemcpyAsync(gbuf, V.gbuf, np * 32, cudaMemcpyDeviceToDevice, st));
+  if (trans) TS_CUDA(cudaMemcpyAsync(trans, V.trans, np * 4, cudaMemcpyDeviceToDevice, st));
+  if (last) TS_CUDA(cudaMemcpyAsync(last, V.last, np * 4, cudaMemcpyDeviceToDevice, st));
+  return TS_OK;
+}
+
+ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stream) {
+  if (!sv || !out) return fail(TS_ERR_ARG, "ts_saved_frag_stats: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(sv->device));
+  ViewTable vt = sv->vt;
+  Scratch tmp(st);
+  for (int i = 0; i < vt.n_views; ++i) {
+    ViewDesc& V = vt.v[i];
+    TS_CUDA(tmp.alloc((void**)&V.rgba, (size_t)V.W * V.H * sizeof(float4)));
+  }
+  unsigned long long* d = nullptr;
+  TS_CUDA(tmp.alloc((void**)&d, 2 * sizeof(unsigned long long)));
+  TS_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st));
+  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, st);
+  TS_CHECK_LAUNCH();
+  unsigned long long h[2] = {0, 0};
+  TS_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+  // visible splats: items with a finite depth
+  uint32_t* db = sv->depth_bits;
+  std::vector<uint32_t> hb((size_t)vt.n_items);
+  if (db && vt.n_items > 0)
+    TS_CUDA(cudaMemcpyAsync(hb.data(), db, (size_t)vt.n_items * 4, cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  out->n_pairs = sv->K;
+  out->n_evaluated = (int64_t)h[0];
+  out->n_blended = (int64_t)h[1];
+  int64_t vis = 0;
+  for (uint32_t b : hb) vis += (b != 0xffffffffu);
+  out->n_visible = vis;
+  return TS_OK;
+}
+
+ts_status ts_l1_loss(const float* rgba, const float* target, int64_t n_pixels, float* loss_out, float* dL_drgba,
+                     void* stream) {
+  if (!rgba || !target || !loss_out || !dL_drgba || n_pixels < 0) return fail(TS_ERR_ARG, "ts_l1_loss: bad argument");
+  ProfScope p((cudaStream_t)stream, "l1_loss");
+  launch_l1_loss(reinterpret_cast<const float4*>(rgba), reinterpret_cast<const float4*>(target), n_pixels, loss_out,
+                 reinterpret_cast<float4*>(dL_drgba), (cudaStream_t)stream);
+  TS_CHECK_LAUNCH();
+  return TS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// Host-side launch wrappers of the renderer's kernels.
+#pragma once
+#include "ts_common.cuh"
+
+namespace ts {
+
+struct GradTable {
+  float* means;
+  float* quats;
+  float* scales;
+  float* opacity;
+  float* texels;
+  float* spec[MAX_LEVELS];
+  float* irr;
+};
+
+// preprocess.cu
+void launch_preprocess(const ViewTable& vt, Record* rec, uint32_t* counts, uint64_t* depth_keys,
+                       uint32_t* item_ids, int4* rects, cudaStream_t st);
+void launch_preprocess_bwd(const ViewTable& vt, const float* g_items, const GradTable& g, cudaStream_t st);
+
+// sort.cu
+size_t scan_temp_bytes(int n);
+void launch_exclusive_scan(const uint32_t* in, uint32_t* out, int n, void* temp, cudaStream_t st);
+size_t radix_temp_bytes(int n);
+// Stable LSD radix sort of (key, value) pairs over key bits [begin_bit, end_bit).
+// Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
+// (k0, v0), 1 if in (k1, v1).
+int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
+                   void* temp, cudaStream_t st);
+int radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
+                   void* temp, cudaStream_t st);
+void launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t* counts_sorted, int n,
+                          cudaStream_t st);
+void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_t* offsets,
+                       const uint32_t* counts_sorted, const int4* rects, uint32_t* tile_keys,
+                       uint32_t* pair_items, int n, cudaStream_t st);
+void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStream_t st);
+void launch_depth_bits(const uint64_t* depth_keys_unsorted, uint32_t* out, int n, cudaStream_t st);
+
+// raster_fwd.cu / raster_bwd.cu
+void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
+                       const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats,
+                       cudaStream_t st);
+void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
+                       const uint2* ranges, int tex_dtype, float* g_items, const GradTable& g,
+                       cudaStream_t st);
+
+// misc.cu
+void launch_pack_texels(const float* src, void* dst, long long n, int dtype, cudaStream_t st);
+void launch_pack_f16(const float* src, __half* dst, long long n, cudaStream_t st);
+void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStream_t st);
+void launch_l1_loss(const float4* rgba, const float4* target, long long n, float* loss, float4* grad,
+                    cudaStream_t st);
+
+}  // namespace ts

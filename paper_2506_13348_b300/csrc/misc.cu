@@ -1,0 +1,74 @@
+// Upload-time packing and the L1 image loss.
+#include "kernels.h"
+#include "prof.h"
+
+namespace ts {
+
+// Atlas pack: float32 texels -> stored dtype, round to nearest even.
+__global__ void k_pack_texels(const float* __restrict__ src, void* __restrict__ dst, long long n, int dtype) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = src[i];
+  if (dtype == DT_F32) {
+    reinterpret_cast<float*>(dst)[i] = x;
+  } else if (dtype == DT_BF16) {
+    reinterpret_cast<__nv_bfloat16*>(dst)[i] = __float2bfloat16_rn(x);
+  } else {
+    reinterpret_cast<__half*>(dst)[i] = __float2half_rn(x);
+  }
+}
+
+void launch_pack_texels(const float* src, void* dst, long long n, int dtype, cudaStream_t st) {
+  if (n > 0) {
+    k_pack_texels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n, dtype);
+    note_launches(1);
+  }
+}
+
+void launch_pack_f16(const float* src, __half* dst, long long n, cudaStream_t st) {
+  launch_pack_texels(src, dst, n, DT_F16, st);
+}
+
+__global__ void k_pad4(const float* __restrict__ src, int comps, float4* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int c = 0; c < comps; ++c) v[c] = src[i * comps + c];
+  dst[i] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStream_t st) {
+  if (n > 0) {
+    k_pad4<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, comps, dst, n);
+    note_launches(1);
+  }
+}
+
+// L1 over RGB: loss = mean |rgb - target|, dL/drgb = sign / (3 n), dL/dalpha = 0.
+__global__ void k_l1_loss(const float4* __restrict__ rgba, const float4* __restrict__ tgt, long long n,
+                          float* __restrict__ loss, float4* __restrict__ grad) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float s = 0.f;
+  if (i < n) {
+    const float4 a = rgba[i], b = tgt[i];
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    s = fabsf(dx) + fabsf(dy) + fabsf(dz);
+    const float k = 1.f / (3.f * (float)n);
+    auto sgn = [](float d) { return d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f); };
+    grad[i] = make_float4(sgn(dx) * k, sgn(dy) * k, sgn(dz) * k, 0.f);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(loss, s / (3.f * (float)n));
+}
+
+void launch_l1_loss(const float4* rgba, const float4* target, long long n, float* loss, float4* grad,
+                    cudaStream_t st) {
+  cudaMemsetAsync(loss, 0, sizeof(float), st);
+  if (n > 0) {
+    k_l1_loss<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rgba, target, n, loss, grad);
+    note_launches(1);
+  }
+}
+
+}  // namespace ts

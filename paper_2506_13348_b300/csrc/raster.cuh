@@ -1,0 +1,97 @@
+// Per-fragment evaluation shared by the forward and backward rasterisers.
+// Both kernels must take identical decisions (support cut, alpha threshold,
+// termination), so the arithmetic lives here once and uses explicit fmaf /
+// rounding intrinsics: no contraction choice is left to the compiler.
+#pragma once
+#include "ts_common.cuh"
+
+namespace ts {
+
+struct Frag {
+  float u, v, rd, G, oG, alpha;
+};
+
+// Closed-form ray-splat intersection (Sec. 3.1): u = h_u.x / h_w.x,
+// v = h_v.x / h_w.x with x = (x', y', 1); Gaussian kernel (Eq. 2); opacity
+// alpha = min(0.99, o G).  Returns false when the fragment does not exist
+// (outside the 3-sigma support square or alpha < 1/255).
+__device__ __forceinline__ bool eval_frag(const Record& r, float xp, float yp, Frag& f) {
+  float den = fmaf(r.r1.z, xp, fmaf(r.r1.w, yp, r.r2.x));
+  float un = fmaf(r.r0.x, xp, fmaf(r.r0.y, yp, r.r0.z));
+  float vn = fmaf(r.r0.w, xp, fmaf(r.r1.x, yp, r.r1.y));
+  f.rd = __fdividef(1.0f, den);
+  f.u = __fmul_rn(un, f.rd);
+  f.v = __fmul_rn(vn, f.rd);
+  if (!(fabsf(f.u) <= 3.0f && fabsf(f.v) <= 3.0f)) return false;
+  float q = fmaf(f.u, f.u, __fmul_rn(f.v, f.v));
+  f.G = __expf(__fmul_rn(-0.5f, q));
+  f.oG = __fmul_rn(r.r2.y, f.G);
+  f.alpha = fminf(kAlphaMax(), f.oG);
+  return f.alpha >= kAlphaMin();
+}
+
+struct TexSample {
+  int ia, ib, ja, jb;
+  float fx, fy;
+};
+
+// Eq. 5: s = (u + 3)/6, t = (v + 3)/6; texel-centre coordinates x = s T - 1/2.
+__device__ __forceinline__ TexSample tex_setup(float u, float v, int T) {
+  TexSample s;
+  float Ts6 = (float)T * (1.0f / 6.0f);
+  float xs = fmaf(u + 3.0f, Ts6, -0.5f);
+  float ys = fmaf(v + 3.0f, Ts6, -0.5f);
+  float fi = floorf(xs), fj = floorf(ys);
+  s.fx = xs - fi;
+  s.fy = ys - fj;
+  int i0 = (int)fi, j0 = (int)fj;
+  s.ia = min(max(i0, 0), T - 1);
+  s.ib = min(max(i0 + 1, 0), T - 1);
+  s.ja = min(max(j0, 0), T - 1);
+  s.jb = min(max(j0 + 1, 0), T - 1);
+  return s;
+}
+
+// Bilinear texel fetch (Eq. 6) of the 8 channels; optionally returns the
+// four corner texels for the backward.
+template <int DT>
+__device__ __forceinline__ void tex_fetch(const void* texels, long long splat, int T, const TexSample& s,
+                                          float out[8], float corners[4][8]) {
+  long long base = splat * (long long)T * T;
+  float t0[8], t1[8], t2[8], t3[8];
+  load_texel(texels, DT, base + s.ja * T + s.ia, t0);
+  load_texel(texels, DT, base + s.ja * T + s.ib, t1);
+  load_texel(texels, DT, base + s.jb * T + s.ia, t2);
+  load_texel(texels, DT, base + s.jb * T + s.ib, t3);
+  float gx = 1.f - s.fx, gy = 1.f - s.fy;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float top = fmaf(s.fx, t1[c], gx * t0[c]);
+    float bot = fmaf(s.fx, t3[c], gx * t2[c]);
+    out[c] = fmaf(s.fy, bot, gy * top);
+    if (corners) {
+      corners[0][c] = t0[c];
+      corners[1][c] = t1[c];
+      corners[2][c] = t2[c];
+      corners[3][c] = t3[c];
+    }
+  }
+}
+
+// Normal mapping (Eq. 7): n = [t_u, t_v, n_f] n^t, in place on x[5..7].
+__device__ __forceinline__ void normal_map(const Record& r, float x[8]) {
+  float a = x[5], b = x[6], c = x[7];
+  x[5] = fmaf(a, r.r2.z, fmaf(b, r.r3.y, c * r.r4.x));
+  x[6] = fmaf(a, r.r2.w, fmaf(b, r.r3.z, c * r.r4.y));
+  x[7] = fmaf(a, r.r3.x, fmaf(b, r.r3.w, c * r.r4.z));
+}
+
+__device__ __forceinline__ void pixel_of(int tile_local, int tiles_x, int& px, int& py) {
+  int tx = tile_local % tiles_x, ty = tile_local / tiles_x;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // 8 x 4 pixel block per warp, 2 x 4 blocks per 16 x 16 tile
+  px = tx * TILE + (warp & 1) * 8 + (lane & 7);
+  py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
+}
+
+}  // namespace ts

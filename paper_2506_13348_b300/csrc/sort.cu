@@ -1,0 +1,319 @@
+// Binning and sorting: exclusive scan, stable LSD radix sort, pair emission
+// and per-tile ranges.
+//
+// Order of work (per batch of views):
+//   1. splats are sorted once by (view, depth bits) -- N items, 32 + view bits;
+//   2. the (tile, item) pairs are emitted in that order;
+//   3. the pairs are stably sorted by global tile id only (ceil(log2 tiles)
+//      bits, 2 passes for up to 65536 tiles).
+// Stability of step 3 keeps the depth order (and the item-id order for equal
+// depths) inside each tile, so the result equals a sort of 64-bit
+// (tile << 32 | depth bits) keys with ties by item id, at a fraction of the
+// traffic: 8-byte pairs over 2 passes instead of 12-byte pairs over 6.
+#include "kernels.h"
+#include "prof.h"
+
+namespace ts {
+
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 4;  // per thread
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+// Block-wide exclusive scan of SCAN_TILE u32 values; writes block sum.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_tiles(const uint32_t* __restrict__ in,
+                                                            uint32_t* __restrict__ out, int n,
+                                                            uint32_t* __restrict__ block_sums) {
+  __shared__ uint32_t warp_sums[SCAN_BLOCK / 32];
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  uint32_t local = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    v[i] = (base + i < n) ? in[base + i] : 0u;
+    local += v[i];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t ws = warp_sums[lane];
+    uint32_t wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    warp_sums[lane] = wi - ws;
+    if (lane == 31 && block_sums) block_sums[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  uint32_t run = warp_sums[warp] + incl - local;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int n, const uint32_t* __restrict__ block_offs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += block_offs[i / SCAN_TILE];
+}
+
+static int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+size_t scan_temp_bytes(int n) {
+  size_t total = 0;
+  while (n > SCAN_TILE) {
+    n = ceil_div(n, SCAN_TILE);
+    total += 2 * (size_t)n * sizeof(uint32_t) + 256;
+  }
+  return total + 256;
+}
+
+void launch_exclusive_scan(const uint32_t* in, uint32_t* out, int n, void* temp, cudaStream_t st) {
+  if (n <= 0) return;
+  const int nb = ceil_div(n, SCAN_TILE);
+  if (nb == 1) {
+    k_scan_tiles<<<1, SCAN_BLOCK, 0, st>>>(in, out, n, nullptr);
+    note_launches(1);
+    return;
+  }
+  uint32_t* sums = reinterpret_cast<uint32_t*>(temp);
+  uint32_t* offs = sums + nb;
+  char* rest = reinterpret_cast<char*>(offs + nb);
+  rest = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(rest) + 255) & ~uintptr_t(255));
+  k_scan_tiles<<<nb, SCAN_BLOCK, 0, st>>>(in, out, n, sums);
+  note_launches(1);
+  launch_exclusive_scan(sums, offs, nb, rest, st);
+  k_scan_add<<<ceil_div(n, 256), 256, 0, st>>>(out, n, offs);
+  note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort, 8-bit digits (fewer for the last pass).
+// A block owns RS_TILE consecutive keys; warp w of the block owns the
+// sub-range [w * RS_WARP, (w+1) * RS_WARP), processed in rounds of 32.
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_WARP = 32 * RS_ROUNDS;
+constexpr int RS_TILE = RS_WARPS * RS_WARP;  // 4096
+constexpr int RADIX = 256;
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift, uint32_t mask) {
+  return (uint32_t)(key >> shift) & mask;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__ keys, int n, int shift,
+                                                            uint32_t mask, uint32_t* __restrict__ counts,
+                                                            int nblocks) {
+  __shared__ uint32_t hist[RADIX];
+  for (int i = threadIdx.x; i < RADIX; i += RS_THREADS) hist[i] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * RS_TILE;
+  for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+    const int idx = base + i;
+    if (idx < n) atomicAdd(&hist[digit_of(keys[idx], shift, mask)], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d <= (int)mask; d += RS_THREADS) counts[(size_t)d * nblocks + blockIdx.x] = hist[d];
+}
+
+template <typename K>
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin,
+                                                               K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                               int n, int shift, uint32_t mask,
+                                                               const uint32_t* __restrict__ offsets, int nblocks) {
+  __shared__ uint32_t whist[RS_WARPS][RADIX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = lane; i < RADIX; i += 32) whist[warp][i] = 0;
+  __syncwarp();
+  const int wbase = blockIdx.x * RS_TILE + warp * RS_WARP;
+  K kr[RS_ROUNDS];
+  uint32_t dg[RS_ROUNDS];
+  const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    const bool ok = idx < n;
+    kr[r] = ok ? kin[idx] : K(0);
+    dg[r] = ok ? digit_of(kr[r], shift, mask) : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+    if (ok && (peers & lt_mask) == 0) whist[warp][dg[r]] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive prefix over warps, offset by the block's global digit offset
+  for (int d = threadIdx.x; d <= (int)mask; d += RS_THREADS) {
+    uint32_t run = offsets[(size_t)d * nblocks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const uint32_t c = whist[w][d];
+      whist[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    const bool ok = idx < n;
+    const unsigned peers = __match_any_sync(0xffffffffu, dg[r]);
+    uint32_t pos = 0;
+    if (ok) {
+      pos = whist[warp][dg[r]] + __popc(peers & lt_mask);
+      kout[pos] = kr[r];
+      vout[pos] = vin[idx];
+    }
+    __syncwarp();
+    if (ok && (peers & lt_mask) == 0) whist[warp][dg[r]] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+size_t radix_temp_bytes(int n) {
+  const int nb = ceil_div(n > 0 ? n : 1, RS_TILE);
+  const size_t cnt = (size_t)RADIX * nb;
+  return 2 * cnt * sizeof(uint32_t) + 512 + scan_temp_bytes((int)cnt);
+}
+
+template <typename K>
+static int radix_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
+                      cudaStream_t st) {
+  if (n <= 1 || end_bit <= begin_bit) return 0;
+  const int nb = ceil_div(n, RS_TILE);
+  const size_t cnt = (size_t)RADIX * nb;
+  uint32_t* counts = reinterpret_cast<uint32_t*>(temp);
+  uint32_t* offs = counts + cnt;
+  char* rest = reinterpret_cast<char*>(offs + cnt);
+  rest = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(rest) + 255) & ~uintptr_t(255));
+  int cur = 0;
+  K* kb[2] = {k0, k1};
+  uint32_t* vb[2] = {v0, v1};
+  for (int bit = begin_bit; bit < end_bit; bit += 8) {
+    const int bits = min(8, end_bit - bit);
+    const uint32_t mask = (1u << bits) - 1u;
+    const int nd = 1 << bits;
+    k_radix_hist<K><<<nb, RS_THREADS, 0, st>>>(kb[cur], n, bit, mask, counts, nb);
+    note_launches(1);
+    launch_exclusive_scan(counts, offs, nd * nb, rest, st);
+    k_radix_scatter<K><<<nb, RS_THREADS, 0, st>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, bit, mask, offs, nb);
+    note_launches(1);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
+                   void* temp, cudaStream_t st) {
+  return radix_sort<uint64_t>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
+}
+int radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
+                   void* temp, cudaStream_t st) {
+  return radix_sort<uint32_t>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_gather_counts(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
+                                uint32_t* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = counts[order[i]];
+}
+
+void launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t* counts_sorted, int n,
+                          cudaStream_t st) {
+  if (n > 0) {
+    k_gather_counts<<<ceil_div(n, 256), 256, 0, st>>>(order, counts, counts_sorted, n);
+    note_launches(1);
+  }
+}
+
+// One warp per 32 depth-sorted items; the warp writes each item's tile
+// pairs in turn with coalesced stores (items differ a lot in tile count).
+__global__ void __launch_bounds__(256) k_emit_pairs(ViewTable vt, const uint32_t* __restrict__ order,
+                                                     const uint32_t* __restrict__ offsets,
+                                                     const uint32_t* __restrict__ counts_sorted,
+                                                     const int4* __restrict__ rects, uint32_t* __restrict__ tile_keys,
+                                                     uint32_t* __restrict__ pair_items, int n) {
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int first = warp_global * 32;
+  if (first >= n) return;
+  const int my = first + lane;
+  uint32_t my_item = 0, my_cnt = 0, my_off = 0;
+  if (my < n) {
+    my_cnt = counts_sorted[my];
+    if (my_cnt) {
+      my_item = order[my];
+      my_off = offsets[my];
+    }
+  }
+  unsigned todo = __ballot_sync(0xffffffffu, my_cnt != 0);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const uint32_t item = __shfl_sync(0xffffffffu, my_item, src);
+    const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
+    const uint32_t off = __shfl_sync(0xffffffffu, my_off, src);
+    const int v = find_view_item(vt, (int)item);
+    const ViewDesc& V = vt.v[v];
+    const int4 rc = rects[item];
+    const int w = rc.y - rc.x + 1;
+    for (uint32_t j = lane; j < cnt; j += 32) {
+      const int tx = rc.x + (int)(j % w), ty = rc.z + (int)(j / w);
+      tile_keys[off + j] = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
+      pair_items[off + j] = item;
+    }
+  }
+}
+
+void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_t* offsets,
+                       const uint32_t* counts_sorted, const int4* rects, uint32_t* tile_keys,
+                       uint32_t* pair_items, int n, cudaStream_t st) {
+  if (n > 0)
+    k_emit_pairs<<<ceil_div(n, 256), 256, 0, st>>>(vt, order, offsets, counts_sorted, rects, tile_keys,
+                                                  pair_items, n);
+    note_launches(1);
+}
+
+__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int K, uint2* __restrict__ ranges) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K) return;
+  const uint32_t t = keys[i];
+  if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
+  if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStream_t st) {
+  if (K > 0) {
+    k_tile_ranges<<<ceil_div(K, 256), 256, 0, st>>>(tile_keys, K, ranges);
+    note_launches(1);
+  }
+}
+
+__global__ void k_depth_bits(const uint64_t* __restrict__ dk, uint32_t* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const uint64_t k = dk[i];
+    out[i] = (k == ~0ull) ? 0xffffffffu : (uint32_t)(k & 0xffffffffull);
+  }
+}
+
+void launch_depth_bits(const uint64_t* depth_keys_unsorted, uint32_t* out, int n, cudaStream_t st) {
+  if (n > 0) {
+    k_depth_bits<<<ceil_div(n, 256), 256, 0, st>>>(depth_keys_unsorted, out, n);
+    note_launches(1);
+  }
+}
+
+}  // namespace ts

@@ -1,0 +1,149 @@
+// Shared device-side definitions of the textured 2DGS renderer (sm_103a).
+//
+// Layout decisions (HBM-resident, 16-byte aligned for vector loads):
+//   splat means / quaternions: float4 per splat (means padded with 0)
+//   scales: float2, opacity: float
+//   texels: [n][T][T][8] in float32 (32 B / texel) or bf16/f16 (16 B / texel)
+//   per-item raster record: 5 x float4 = 80 B (see Record below)
+//   pairs: (global tile id u32, item id u32) as two planes
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace ts {
+
+constexpr int TILE = 16;
+constexpr int TILE_PIX = TILE * TILE;
+constexpr int MAX_VIEWS = 32;
+constexpr int MAX_LEVELS = 12;
+constexpr int NCH = 8;
+
+// Thresholds of the method, as float32 values (identical in the oracle).
+__host__ __device__ constexpr float kNear() { return 0.2f; }
+__host__ __device__ constexpr float kAlphaMin() { return 1.0f / 255.0f; }
+__host__ __device__ constexpr float kAlphaMax() { return 0.99f; }
+__host__ __device__ constexpr float kTMin() { return 1e-4f; }
+__host__ __device__ constexpr float kAMin() { return 1e-7f; }
+__host__ __device__ constexpr float kNdotVMin() { return 1e-4f; }
+
+enum Dtype : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
+
+// Environment light (Eq. 11-12): specular mip chain, irradiance cube, BRDF LUT.
+struct EnvDesc {
+  const void* spec[MAX_LEVELS];  // [6][R_l][R_l][3]
+  int spec_res[MAX_LEVELS];
+  int levels;
+  const void* irr;  // [6][R][R][3]
+  int irr_res;
+  int cube_dtype;   // DT_F32 or DT_F16
+  const float* lut; // [R][R][2]
+  int lut_res;
+};
+
+// One view of a batch: camera, output buffers and the scene it renders.
+struct ViewDesc {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int W, H, tiles_x, tiles_y;
+  int tile_off;   // first global tile of the view
+  int item_off;   // first item (view-local splat index 0 maps here)
+  int n_splats;
+  // scene
+  const float4* means;
+  const float4* quats;
+  const float2* scales;
+  const float* opacity;
+  const void* texels;
+  int T;
+  int tex_dtype;
+  EnvDesc env;
+  // outputs / saved state
+  float4* rgba;   // [H][W]
+  float4* gbuf;   // [H][W][2] (X of Eq. 9, 8 channels)
+  float* trans;   // [H][W]
+  int* last;      // [H][W]
+  const float4* dl;  // backward input dL/drgba [H][W]
+};
+
+struct ViewTable {
+  int n_views;
+  int n_tiles;   // total tiles
+  int n_items;   // total items
+  ViewDesc v[MAX_VIEWS];
+};
+
+// Raster record of one (view, splat) item, written by the preprocess.
+// h_u, h_v, h_w are the homography rows of the splat in centred pixel
+// coordinates (x' = x + 0.5 - cx, y' = y + 0.5 - cy): u = h_u.x / h_w.x,
+// v = h_v.x / h_w.x with x = (x', y', 1) (closed-form ray-splat
+// intersection, Sec. 3.1).  tu, tv, nf: world-space tangent frame with the
+// normal turned towards the camera (for normal mapping, Eq. 7).
+struct Record {
+  float4 r0;  // hu0 hu1 hu2 hv0
+  float4 r1;  // hv1 hv2 hw0 hw1
+  float4 r2;  // hw2 opacity tu0 tu1
+  float4 r3;  // tu2 tv0 tv1 tv2
+  float4 r4;  // nf0 nf1 nf2 (splat id bits)
+};
+static_assert(sizeof(Record) == 80, "record is 5 x 16 B");
+
+__device__ __forceinline__ int find_view(const ViewTable& vt, int tile) {
+  int v = 0;
+  while (v + 1 < vt.n_views && vt.v[v + 1].tile_off <= tile) ++v;
+  return v;
+}
+__device__ __forceinline__ int find_view_item(const ViewTable& vt, int item) {
+  int v = 0;
+  while (v + 1 < vt.n_views && vt.v[v + 1].item_off <= item) ++v;
+  return v;
+}
+
+// ---- texel loads (stored dtype -> float32) ----------------------------------
+__device__ __forceinline__ void load_texel(const void* base, int dtype, long long idx, float out[8]) {
+  if (dtype == DT_F32) {
+    const float4* p = reinterpret_cast<const float4*>(base) + idx * 2;
+    float4 a = __ldg(p), b = __ldg(p + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+  } else {
+    uint4 raw = __ldg(reinterpret_cast<const uint4*>(base) + idx);
+    uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (dtype == DT_BF16) {
+        out[2 * i] = __uint_as_float(w[i] << 16);
+        out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+      } else {
+        __half2 h = *reinterpret_cast<__half2*>(&w[i]);
+        float2 f = __half22float2(h);
+        out[2 * i] = f.x;
+        out[2 * i + 1] = f.y;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float3 load_cube3(const void* base, int dtype, long long idx) {
+  if (dtype == DT_F32) {
+    const float* p = reinterpret_cast<const float*>(base) + idx * 3;
+    return make_float3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+  }
+  const __half* p = reinterpret_cast<const __half*>(base) + idx * 3;
+  return make_float3(__half2float(p[0]), __half2float(p[1]), __half2float(p[2]));
+}
+
+// Vector reduction into global memory (sm_90+ red.global.add.v4.f32).
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void red_add(float* addr, float a) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(a) : "memory");
+}
+
+}  // namespace ts

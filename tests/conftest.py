@@ -11,3 +11,11 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built_library():
+    """Compile libtexsplat.so in-tree if it is missing or stale (nvcc
+    cross-compiles without a GPU)."""
+    from paper_2506_13348_b300 import build as B
+    B.build()

@@ -1,0 +1,135 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: tile/sort lists bit-exact; images within 1e-4 max-abs on pixels the
+oracle does not flag as ambiguous (a threshold decision within a hair of
+flipping between FP32 and FP64), with at most 0.1 % of pixels flagged.
+"""
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+from oracle import keys as K
+from oracle import render as R
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2506_13348_b300 as P
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return P
+
+
+def gpu_render(P, scene, env, cam, store="f32", env_store="f32"):
+    sc = P.Scene.from_arrays(scene, env, store=store, env_store=env_store)
+    out, saved = P.render(sc, cam, save=True)
+    torch.cuda.synchronize()
+    return sc, out, saved
+
+
+def compare_lists(saved, kl, n):
+    ids, rng, db = saved.lists(n)
+    assert ids.size == kl["ids"].size
+    np.testing.assert_array_equal(ids, kl["ids"])
+    ref_rng = kl["tile_ranges"]
+    nonempty = ref_rng[:, 1] > ref_rng[:, 0]
+    np.testing.assert_array_equal(rng[nonempty], ref_rng[nonempty])
+    assert np.all(rng[~nonempty, 1] == rng[~nonempty, 0])  # empty tiles are empty ranges
+    vis = kl["view"]["visible"]
+    np.testing.assert_array_equal(db[vis], kl["view"]["depth_bits"][vis])
+    assert np.all(db[~vis] == 0xFFFFFFFF)
+
+
+def compare_image(gpu_rgba, ref, tol=IMG_TOL, max_masked=1e-3):
+    g = gpu_rgba.detach().cpu().numpy().astype(np.float64)
+    r = ref["rgba"].detach().numpy()
+    amb = ref["ambiguous"].numpy()
+    assert amb.mean() <= max_masked, amb.mean()
+    err = np.abs(g - r).max(-1)
+    bad = (err > tol) & ~amb
+    assert not bad.any(), (int(bad.sum()), float(err[~amb].max()), np.argwhere(bad)[:5])
+    return float(err[~amb].max())
+
+
+def test_cfg0_keys_bit_exact_and_image(P):
+    scene = sg.make_scene(0)
+    env = sg.make_env(0)
+    cam = sg.look_at_camera((4.0, 0.0, 0.0), 128, 128)
+    kl = K.build_keys(scene, cam)
+    sc, out, saved = gpu_render(P, scene, env, cam)
+    compare_lists(saved, kl, len(scene["opacity"]))
+    ref = R.render(scene, cam, env, keylist=kl)
+    compare_image(out, ref)
+    # per-pixel forward state
+    g, tr, last = saved.pixels(0)
+    amb = ref["ambiguous"].numpy()
+    np.testing.assert_allclose(g.cpu().numpy()[~amb], ref["X"].numpy()[~amb], atol=IMG_TOL)
+    np.testing.assert_allclose(tr.cpu().numpy()[~amb], ref["T"].numpy()[~amb], atol=IMG_TOL)
+    # last blended fragment: oracle index is within the tile list
+    tiles_x = kl["view"]["tiles_x"]
+    yy, xx = np.meshgrid(np.arange(128), np.arange(128), indexing="ij")
+    start = kl["tile_ranges"][(yy // 16) * tiles_x + xx // 16, 0]
+    ol = ref["last"].numpy()
+    exp_last = np.where(ol >= 0, start + ol, -1)
+    np.testing.assert_array_equal(last.cpu().numpy()[~amb], exp_last[~amb])
+
+
+@pytest.mark.parametrize("seed,W,H,eye", [(3, 100, 77, (2.5, 1.5, 1.0)), (5, 64, 48, (0.0, -3.0, 2.0)),
+                                          (8, 33, 129, (1.2, 1.2, -1.8))])
+def test_small_scenes_ragged_sizes(P, seed, W, H, eye):
+    scene = sg.make_scene(1, n=600, T=4, seed=seed)
+    env = sg.make_env(seed, cube_res=16, levels=3, irr_res=8, lut_res=32)
+    cam = sg.look_at_camera(eye, W, H)
+    kl = K.build_keys(scene, cam)
+    sc, out, saved = gpu_render(P, scene, env, cam)
+    compare_lists(saved, kl, 600)
+    compare_image(out, R.render(scene, cam, env, keylist=kl))
+
+
+def test_empty_and_culled_scenes(P):
+    env = sg.make_env(0, cube_res=8, irr_res=4, lut_res=16)
+    cam = sg.look_at_camera((4.0, 0.0, 0.0), 40, 24)
+    empty = dict(means=np.zeros((0, 3), np.float32), quats=np.zeros((0, 4), np.float32),
+                 scales=np.zeros((0, 2), np.float32), opacity=np.zeros(0, np.float32),
+                 texels=np.zeros((0, 4, 4, 8), np.float32), T=4)
+    sc, out, saved = gpu_render(P, empty, env, cam)
+    assert torch.count_nonzero(out).item() == 0
+    assert saved.sizes()[0] == 0
+    # every splat behind the camera: nothing binned
+    scene = sg.make_scene(0, n=50, T=2, seed=1)
+    scene["means"][:, 0] += 10.0
+    sc, out, saved = gpu_render(P, scene, env, cam)
+    assert saved.sizes()[0] == 0
+    assert torch.count_nonzero(out).item() == 0
+
+
+def test_forward_deterministic_and_batched_equals_alone(P):
+    scene = sg.make_scene(1, n=3000, T=4, seed=2)
+    env = sg.make_env(2, cube_res=16, levels=2, irr_res=8, lut_res=32)
+    cams = [sg.look_at_camera(e, w, h) for e, w, h in [((3.0, 0.5, 0.5), 96, 64), ((0.5, 3.5, 0.2), 50, 70),
+                                                        ((-2.0, -2.0, 2.0), 128, 128)]]
+    sc = P.Scene.from_arrays(scene, env)
+    alone = [P.render(sc, c)[0].clone() for c in cams]
+    again = [P.render(sc, c)[0].clone() for c in cams]
+    outs, _ = P.render_views([sc] * 3, cams)
+    torch.cuda.synchronize()
+    for a, b, c in zip(alone, again, outs):
+        assert torch.equal(a, b)
+        assert torch.equal(a, c)
+
+
+@pytest.mark.parametrize("store", ["bf16", "f16"])
+def test_reduced_precision_atlas_pipeline_parity(P, store):
+    # the oracle is fed the same rounded texels: pipeline parity within 1e-4
+    scene = sg.make_scene(0, n=400, T=8, seed=4)
+    env = sg.make_env(4, cube_res=16, irr_res=8, lut_res=32)
+    cam = sg.look_at_camera((3.0, 1.0, 0.5), 96, 96)
+    tt = torch.from_numpy(scene["texels"])
+    rounded = tt.to(torch.bfloat16 if store == "bf16" else torch.float16).float().numpy()
+    sc, out, saved = gpu_render(P, scene, env, cam, store=store)
+    ref = R.render(dict(scene, texels=rounded), cam, env)
+    compare_image(out, ref)

@@ -180,6 +180,38 @@ ts_status ts_saved_frag_stats(const ts_saved* saved, ts_frag_stats* out, void* s
 ts_status ts_l1_loss(const float* rgba, const float* target, int64_t n_pixels, float* loss_out,
                      float* dL_drgba, void* stream);
 
+/* ---- rendering without device allocation ------------------------------------ */
+
+/* The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory while they render: a renderer embedded in a
+ * host application that owns the whole device budget, a real-time frame
+ * loop that cannot accept an allocation's latency or failure, or a plugin
+ * that may only touch the buffers it is handed.
+ *
+ * Same forward render as ts_render (identical kernels and results), but
+ * every input is a caller device buffer and the call allocates nothing: no
+ * cudaMalloc / cudaFree / allocating library call.  Its working set lives in
+ * one fixed device array of about 21 MB compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   Limits: n <= 32768 splats, at most 8192 16x16 tiles (1920x1080 fits),
+ *   at most 1048576 (tile, splat) pairs after binning; beyond them the call
+ *   returns TS_ERR_CAPACITY (the pair limit is found after binning, so the
+ *   output is then left unwritten).
+ *   Inputs: means [n][3], quats [n][4] (16-byte aligned), scales [n][2]
+ *   (8-byte aligned), opacity [n], texels [n][T][T][8] float32 (16-byte
+ *   aligned), the environment as in ts_upload_envmap in float32 (spec
+ *   levels concatenated), camera by value, out_rgba [H][W][4].
+ *   The first call on a device looks up the array's device address (once
+ *   per device, with that device current): make that first call before any
+ *   stream capture.  Every call shares the array: the call clears what must
+ *   start at zero, and calls that overlap on the GPU (streams not ordered
+ *   with each other) race on it.  The call synchronises `stream` once to
+ *   read the pair count. */
+ts_status ts_render_noalloc(int64_t n, const float* means, const float* quats, const float* scales,
+                            const float* opacity, int T, const float* texels, int levels, int base_res,
+                            const float* spec, int irr_res, const float* irr, int lut_res, const float* lut,
+                            const ts_camera* cam, float* out_rgba, void* stream);
+
 /* ---- accounting and stage timing ------------------------------------------- */
 
 /* Number of kernels this library has launched since it was loaded (all

@@ -20,6 +20,7 @@ EXPORTED = [
     "ts_render", "ts_render_views", "ts_render_backward", "ts_release_saved", "ts_saved_sizes",
     "ts_saved_copy_lists", "ts_saved_copy_pixels", "ts_saved_frag_stats", "ts_l1_loss",
     "ts_launch_count", "ts_profile_enable", "ts_profile_report", "ts_last_error", "ts_version",
+    "ts_render_noalloc",
 ]
 
 
@@ -70,6 +71,8 @@ def lib() -> C.CDLL:
         "ts_l1_loss": [vp, vp, i64, vp, vp, vp],
         "ts_profile_enable": [i32],
         "ts_profile_report": [C.c_char_p, C.c_size_t],
+        "ts_render_noalloc": [i64, vp, vp, vp, vp, i32, vp, i32, i32, vp, i32, vp, i32, vp,
+                              C.POINTER(TsCamera), vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -115,6 +115,8 @@ struct ts_saved {
   int64_t K = 0;
 };
 
+int ts::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 static void free_scene_buffers(ts_scene* s) {
   void* ptrs[] = {s->means, s->quats, s->scales, s->opacity, s->texels, s->spec, s->irr, s->lut};
   for (void* p : ptrs)

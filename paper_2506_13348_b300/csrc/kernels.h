@@ -1,5 +1,7 @@
 // Host-side launch wrappers of the renderer's kernels.
 #pragma once
+#include <string>
+
 #include "ts_common.cuh"
 
 namespace ts {
@@ -13,6 +15,9 @@ struct GradTable {
   float* spec[MAX_LEVELS];
   float* irr;
 };
+
+// api.cu: records the message returned by ts_last_error() and returns code
+int set_error(int code, const std::string& msg);
 
 // preprocess.cu
 void launch_preprocess(const ViewTable& vt, Record* rec, uint32_t* counts, uint64_t* depth_keys,

@@ -331,7 +331,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   ViewTable vt;
   memset(&vt, 0, sizeof(vt));
   vt.n_views = n_views;
-  long long tiles = 0, items = 0;
+  long long tiles = 0, items = 0, pixels = 0;
   for (int i = 0; i < n_views; ++i) {
     const ts_camera& c = cams[i];
     const ts_scene* s = scenes[i];
@@ -344,6 +344,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     V.tiles_y = (c.height + TILE - 1) / TILE;
     V.tile_off = (int)tiles;
     V.item_off = (int)items;
+    V.pix_off = (int)pixels;
     V.n_splats = (int)s->n;
     V.means = s->means; V.quats = s->quats; V.scales = s->scales; V.opacity = s->opacity;
     V.texels = s->texels; V.T = s->T; V.tex_dtype = s->tex_dtype;
@@ -351,8 +352,10 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     V.rgba = reinterpret_cast<float4*>(out_rgba[i]);
     tiles += (long long)V.tiles_x * V.tiles_y;
     items += s->n;
+    pixels += (long long)V.W * V.H;
   }
-  if (items > INT32_MAX / 2 || tiles > INT32_MAX / 2) return fail(TS_ERR_CAPACITY, "ts_render_views: batch too large");
+  if (items > INT32_MAX / 2 || tiles > INT32_MAX / 2 || pixels > INT32_MAX / 4)
+    return fail(TS_ERR_CAPACITY, "ts_render_views: batch too large");
   vt.n_tiles = (int)tiles;
   vt.n_items = (int)items;
   const int n_items = vt.n_items;
@@ -543,11 +546,19 @@ ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, c
   }
   Scratch tmp(st);
   float* g_items = nullptr;
+  float4* gxa = nullptr;
+  long long n_pix = 0;
+  for (int i = 0; i < vt.n_views; ++i) n_pix += (long long)vt.v[i].W * vt.v[i].H;
   TS_CUDA(tmp.alloc((void**)&g_items, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(float)));
+  TS_CUDA(tmp.alloc((void**)&gxa, (size_t)std::max(n_pix, 1ll) * 3 * sizeof(float4)));
   TS_CUDA(cudaMemsetAsync(g_items, 0, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(float), st));
   {
+    ProfScope p(st, "shade_bwd");
+    launch_shade_bwd(vt, gxa, g, st);
+  }
+  {
     ProfScope p(st, "raster_bwd");
-    launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, g_items, g, st);
+    launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, gxa, g_items, g, st);
   }
   {
     ProfScope p(st, "preprocess_bwd");

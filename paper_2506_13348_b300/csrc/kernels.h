@@ -48,8 +48,10 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats,
                        cudaStream_t st);
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, float* g_items, const GradTable& g,
-                       cudaStream_t st);
+                       const uint2* ranges, int tex_dtype, const float4* gxa, float* g_items,
+                       const GradTable& g, cudaStream_t st);
+// shade_bwd.cu: per-pixel shading adjoint -> gxa [pixels][3] (dL/dX 0-3, 4-7, dL/dA)
+void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cudaStream_t st);
 
 // misc.cu
 void launch_pack_texels(const float* src, void* dst, long long n, int dtype, cudaStream_t st);

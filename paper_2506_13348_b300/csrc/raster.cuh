@@ -30,6 +30,33 @@ __device__ __forceinline__ bool eval_frag(const Record& r, float xp, float yp, F
   return f.alpha >= kAlphaMin();
 }
 
+// Conservative test: can splat r make a fragment at any pixel centre of the
+// block [x0, x1] x [y0, y1] (centred pixel coordinates)?  The block maps to a
+// convex quad in the splat's (u, v) plane with the corner images as vertices
+// whenever the homography's denominator keeps its sign over the block; the
+// splat is rejected only when all four corners lie beyond the same side of
+// the support square |u|, |v| <= 3 by a 0.1 % margin, far above the FP32
+// error of any pixel's (u, v).  Blocks the plane crosses edge-on are kept.
+__device__ __forceinline__ bool block_may_hit(const Record& r, float x0, float x1, float y0, float y1) {
+  float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+  float dmin = 3.0e38f, dmax = -3.0e38f;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float x = (c & 1) ? x1 : x0, y = (c & 2) ? y1 : y0;
+    const float den = fmaf(r.r1.z, x, fmaf(r.r1.w, y, r.r2.x));
+    const float un = fmaf(r.r0.x, x, fmaf(r.r0.y, y, r.r0.z));
+    const float vn = fmaf(r.r0.w, x, fmaf(r.r1.x, y, r.r1.y));
+    const float rd = __fdividef(1.0f, den);
+    const float u = un * rd, v = vn * rd;
+    umin = fminf(umin, u); umax = fmaxf(umax, u);
+    vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+    dmin = fminf(dmin, den); dmax = fmaxf(dmax, den);
+  }
+  if (!(dmin > 0.f || dmax < 0.f)) return true;
+  const float lim = 3.003f;
+  return !(umin > lim || umax < -lim || vmin > lim || vmax < -lim);
+}
+
 struct TexSample {
   int ia, ib, ja, jb;
   float fx, fy;

@@ -2,15 +2,18 @@
 //
 // Prologue: the shading adjoint (Eq. 10-12) turns dL/drgba into dL/dX (the
 // 8 G-buffer channels) and dL/dA, scattering environment gradients.
-// Main loop: the tile's list is walked back to front from the last
-// fragment any pixel of the tile blended, recomputing each fragment's (u,v),
-// alpha and texel value from the record (the per-pixel fragment lists are
-// never stored), recovering the transmittance in front of it by division
-// (alpha <= 0.99) and the colour behind it by the usual recurrence.  The
-// gradients of a fragment w.r.t. its splat's record (19 values) are summed
-// over the warp with a butterfly reduce-scatter (31 shuffles for 32 values)
-// and added once per warp; texel gradients go out as 16-byte vector
-// reductions.
+// Main loop: each warp (an 8x4 pixel block) walks the tile's list back to
+// front on its own, from the last fragment any of its pixels blended, with
+// no block-wide barrier.  Each fragment's (u,v), alpha and texel value are
+// recomputed from the splat's record (the per-pixel fragment lists are never
+// stored); the transmittance in front of it is recovered by division
+// (alpha <= 0.99) and the colour behind it by the usual recurrence.
+// Reductions (all lanes of a warp work on the same splat at a time):
+//   * the 19 record gradients of the fragment are transposed through shared
+//     memory and lane L < 19 sums value L over the warp (independent loads,
+//     tree add), adding it once per warp;
+//   * texel gradients go out as 16-byte vector reductions per lane (L2
+//     absorbs them; grouping lanes by bilinear cell first measured slower).
 #include "raster.cuh"
 #include "shading.cuh"
 #include "kernels.h"
@@ -18,30 +21,17 @@
 
 namespace ts {
 
-// Butterfly reduce-scatter: on return lane L holds the warp sum of v[L].
-__device__ __forceinline__ float warp_reduce_scatter32(float v[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int step = 16, cnt = 16; step >= 1; step >>= 1, cnt >>= 1) {
-    const bool upper = lane & step;
-#pragma unroll
-    for (int k = 0; k < cnt; ++k) {
-      const float send = upper ? v[k] : v[k + cnt];
-      const float keep = upper ? v[k + cnt] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, step);
-    }
-  }
-  return v[0];
-}
-
 template <int DT>
-__global__ void __launch_bounds__(256) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
-                                                     const uint32_t* __restrict__ pair_items,
-                                                     const uint2* __restrict__ ranges, float* __restrict__ g_items,
-                                                     GradTable g) {
-  __shared__ Record srec[256];
-  __shared__ uint32_t sitem[256];
-  __shared__ int s_hi;
+__global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
+                                                        const uint32_t* __restrict__ pair_items,
+                                                        const uint2* __restrict__ ranges,
+                                                        const float4* __restrict__ gxa, float* __restrict__ g_items,
+                                                        GradTable g) {
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ __align__(16) float s_gi[8][19][36];  // record gradients, value-major, per warp
+  __shared__ float4 s_rec[8][32][3];               // first 48 bytes of the records of a chunk
+  __shared__ uint32_t s_item[8][32];
+  const int warp = threadIdx.x >> 5;
   const int tile = blockIdx.x;
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
@@ -50,116 +40,130 @@ __global__ void __launch_bounds__(256) k_raster_bwd(ViewTable vt, const Record* 
   const bool inside = px < V.W && py < V.H;
   const float xp = (float)px + 0.5f - V.cx;
   const float yp = (float)py + 0.5f - V.cy;
-  const uint2 range = ranges[tile];
+  const int lo = (int)ranges[tile].x;
   const int T = V.T;
   const float Ts6 = (float)T * (1.0f / 6.0f);
+  const int lane = threadIdx.x & 31;
 
   float gX[8], gA = 0.f, Tcur = 1.f;
   int last = -1;
 #pragma unroll
   for (int c = 0; c < 8; ++c) gX[c] = 0.f;
-  if (threadIdx.x == 0) s_hi = -1;
   if (inside) {
     const int pix = py * V.W + px;
-    const float4 a = V.gbuf[2 * pix], b = V.gbuf[2 * pix + 1];
-    const float X[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const long long gp = (long long)V.pix_off + pix;
+    const float4 a = gxa[3 * gp], b = gxa[3 * gp + 1];
+    gX[0] = a.x; gX[1] = a.y; gX[2] = a.z; gX[3] = a.w;
+    gX[4] = b.x; gX[5] = b.y; gX[6] = b.z; gX[7] = b.w;
+    gA = gxa[3 * gp + 2].x;
     Tcur = V.trans[pix];
     last = V.last[pix];
-    const float4 dl = V.dl[pix];
-    shade_pixel_bwd(V.env, X, 1.f - Tcur, world_ray(V, xp, yp), dl, gX, gA, g.spec, g.irr);
   }
-  __syncthreads();
-  if (last >= 0) atomicMax(&s_hi, last);
-  __syncthreads();
-  const int hi_all = s_hi;
+  const int hi = __reduce_max_sync(FULL, last);
 
-  float S[8], SA = 0.f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) S[c] = 0.f;
-  const int lane = threadIdx.x & 31;
+  // dL/dX . (colour behind the current fragment) + dL/dA . (coverage behind it)
+  float P = 0.f;
 
-  for (int hi = hi_all; hi >= (int)range.x; hi -= 256) {
-    const int lo = max((int)range.x, hi - 255);
-    __syncthreads();
-    {
-      const int i = lo + (int)threadIdx.x;
-      if (i <= hi) {
-        const uint32_t it = pair_items[i];
-        sitem[threadIdx.x] = it;
-        srec[threadIdx.x] = rec[it];
-      }
+  // the warp's 8x4 pixel block in centred pixel coordinates (for culling)
+  const float bx0 = (float)(px - (lane & 7)) + 0.5f - V.cx, bx1 = bx0 + 7.f;
+  const float by0 = (float)(py - (lane >> 3)) + 0.5f - V.cy, by1 = by0 + 3.f;
+
+  // The list is taken 32 entries at a time, back to front: lane t loads the
+  // record of entry ch - t and tests it against the warp's block; only the
+  // surviving entries are processed, in back-to-front order.
+  for (int ch = hi; ch >= lo; ch -= 32) {
+    const int e = ch - lane;
+    bool cand = false;
+    if (e >= lo) {
+      const uint32_t it = __ldg(pair_items + e);
+      const float4* rp = reinterpret_cast<const float4*>(rec + it);
+      Record c;
+      c.r0 = __ldg(rp);
+      c.r1 = __ldg(rp + 1);
+      c.r2 = __ldg(rp + 2);
+      cand = block_may_hit(c, bx0, bx1, by0, by1);
+      s_rec[warp][lane][0] = c.r0;
+      s_rec[warp][lane][1] = c.r1;
+      s_rec[warp][lane][2] = c.r2;
+      s_item[warp][lane] = it;
     }
-    __syncthreads();
-    for (int j = hi; j >= lo; --j) {
-      const Record r = srec[j - lo];
-      float gi[32];
-#pragma unroll
-      for (int k = 0; k < 32; ++k) gi[k] = 0.f;
-      Frag f;
-      const bool ok = (j <= last) && eval_frag(r, xp, yp, f);
+    const unsigned cmask = __ballot_sync(FULL, cand);
+    __syncwarp();
+  for (unsigned cm = cmask; cm; cm &= cm - 1) {
+    const int t = __ffs(cm) - 1;
+    const int j = ch - t;
+    const uint32_t item = s_item[warp][t];
+    const float4* rp = reinterpret_cast<const float4*>(rec + item);
+    Record r;
+    r.r0 = s_rec[warp][t][0];
+    r.r1 = s_rec[warp][t][1];
+    r.r2 = s_rec[warp][t][2];
+    Frag f;
+    const bool ok = (j <= last) && eval_frag(r, xp, yp, f);
+    if (__any_sync(FULL, ok)) {
+      r.r3 = __ldg(rp + 3);
+      r.r4 = __ldg(rp + 4);
+      const long long splat = (long long)__float_as_int(r.r4.w);
+      float t8[8], w4[4] = {0.f, 0.f, 0.f, 0.f};
+      TexSample ts_;
+      ts_.ia = ts_.ib = ts_.ja = ts_.jb = 0;
+      float gi[19];
       if (ok) {
-        const TexSample ts_ = tex_setup(f.u, f.v, T);
-        const long long splat = (long long)__float_as_int(r.r4.w);
-        float x[8], cr[4][8];
-        tex_fetch<DT>(V.texels, splat, T, ts_, x, cr);
-        const float nt0 = x[5], nt1 = x[6], nt2 = x[7];
-        normal_map(r, x);
+        ts_ = tex_setup(f.u, f.v, T);
         const float om = 1.f - f.alpha;
         const float Tb = Tcur / om;
-        float ga = 0.f;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) ga += gX[c] * (x[c] - S[c]);
-        ga += gA * (1.f - SA);
-        ga *= Tb;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) S[c] = f.alpha * x[c] + om * S[c];
-        SA = f.alpha + om * SA;
         const float wgt = f.alpha * Tb;
-        Tcur = Tb;
-        float gx[8];
+        // g8: dL/dX pulled back to the texture channels (0-4 direct, 5-7
+        // through the normal map n = [t_u t_v n_f] n^t, i.e. R'^T dL/dN)
+        float g8[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) gx[c] = wgt * gX[c];
-        // alpha = min(0.99, o G)
+        for (int c = 0; c < 5; ++c) g8[c] = gX[c];
+        g8[5] = r.r2.z * gX[5] + r.r2.w * gX[6] + r.r3.x * gX[7];
+        g8[6] = r.r3.y * gX[5] + r.r3.z * gX[6] + r.r3.w * gX[7];
+        g8[7] = r.r4.x * gX[5] + r.r4.y * gX[6] + r.r4.z * gX[7];
+        // stream the four bilinear corners: only the projections g8 . texel
+        // and the tangent normal are needed
+        const float hx = 1.f - ts_.fx, hy = 1.f - ts_.fy;
+        w4[0] = hx * hy; w4[1] = ts_.fx * hy; w4[2] = hx * ts_.fy; w4[3] = ts_.fx * ts_.fy;
+        float nt0 = 0.f, nt1 = 0.f, nt2 = 0.f, gxx = 0.f, dxs = 0.f, dys = 0.f;
+        const long long base = splat * (long long)T * T;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int jj = (k & 2) ? ts_.jb : ts_.ja;
+          const int ii = (k & 1) ? ts_.ib : ts_.ia;
+          float cv[8];
+          load_texel(V.texels, DT, base + jj * T + ii, cv);
+          float tdot = 0.f;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) tdot = fmaf(g8[c], cv[c], tdot);
+          nt0 = fmaf(w4[k], cv[5], nt0);
+          nt1 = fmaf(w4[k], cv[6], nt1);
+          nt2 = fmaf(w4[k], cv[7], nt2);
+          gxx = fmaf(w4[k], tdot, gxx);
+          const float wyk = (k & 2) ? ts_.fy : hy;
+          const float wxk = (k & 1) ? ts_.fx : hx;
+          dxs += ((k & 1) ? wyk : -wyk) * tdot;
+          dys += ((k & 2) ? wxk : -wxk) * tdot;
+        }
+        // dL/dalpha = T_before (Q - P): Q = gX.x + gA of this fragment, P the
+        // same projection of everything blended behind it (P <- a Q + (1-a) P)
+        const float Q = gxx + gA;
+        const float ga = (Q - P) * Tb;
+        P = fmaf(f.alpha, Q, om * P);
+        Tcur = Tb;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) t8[c] = wgt * g8[c];
+        dxs *= wgt;
+        dys *= wgt;
+        const float gn0 = wgt * gX[5], gn1 = wgt * gX[6], gn2 = wgt * gX[7];
+        // alpha = min(0.99, o G), G = exp(-(u^2+v^2)/2)
         float go = 0.f, gG = 0.f;
         if (f.oG <= kAlphaMax()) {
           go = ga * f.G;
           gG = ga * r.r2.y;
         }
-        float gu = -gG * f.G * f.u, gv = -gG * f.G * f.v;
-        // normal mapping adjoint: x[5..7] = nt0 t_u + nt1 t_v + nt2 n_f
-        const float gn0 = gx[5], gn1 = gx[6], gn2 = gx[7];
-        float t8[8];
-        t8[0] = gx[0]; t8[1] = gx[1]; t8[2] = gx[2]; t8[3] = gx[3]; t8[4] = gx[4];
-        t8[5] = r.r2.z * gn0 + r.r2.w * gn1 + r.r3.x * gn2;
-        t8[6] = r.r3.y * gn0 + r.r3.z * gn1 + r.r3.w * gn2;
-        t8[7] = r.r4.x * gn0 + r.r4.y * gn1 + r.r4.z * gn2;
-        gi[10] = nt0 * gn0; gi[11] = nt0 * gn1; gi[12] = nt0 * gn2;
-        gi[13] = nt1 * gn0; gi[14] = nt1 * gn1; gi[15] = nt1 * gn2;
-        gi[16] = nt2 * gn0; gi[17] = nt2 * gn1; gi[18] = nt2 * gn2;
-        // bilinear adjoint: texel gradients and d/du, d/dv
-        const float fx = ts_.fx, fy = ts_.fy, hx = 1.f - fx, hy = 1.f - fy;
-        float dxs = 0.f, dys = 0.f;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          dxs += t8[c] * (hy * (cr[1][c] - cr[0][c]) + fy * (cr[3][c] - cr[2][c]));
-          dys += t8[c] * (hx * (cr[2][c] - cr[0][c]) + fx * (cr[3][c] - cr[1][c]));
-        }
-        gu += dxs * Ts6;
-        gv += dys * Ts6;
-        if (g.texels) {
-          const long long base = splat * (long long)T * T;
-          const long long idx[4] = {base + ts_.ja * T + ts_.ia, base + ts_.ja * T + ts_.ib,
-                                    base + ts_.jb * T + ts_.ia, base + ts_.jb * T + ts_.ib};
-          const float w4[4] = {hx * hy, fx * hy, hx * fy, fx * fy};
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (w4[k] != 0.f) {
-              float* p = g.texels + idx[k] * 8;
-              red_add_v4(p, w4[k] * t8[0], w4[k] * t8[1], w4[k] * t8[2], w4[k] * t8[3]);
-              red_add_v4(p + 4, w4[k] * t8[4], w4[k] * t8[5], w4[k] * t8[6], w4[k] * t8[7]);
-            }
-          }
-        }
+        const float gu = fmaf(dxs, Ts6, -gG * f.G * f.u);
+        const float gv = fmaf(dys, Ts6, -gG * f.G * f.v);
         // u = un / den, v = vn / den
         const float gun = gu * f.rd, gvn = gv * f.rd;
         const float gden = -(gu * f.u + gv * f.v) * f.rd;
@@ -167,25 +171,91 @@ __global__ void __launch_bounds__(256) k_raster_bwd(ViewTable vt, const Record* 
         gi[3] = gvn * xp; gi[4] = gvn * yp; gi[5] = gvn;
         gi[6] = gden * xp; gi[7] = gden * yp; gi[8] = gden;
         gi[9] = go;
+        gi[10] = nt0 * gn0; gi[11] = nt0 * gn1; gi[12] = nt0 * gn2;
+        gi[13] = nt1 * gn0; gi[14] = nt1 * gn1; gi[15] = nt1 * gn2;
+        gi[16] = nt2 * gn0; gi[17] = nt2 * gn1; gi[18] = nt2 * gn2;
       }
-      if (__any_sync(0xffffffffu, ok)) {
-        const float tot = warp_reduce_scatter32(gi);
-        if (lane < 19 && tot != 0.f) red_add(g_items + (size_t)sitem[j - lo] * 20 + lane, tot);
+      // per-splat record gradients (19 values): transpose through shared
+      // memory (value-major, rows padded to 36 floats so the 16-byte reads
+      // below are conflict-free), then lane L < 19 adds up value L of all
+      // 32 lanes with a tree and issues one reduction per warp
+      if (!ok) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) gi[q] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 19; ++q) s_gi[warp][q][lane] = gi[q];
+      __syncwarp();
+      if (lane < 19) {
+        const float4* col = reinterpret_cast<const float4*>(s_gi[warp][lane]);
+        float4 a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = col[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[q].x += a[q + 4].x; a[q].y += a[q + 4].y; a[q].z += a[q + 4].z; a[q].w += a[q + 4].w;
+        }
+        a[0].x += a[2].x; a[0].y += a[2].y; a[0].z += a[2].z; a[0].w += a[2].w;
+        a[1].x += a[3].x; a[1].y += a[3].y; a[1].z += a[3].z; a[1].w += a[3].w;
+        const float s = (a[0].x + a[1].x) + (a[0].y + a[1].y) + (a[0].z + a[1].z) + (a[0].w + a[1].w);
+        if (s != 0.f) red_add(g_items + (size_t)item * 20 + lane, s);
+      }
+      __syncwarp();
+      // texel gradients: pixels of a 2x2 quad that use the same bilinear cell
+      // (the four texels) are summed first -- horizontal pairs (lane ^ 1),
+      // then vertical pairs (lane ^ 8) -- and one lane per merged group
+      // issues the 16-byte vector reductions (L2 atomic throughput bounds this
+      // part, so fewer, fuller reductions pay for the shuffles)
+      if (g.texels) {
+        const unsigned key = ok ? (unsigned)((ts_.ja * T + ts_.ia) | ((ts_.jb * T + ts_.ib) << 10)) : FULL;
+        // merge decisions (identical for the four corners); every lane takes
+        // part in every shuffle
+        const unsigned pkey1 = __shfl_xor_sync(FULL, key, 1);
+        const bool m1 = ok && pkey1 == key;  // same key implies the partner is ok too
+        const bool k1 = (lane & 1) == 0;
+        const bool issue1 = ok && !(m1 && !k1);
+        const unsigned key2 = issue1 ? key : FULL - 1u;
+        const unsigned pkey2 = __shfl_xor_sync(FULL, key2, 8);
+        const bool m2 = issue1 && pkey2 == key2;
+        const bool k2 = (lane & 8) == 0;
+        const bool issue = issue1 && !(m2 && !k2);
+        float* gtex = g.texels + splat * (long long)T * T * 8;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float vt[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            float x = ok ? w4[k] * t8[c] : 0.f;
+            const float p1 = __shfl_xor_sync(FULL, x, 1);
+            if (m1 && k1) x += p1;
+            const float p2 = __shfl_xor_sync(FULL, x, 8);
+            if (m2 && k2) x += p2;
+            vt[c] = x;
+          }
+          if (issue) {
+            const int jj = (k & 2) ? ts_.jb : ts_.ja, ii = (k & 1) ? ts_.ib : ts_.ia;
+            float* p = gtex + (jj * T + ii) * 8;
+            red_add_v4(p, vt[0], vt[1], vt[2], vt[3]);
+            red_add_v4(p + 4, vt[4], vt[5], vt[6], vt[7]);
+          }
+        }
       }
     }
+  }
+    __syncwarp();
   }
 }
 
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, float* g_items, const GradTable& g,
-                       cudaStream_t st) {
+                       const uint2* ranges, int tex_dtype, const float4* gxa, float* g_items,
+                       const GradTable& g, cudaStream_t st) {
   dim3 grid(vt.n_tiles), block(256);
   if (tex_dtype == DT_F32)
-    k_raster_bwd<DT_F32><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, g_items, g);
+    k_raster_bwd<DT_F32><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
   else if (tex_dtype == DT_BF16)
-    k_raster_bwd<DT_BF16><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, g_items, g);
+    k_raster_bwd<DT_BF16><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
   else
-    k_raster_bwd<DT_F16><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, g_items, g);
+    k_raster_bwd<DT_F16><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
   note_launches(1);
 }
 

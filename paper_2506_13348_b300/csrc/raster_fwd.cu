@@ -1,14 +1,25 @@
 // Forward rasteriser: one CTA per 16x16 tile, one thread per pixel.
 //
 // The tile's depth-sorted splat list is walked front to back in batches of
-// 256 records staged in shared memory (one coalesced 80-byte record load
-// per thread).  Each pixel evaluates the closed-form (u, v) of every listed
-// splat, the Gaussian and the opacity, fetches the bilinear texel of the
-// splat's chart, maps the tangent normal to world space and blends the 8
-// G-buffer channels (Eq. 3, Eq. 8-9).  The CTA leaves the list as soon as
-// every pixel's transmittance fell below 1e-4 (block-wide vote).  Shading
-// (Eq. 10-12) is fused into the epilogue, so the G-buffer is written only
-// when the caller keeps it for the backward.
+// 256 records staged in shared memory (one 80-byte record load per thread).
+// Each batch is processed in chunks of 32 entries in three phases:
+//   0. lane t tests entry t of the chunk against the warp's whole 8x4 pixel
+//      block (conservative, see block_may_hit); typically most entries of a
+//      tile list miss a given block and are dropped here at ~2 instructions
+//      per entry;
+//   1. every lane tests the surviving entries for its pixel in lockstep (closed-form
+//      (u,v) of the splat, support cut, Gaussian, opacity -- Sec. 3.1,
+//      Eq. 2) and keeps a bitmask of the fragments that exist;
+//   2. every lane then blends its own set bits in list order: bilinear texel
+//      fetch from the splat's chart (Eq. 5-6), normal mapping (Eq. 7) and
+//      front-to-back compositing of the 8 G-buffer channels (Eq. 3, 8-9).
+// Phase 2 lets lanes work on different splats at the same time, so a warp
+// pays for max(fragments per lane) blends per chunk rather than for every
+// entry any lane blends.  Each pixel still blends exactly the fragments of
+// the definition, in order, with the same arithmetic.  The CTA leaves the list
+// once every pixel's transmittance fell below 1e-4.  Shading (Eq. 10-12) is
+// fused into the epilogue; the G-buffer is written only when the backward
+// needs it.
 #include "raster.cuh"
 #include "shading.cuh"
 #include "kernels.h"
@@ -22,6 +33,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
                                                      const uint2* __restrict__ ranges,
                                                      unsigned long long* __restrict__ stats) {
   __shared__ Record srec[256];
+  constexpr unsigned FULL = 0xffffffffu;
   const int tile = blockIdx.x;
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
@@ -32,14 +44,19 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
   const float yp = (float)py + 0.5f - V.cy;
   const uint2 range = ranges[tile];
   const int T = V.T;
+  const int lane = threadIdx.x & 31;
+  // the warp's 8x4 pixel block in centred pixel coordinates (for culling)
+  const float bx0 = (float)(px - (lane & 7)) + 0.5f - V.cx, bx1 = bx0 + 7.f;
+  const float by0 = (float)(py - (lane >> 3)) + 0.5f - V.cy, by1 = by0 + 3.f;
 
   float Tr = 1.f;
   float X[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) X[c] = 0.f;
   int last = -1;
+  int stop = -1;  // list index at which the pixel terminated (statistics)
   bool done = !inside;
-  unsigned n_eval = 0, n_blend = 0;
+  unsigned n_blend = 0;
 
   for (unsigned base = range.x; base < range.y; base += 256) {
     if (__syncthreads_count(done) == 256) break;
@@ -47,22 +64,43 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
     if (i < range.y) srec[threadIdx.x] = rec[pair_items[i]];
     __syncthreads();
     const int nb = min(256u, range.y - base);
-    for (int j = 0; j < nb && !done; ++j) {
-      const Record r = srec[j];
-      if (STATS) ++n_eval;
-      Frag f;
-      if (!eval_frag(r, xp, yp, f)) continue;
-      TexSample ts_ = tex_setup(f.u, f.v, T);
-      float x[8];
-      tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x, nullptr);
-      normal_map(r, x);
-      const float w = f.alpha * Tr;
+    for (int c0 = 0; c0 < nb; c0 += 32) {
+      if (__all_sync(FULL, done)) break;
+      // phase 0: lane t tests entry c0 + t against the warp's 8x4 block
+      const int cn = min(32, nb - c0);
+      const bool cand = lane < cn && block_may_hit(srec[c0 + lane], bx0, bx1, by0, by1);
+      const unsigned cmask = __ballot_sync(FULL, cand);
+      // phase 1: which of the surviving entries make a fragment at this pixel
+      unsigned mask = 0;
+      if (!done) {
+        for (unsigned m = cmask; m; m &= m - 1) {
+          const int t = __ffs(m) - 1;
+          Frag f;
+          if (eval_frag(srec[c0 + t], xp, yp, f)) mask |= 1u << t;
+        }
+      }
+      // phase 2: blend them in order
+      while (mask && !done) {
+        const int t = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const Record r = srec[c0 + t];
+        Frag f;
+        eval_frag(r, xp, yp, f);
+        const TexSample ts_ = tex_setup(f.u, f.v, T);
+        float x[8];
+        tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x, nullptr);
+        normal_map(r, x);
+        const float w = f.alpha * Tr;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
-      Tr = Tr * (1.f - f.alpha);
-      last = (int)(base + j);
-      if (STATS) ++n_blend;
-      if (Tr < kTMin()) done = true;
+        for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
+        Tr = Tr * (1.f - f.alpha);
+        last = (int)(base + c0 + t);
+        if (STATS) ++n_blend;
+        if (Tr < kTMin()) {
+          done = true;
+          stop = last;
+        }
+      }
     }
   }
 
@@ -79,11 +117,14 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
     }
   }
   if (STATS) {
-    unsigned long long e = n_eval, b = n_blend;
+    // evaluated fragments of the definition: list entries up to and including
+    // the one that terminated the pixel (the whole list if it never did)
+    unsigned long long e = inside ? (unsigned long long)((stop >= 0 ? stop + 1 : (int)range.y) - (int)range.x) : 0ull;
+    unsigned long long b = n_blend;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      e += __shfl_xor_sync(0xffffffffu, e, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
+      e += __shfl_xor_sync(FULL, e, o);
+      b += __shfl_xor_sync(FULL, b, o);
     }
     if ((threadIdx.x & 31) == 0) {
       atomicAdd(stats + 0, e);
@@ -96,12 +137,12 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats,
                        cudaStream_t st) {
   dim3 grid(vt.n_tiles), block(256);
-#define TS_LAUNCH(DTV)                                                                         \
-  if (stats)                                                                                   \
-    k_raster_fwd<DTV, false, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
-  else if (save)                                                                               \
-    k_raster_fwd<DTV, true, false><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
-  else                                                                                         \
+#define TS_LAUNCH(DTV)                                                                          \
+  if (stats)                                                                                    \
+    k_raster_fwd<DTV, false, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);  \
+  else if (save)                                                                                \
+    k_raster_fwd<DTV, true, false><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);  \
+  else                                                                                          \
     k_raster_fwd<DTV, false, false><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
   if (tex_dtype == DT_F32) {
     TS_LAUNCH(DT_F32)

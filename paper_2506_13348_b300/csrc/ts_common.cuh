@@ -51,6 +51,7 @@ struct ViewDesc {
   int W, H, tiles_x, tiles_y;
   int tile_off;   // first global tile of the view
   int item_off;   // first item (view-local splat index 0 maps here)
+  int pix_off;    // first pixel of the view in batch-wide per-pixel buffers
   int n_splats;
   // scene
   const float4* means;

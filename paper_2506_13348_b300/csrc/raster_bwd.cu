@@ -208,17 +208,23 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
       // part, so fewer, fuller reductions pay for the shuffles)
       if (g.texels) {
         const unsigned key = ok ? (unsigned)((ts_.ja * T + ts_.ia) | ((ts_.jb * T + ts_.ib) << 10)) : FULL;
-        // merge decisions (identical for the four corners); every lane takes
-        // part in every shuffle
-        const unsigned pkey1 = __shfl_xor_sync(FULL, key, 1);
-        const bool m1 = ok && pkey1 == key;  // same key implies the partner is ok too
-        const bool k1 = (lane & 1) == 0;
-        const bool issue1 = ok && !(m1 && !k1);
-        const unsigned key2 = issue1 ? key : FULL - 1u;
-        const unsigned pkey2 = __shfl_xor_sync(FULL, key2, 8);
-        const bool m2 = issue1 && pkey2 == key2;
-        const bool k2 = (lane & 8) == 0;
-        const bool issue = issue1 && !(m2 && !k2);
+        // merge decisions (identical for the four corners), butterfly over
+        // lane bits 0 (x) and 3 (y): at each level two lanes that still hold
+        // values and share the cell combine into the lower lane.  (Merging
+        // 4x4 pixel groups as well measured slower: the extra shuffles cost
+        // more than the reductions they save.)  Every lane takes part in
+        // every shuffle.
+        constexpr int NLVL = 2;
+        const int offs[NLVL] = {1, 8};
+        bool mrg[NLVL];
+        bool issue = ok;
+#pragma unroll
+        for (int l = 0; l < NLVL; ++l) {
+          const unsigned kl = issue ? key : FULL - 1u;
+          const unsigned pk = __shfl_xor_sync(FULL, kl, offs[l]);
+          mrg[l] = issue && pk == kl;  // same live key implies the partner is live too
+          if (mrg[l] && (lane & offs[l])) issue = false;
+        }
         float* gtex = g.texels + splat * (long long)T * T * 8;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -226,10 +232,11 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             float x = ok ? w4[k] * t8[c] : 0.f;
-            const float p1 = __shfl_xor_sync(FULL, x, 1);
-            if (m1 && k1) x += p1;
-            const float p2 = __shfl_xor_sync(FULL, x, 8);
-            if (m2 && k2) x += p2;
+#pragma unroll
+            for (int l = 0; l < NLVL; ++l) {
+              const float p = __shfl_xor_sync(FULL, x, offs[l]);
+              if (mrg[l] && !(lane & offs[l])) x += p;
+            }
             vt[c] = x;
           }
           if (issue) {

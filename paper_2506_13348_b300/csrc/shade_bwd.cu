@@ -90,8 +90,12 @@ __global__ void __launch_bounds__(SB_THREADS) k_shade_bwd(ViewTable vt, long lon
     for (int i = threadIdx.x; i < lay.total; i += blockDim.x) s_env[i] = 0.f;
     __syncthreads();
   }
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n_pix;
-       p += (long long)gridDim.x * blockDim.x) {
+  // each CTA takes a contiguous run of pixels (a band of rows): neighbouring
+  // pixels reflect similar directions, so a CTA touches few cube texels and
+  // its flush below skips the untouched (zero) ones
+  const long long per = (n_pix + gridDim.x - 1) / gridDim.x;
+  const long long p_end = min(n_pix, per * (blockIdx.x + 1));
+  for (long long p = per * blockIdx.x + threadIdx.x; p < p_end; p += blockDim.x) {
     // view of this pixel (views are few; linear scan)
     int v = 0;
     long long off = 0;

@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--cpu-tiles", type=int, default=6, help="tiles of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-view latency measurement")
+    ap.add_argument("--serve-only", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-warmup", type=int, default=100)
+    ap.add_argument("--serve-rate", type=float, default=1.0, help="arrival rate / plain saturated fps")
     return ap.parse_args()
 
 
@@ -282,6 +287,11 @@ def run_ours(args):
             "clocks": clocks}
     if not args.no_e2e:
         line["e2e"] = run_e2e(P, sc, my_cams, n_needed, args, dev, pg, world)
+    if rank == 0 and not args.no_serve:
+        del grads
+        sc.close()
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, thr, px = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -293,6 +303,89 @@ def run_ours(args):
         pg.barrier()
         pg.destroy_process_group()
     return 0
+
+
+def run_serving(args, device):
+    """Served-view latency: 3 resident scenes (200k / 500k / 1M splats, 8x8
+    texels), Poisson arrivals of views at random cameras (radius U[3.5, 5])
+    and resolutions drawn from {400x400, 800x800, 1280x720, 1920x1080}.
+    'plain' = FP32 atlas, one request at a time, FIFO on one stream;
+    'served' = BF16 atlas, continuous batching (2 streams, up to 8 views per
+    batch).  Both see the same arrival schedule at rate = rate_factor x the
+    plain renderer's saturated throughput."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2506_13348_b300 as P
+    import scenegen as sg
+
+    env = sg.make_env(3, cube_res=32, levels=1, irr_res=8, lut_res=128)
+    sizes = [200_000, 500_000, 1_000_000]
+    plain_sc, served_sc = [], []
+    for i, n in enumerate(sizes):
+        s = sg.make_scene(1, n=n, T=8, seed=300 + i)
+        plain_sc.append(P.Scene.from_arrays(s, env, device=device, store="f32"))
+        served_sc.append(P.Scene.from_arrays(s, env, device=device, store="bf16"))
+        del s
+    rng = np.random.default_rng(3)
+    nreq = args.serve_requests + args.serve_warmup
+    res = [(400, 400), (800, 800), (1280, 720), (1920, 1080)]
+    cams = sg.random_sphere_cameras(rng, nreq, 3.5, 5.0, res)
+    which = rng.integers(0, 3, size=nreq)
+
+    def run(server, scenes, gaps):
+        tickets = [None] * nreq
+        done = threading.Event()
+
+        def consumer():
+            for i in range(nreq):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                server.wait(tickets[i], None, timeout_s=120.0)
+                if i == args.serve_warmup - 1:
+                    server.reset_stats()
+            done.set()
+
+        th = threading.Thread(target=consumer)
+        th.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(nreq):
+            if gaps is not None:
+                t_next += gaps[i]
+                while True:
+                    d = t_next - time.perf_counter()
+                    if d <= 0:
+                        break
+                    time.sleep(min(d, 0.001) if d > 0.0015 else 0)
+            tickets[i] = server.submit(scenes[which[i]], cams[i])
+        th.join()
+        return server.stats()
+
+    arena = 24 << 30
+    plain = P.Server(device=device, arena_bytes=arena, n_streams=1, max_batch=1)
+    sat = run(plain, plain_sc, None)  # all at once: saturated FIFO throughput
+    rate = args.serve_rate * sat["fps"]
+    gaps = np.random.default_rng(33).exponential(1.0 / rate, size=nreq)
+    p = run(plain, plain_sc, gaps)
+    plain.close()
+    served = P.Server(device=device, arena_bytes=arena, n_streams=2, max_batch=8)
+    s = run(served, served_sc, gaps)
+    s_sat = run(served, served_sc, None)
+    served.close()
+    keep = ("p50_ms", "p99_ms", "mean_ms", "fps", "mpix_per_s", "mean_batch", "completed", "rejected")
+    for sc in plain_sc + served_sc:
+        sc.close()
+    return {"workload": "cfg3: scenes of 200k/500k/1M splats (8x8 texels), Poisson arrivals, "
+                        "resolutions {400^2, 800^2, 1280x720, 1920x1080}, radius U[3.5,5]",
+            "requests": args.serve_requests, "warmup_requests": args.serve_warmup,
+            "arrival_rate_fps": rate, "rate_factor": args.serve_rate,
+            "plain_saturated_fps": sat["fps"], "served_saturated_fps": s_sat["fps"],
+            "served_saturated_mean_batch": s_sat["mean_batch"],
+            "plain_fp32_one_at_a_time": {k: p[k] for k in keep},
+            "served_bf16_batched": {k: s[k] for k in keep}}
 
 
 def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
@@ -365,6 +458,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve_only:
+        import torch
+        torch.cuda.set_device(dist_env()[2])
+        print(json.dumps({"serving": run_serving(args, dist_env()[2])}))
+        return 0
     return run_ours(args)
 
 

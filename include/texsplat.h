@@ -172,6 +172,52 @@ ts_status ts_saved_copy_pixels(const ts_saved* saved, int view, float* gbuf, flo
  * over the same lists).  Synchronises the stream. */
 ts_status ts_saved_frag_stats(const ts_saved* saved, ts_frag_stats* out, void* stream);
 
+/* Geometry size, texture resolution and stored atlas dtype of a scene (any
+ * pointer may be NULL).  TS_ERR_STATE if geometry or atlas is missing. */
+ts_status ts_scene_info(const ts_scene* scene, int64_t* n, int* T, int* dtype);
+
+/* ---- serving: continuous batching of view requests ------------------------------ */
+
+typedef struct ts_server ts_server;
+
+typedef struct ts_serve_stats {
+  int64_t submitted, completed, rejected, failed, batches;
+  double mean_batch;      /* views per launched batch */
+  double p50_ms, p99_ms;  /* latency, submission -> completion of the batch's last kernel */
+  double mean_ms;
+  double fps;             /* completed views / (last completion - first submission) */
+  double mpix_per_s;
+} ts_serve_stats;
+
+/* Starts a view server on `device` with n_streams worker threads (one CUDA
+ * stream each, 1..16), batches of at most max_batch views (1..32), and a
+ * device-memory budget of arena_bytes for requests in flight (outputs plus
+ * estimated binning memory).  Scenes stay resident: requests name a scene
+ * created and uploaded beforehand; it must outlive its requests. */
+ts_status ts_server_create(ts_server** out, int device, size_t arena_bytes, int n_streams, int max_batch);
+
+/* Stops the workers (queued requests are dropped) and frees everything. */
+ts_status ts_server_destroy(ts_server* server);
+
+/* Queues one view (forward render, no backward state) and returns a ticket
+ * at once.  A worker that becomes free takes every queued request that fits
+ * -- same atlas dtype, within max_batch and the memory budget -- into one
+ * batched launch sequence (ts_render_views); requests arriving meanwhile
+ * join the next batch.  TS_ERR_CAPACITY if the request alone exceeds the
+ * budget (counted as rejected). */
+ts_status ts_server_submit(ts_server* server, ts_scene* scene, const ts_camera* cam, uint64_t* ticket);
+
+/* Waits up to timeout_s seconds for a ticket (TS_ERR_TIMEOUT, ticket kept),
+ * then copies its RGBA image [H][W][4] to out_rgba (device memory if
+ * out_on_device, else host; NULL discards) and retires the ticket.  The
+ * image is identical to ts_render's for the same scene and camera. */
+ts_status ts_server_wait(ts_server* server, uint64_t ticket, float* out_rgba, int out_on_device,
+                         double timeout_s);
+
+/* Latency / throughput counters since creation or the last reset. */
+ts_status ts_server_stats(ts_server* server, ts_serve_stats* out);
+ts_status ts_server_reset_stats(ts_server* server);
+
 /* ---- training helpers --------------------------------------------------------- */
 
 /* L1 image loss over the RGB channels: loss_out[0] = mean |rgba - target|

@@ -20,7 +20,8 @@ EXPORTED = [
     "ts_render", "ts_render_views", "ts_render_backward", "ts_release_saved", "ts_saved_sizes",
     "ts_saved_copy_lists", "ts_saved_copy_pixels", "ts_saved_frag_stats", "ts_l1_loss",
     "ts_launch_count", "ts_profile_enable", "ts_profile_report", "ts_last_error", "ts_version",
-    "ts_render_noalloc",
+    "ts_render_noalloc", "ts_scene_info", "ts_server_create", "ts_server_destroy", "ts_server_submit",
+    "ts_server_wait", "ts_server_stats", "ts_server_reset_stats",
 ]
 
 
@@ -36,6 +37,13 @@ class TsGrads(C.Structure):
 class TsFragStats(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_evaluated", C.c_int64), ("n_blended", C.c_int64),
                 ("n_visible", C.c_int64)]
+
+
+class TsServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
+                ("failed", C.c_int64), ("batches", C.c_int64), ("mean_batch", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("fps", C.c_double),
+                ("mpix_per_s", C.c_double)]
 
 
 class TexSplatError(RuntimeError):
@@ -73,6 +81,13 @@ def lib() -> C.CDLL:
         "ts_profile_report": [C.c_char_p, C.c_size_t],
         "ts_render_noalloc": [i64, vp, vp, vp, vp, i32, vp, i32, i32, vp, i32, vp, i32, vp,
                               C.POINTER(TsCamera), vp, vp],
+        "ts_scene_info": [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)],
+        "ts_server_create": [C.POINTER(vp), i32, C.c_size_t, i32, i32],
+        "ts_server_destroy": [vp],
+        "ts_server_submit": [vp, vp, C.POINTER(TsCamera), C.POINTER(C.c_uint64)],
+        "ts_server_wait": [vp, C.c_uint64, vp, i32, C.c_double],
+        "ts_server_stats": [vp, C.POINTER(TsServeStats)],
+        "ts_server_reset_stats": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -252,3 +252,52 @@ class TexSplatRender(torch.autograd.Function):
         ctx.saved.release()
         return (None, None, None, grads["means"], grads["quats"], grads["scales"], grads["opacity"],
                 grads["texels"], grads["spec"], grads["irr"].reshape(6, *([int((scene.irr_size / 18) ** 0.5)] * 2), 3))
+
+
+class Server:
+    """Continuous-batching view server (library worker threads and streams).
+
+    ``submit`` returns a ticket at once; ``wait`` returns the image.  Scenes
+    must stay alive while their requests are pending."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 8 << 30, n_streams: int = 2, max_batch: int = 8):
+        from ._lib import TsServeStats  # noqa: F401
+        h = C.c_void_p()
+        check(lib().ts_server_create(C.byref(h), device, arena_bytes, n_streams, max_batch), "ts_server_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().ts_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, scene: Scene, cam: dict) -> int:
+        c = make_camera(cam)
+        t = C.c_uint64()
+        check(lib().ts_server_submit(self.handle, scene.handle, C.byref(c), C.byref(t)), "ts_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, out: torch.Tensor | None = None, timeout_s: float = 60.0):
+        """Copies the result into ``out`` (CUDA or CPU float32 [H,W,4]);
+        returns ``out``.  ``out=None`` discards the image."""
+        ptr = C.c_void_p(out.data_ptr()) if out is not None else C.c_void_p(0)
+        on_dev = 1 if (out is not None and out.is_cuda) else 0
+        check(lib().ts_server_wait(self.handle, C.c_uint64(ticket), ptr, on_dev, C.c_double(timeout_s)),
+              "ts_server_wait")
+        return out
+
+    def stats(self) -> dict:
+        from ._lib import TsServeStats
+        s = TsServeStats()
+        check(lib().ts_server_stats(self.handle, C.byref(s)), "ts_server_stats")
+        return {k: getattr(s, k) for k, _ in TsServeStats._fields_}
+
+    def reset_stats(self):
+        check(lib().ts_server_reset_stats(self.handle), "ts_server_reset_stats")

@@ -634,6 +634,15 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   return TS_OK;
 }
 
+ts_status ts_scene_info(const ts_scene* s, int64_t* n, int* T, int* dtype) {
+  if (!s) return fail(TS_ERR_ARG, "ts_scene_info: scene is NULL");
+  if (!s->means || !s->texels) return fail(TS_ERR_STATE, "ts_scene_info: geometry or atlas missing");
+  if (n) *n = s->n;
+  if (T) *T = s->T;
+  if (dtype) *dtype = s->tex_dtype;
+  return TS_OK;
+}
+
 ts_status ts_l1_loss(const float* rgba, const float* target, int64_t n_pixels, float* loss_out, float* dL_drgba,
                      void* stream) {
   if (!rgba || !target || !loss_out || !dL_drgba || n_pixels < 0) return fail(TS_ERR_ARG, "ts_l1_loss: bad argument");

@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-warmup", type=int, default=100)
     ap.add_argument("--serve-rate", type=float, default=1.0, help="arrival rate / plain saturated fps")
+    ap.add_argument("--no-large", action="store_true", help="skip the 3M-splat training-step measurement")
+    ap.add_argument("--large-only", action="store_true")
+    ap.add_argument("--large-steps", type=int, default=10)
+    ap.add_argument("--large-warmup", type=int, default=3)
     return ap.parse_args()
 
 
@@ -292,6 +296,8 @@ def run_ours(args):
         sc.close()
         torch.cuda.empty_cache()
         line["serving"] = run_serving(args, local)
+    if rank == 0 and not args.no_large:
+        line["large_scene"] = run_large_scene(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, thr, px = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -388,6 +394,55 @@ def run_serving(args, device):
             "served_bf16_batched": {k: s[k] for k in keep}}
 
 
+def run_large_scene(args, device):
+    """Large-scene training step: 3M splats in a 10^3 box (60% on 32
+    spheres, 40% uniform), 8x8 texels stored in BF16 with float32 masters,
+    4 views of 1600x1064 per step from a radius-12 Fibonacci set: batched
+    forward, L1 loss, backward, Adam on geometry and texels (master ->
+    stored atlas), in-place geometry update."""
+    import torch
+
+    import paper_2506_13348_b300 as P
+    import scenegen as sg
+
+    dev = torch.device("cuda", device)
+    torch.cuda.reset_peak_memory_stats(dev)
+    geo = sg.make_scene(4, with_texels=False)
+    n = len(geo["opacity"])
+    tex = sg.scenes.texels_torch(n, 8, seed=4, device=dev)
+    env = sg.make_env(4, cube_res=32, levels=1, irr_res=8, lut_res=128)
+    sc = P.Scene.from_arrays(dict(geo, texels=tex), env, device=device, store="bf16")
+    tr = P.Trainer(sc, dict(geo, texels=tex), store="bf16")
+    del tex
+    W, H, V = 1600, 1064, 4
+    cams = sg.fibonacci_cameras(40, 12.0, W, H)
+    targets = [torch.from_numpy(sg.make_target(i, W, H)).to(dev) for i in range(V)]
+    outs = [torch.empty(H, W, 4, device=dev) for _ in range(V)]
+    dls = [torch.empty_like(o) for o in outs]
+    for i in range(args.large_warmup):
+        tr.step(cams[(i * V) % 40:(i * V) % 40 + V], targets, outs, dls)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.large_steps):
+        j = ((args.large_warmup + i) * V) % 40
+        tr.step(cams[j:j + V], targets, outs, dls)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.large_steps
+    peak = torch.cuda.max_memory_allocated(dev) / 1e9
+    free, total = torch.cuda.mem_get_info(dev)
+    out = {"workload": "cfg4: 3M splats in [-5,5]^3 (60% on 32 spheres, 40% uniform), 8x8 texels BF16 with "
+                       "FP32 masters + Adam, 4 views of 1600x1064 per step",
+           "splats": n, "steps": args.large_steps, "ms_per_step": ms,
+           "mpix_per_s": V * W * H / 1e6 / (ms / 1e3),
+           "torch_peak_alloc_gb": peak, "device_used_gb": (total - free) / 1e9}
+    sc.close()
+    del tr
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
     """Same step through the public API with host buffers: the target image
     goes host->device from pinned memory and the loss comes back each step."""
@@ -458,10 +513,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.serve_only:
+    if args.serve_only or args.large_only:
         import torch
         torch.cuda.set_device(dist_env()[2])
-        print(json.dumps({"serving": run_serving(args, dist_env()[2])}))
+        res = {}
+        if args.serve_only:
+            res["serving"] = run_serving(args, dist_env()[2])
+        if args.large_only:
+            res["large_scene"] = run_large_scene(args, dist_env()[2])
+        print(json.dumps(res))
         return 0
     return run_ours(args)
 

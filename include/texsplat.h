@@ -176,6 +176,36 @@ ts_status ts_saved_frag_stats(const ts_saved* saved, ts_frag_stats* out, void* s
  * pointer may be NULL).  TS_ERR_STATE if geometry or atlas is missing. */
 ts_status ts_scene_info(const ts_scene* scene, int64_t* n, int* T, int* dtype);
 
+/* ---- training: optimiser step and in-place scene updates ------------------------ */
+
+/* Adam (Kingma & Ba) hyper-parameters; step >= 1 is the 1-based update count
+ * used for the bias corrections. */
+typedef struct ts_adam {
+  float lr, beta1, beta2, eps;
+  int64_t step;
+} ts_adam;
+
+/* One Adam step on n float32 master parameters `param` with gradient `grad`
+ * and moments m, v (all device, 16-byte aligned, updated in place).  If
+ * zero_grad, `grad` is zeroed after use (the backward accumulates).  If
+ * `shadow` is non-NULL the updated parameters are also written there in
+ * `shadow_dtype` (float32, or bfloat16 / float16 rounded to nearest even) --
+ * e.g. the scene's stored atlas from ts_scene_texels, so training keeps
+ * float32 masters while rendering reads the reduced-precision copy.
+ * Stream-ordered, no synchronisation. */
+ts_status ts_adam_update(float* param, float* grad, float* m, float* v, int64_t n, const ts_adam* hp, void* shadow,
+                         ts_dtype shadow_dtype, int zero_grad, void* stream);
+
+/* Device pointer, resolution and dtype of a scene's stored atlas
+ * ([n][T][T][8] in that dtype); valid until the atlas is re-uploaded. */
+ts_status ts_scene_texels(ts_scene* scene, void** texels, int* T, int* dtype);
+
+/* Overwrites the scene's geometry (same n as uploaded) from device arrays,
+ * stream-ordered without synchronisation (for updates between training
+ * steps).  Layouts as in ts_upload_gaussians. */
+ts_status ts_scene_set_geometry(ts_scene* scene, const float* means, const float* quats, const float* scales,
+                                const float* opacity, void* stream);
+
 /* ---- serving: continuous batching of view requests ------------------------------ */
 
 typedef struct ts_server ts_server;

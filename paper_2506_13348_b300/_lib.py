@@ -21,7 +21,8 @@ EXPORTED = [
     "ts_saved_copy_lists", "ts_saved_copy_pixels", "ts_saved_frag_stats", "ts_l1_loss",
     "ts_launch_count", "ts_profile_enable", "ts_profile_report", "ts_last_error", "ts_version",
     "ts_render_noalloc", "ts_scene_info", "ts_server_create", "ts_server_destroy", "ts_server_submit",
-    "ts_server_wait", "ts_server_stats", "ts_server_reset_stats",
+    "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
+    "ts_adam_update",
 ]
 
 
@@ -44,6 +45,11 @@ class TsServeStats(C.Structure):
                 ("failed", C.c_int64), ("batches", C.c_int64), ("mean_batch", C.c_double),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("fps", C.c_double),
                 ("mpix_per_s", C.c_double)]
+
+
+class TsAdam(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("step", C.c_int64)]
 
 
 class TexSplatError(RuntimeError):
@@ -82,6 +88,9 @@ def lib() -> C.CDLL:
         "ts_render_noalloc": [i64, vp, vp, vp, vp, i32, vp, i32, i32, vp, i32, vp, i32, vp,
                               C.POINTER(TsCamera), vp, vp],
         "ts_scene_info": [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32)],
+        "ts_scene_texels": [vp, C.POINTER(vp), C.POINTER(i32), C.POINTER(i32)],
+        "ts_scene_set_geometry": [vp, vp, vp, vp, vp, vp],
+        "ts_adam_update": [vp, vp, vp, vp, i64, C.POINTER(TsAdam), vp, i32, i32, vp],
         "ts_server_create": [C.POINTER(vp), i32, C.c_size_t, i32, i32],
         "ts_server_destroy": [vp],
         "ts_server_submit": [vp, vp, C.POINTER(TsCamera), C.POINTER(C.c_uint64)],

@@ -301,3 +301,69 @@ class Server:
 
     def reset_stats(self):
         check(lib().ts_server_reset_stats(self.handle), "ts_server_reset_stats")
+
+
+def adam_update(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int,
+                lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, shadow_ptr: int = 0,
+                shadow_dtype="f32", zero_grad: bool = True, stream=None):
+    """One fused Adam step in the library (see ts_adam_update)."""
+    from ._lib import TsAdam
+    hp = TsAdam(lr, beta1, beta2, eps, step)
+    check(lib().ts_adam_update(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), C.byref(hp),
+                               C.c_void_p(shadow_ptr), DTYPES[shadow_dtype], 1 if zero_grad else 0,
+                               _stream(stream)), "ts_adam_update")
+
+
+def scene_texels(scene: Scene):
+    """(device pointer, T, dtype code) of the scene's stored atlas."""
+    p, T, dt = C.c_void_p(), C.c_int(), C.c_int()
+    check(lib().ts_scene_texels(scene.handle, C.byref(p), C.byref(T), C.byref(dt)), "ts_scene_texels")
+    return p.value, T.value, dt.value
+
+
+class Trainer:
+    """Multi-view training step on one scene, all in library kernels: a
+    batched forward of V views (saved state), the L1 loss of each view, one
+    backward over the batch, then Adam on float32 masters of geometry and
+    texels with the texel master written back into the scene's stored atlas
+    (bf16 / f16 / f32) and the geometry updated in place."""
+
+    def __init__(self, scene: Scene, data: dict, store: str = "bf16", lr_geom: float = 1e-4,
+                 lr_tex: float = 1e-2):
+        dev = torch.device("cuda", scene.device)
+        f = lambda a: _dev_f32(a, dev).clone()  # noqa: E731
+        self.scene, self.store = scene, store
+        self.master = dict(means=f(data["means"]), quats=f(data["quats"]), scales=f(data["scales"]),
+                           opacity=f(data["opacity"]), texels=f(data["texels"]))
+        self.m = {k: torch.zeros_like(t) for k, t in self.master.items()}
+        self.v = {k: torch.zeros_like(t) for k, t in self.master.items()}
+        self.grads = zero_grads(scene)
+        self.lr = dict(means=lr_geom, quats=lr_geom, scales=lr_geom, opacity=lr_geom, texels=lr_tex)
+        self.step_count = 0
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def step(self, cams, targets, outs=None, dls=None):
+        """One step over the views ``cams`` with target images ``targets``
+        ([H,W,4] CUDA each).  Returns the per-view loss tensor (device)."""
+        n = len(cams)
+        outs, saved = render_views([self.scene] * n, cams, outs=outs, save=True)
+        if dls is None:
+            dls = [torch.empty_like(o) for o in outs]
+        losses = torch.zeros(n, dtype=torch.float32, device=outs[0].device)
+        for i in range(n):
+            l1_loss(outs[i], targets[i], losses[i:i + 1], dls[i])
+        render_backward(saved, dls, self.grads)
+        saved.release()
+        self.step_count += 1
+        tex_ptr, _, dt = scene_texels(self.scene)
+        for k in ("means", "quats", "scales", "opacity", "texels"):
+            adam_update(self.master[k], self.grads[k], self.m[k], self.v[k], self.step_count, self.lr[k],
+                        shadow_ptr=tex_ptr if k == "texels" else 0,
+                        shadow_dtype={0: "f32", 1: "bf16", 2: "f16"}[dt] if k == "texels" else "f32")
+        ms = self.master
+        check(lib().ts_scene_set_geometry(self.scene.handle, _ptr(ms["means"]), _ptr(ms["quats"]),
+                                          _ptr(ms["scales"]), _ptr(ms["opacity"]), _stream(None)),
+              "ts_scene_set_geometry")
+        self.grads["spec"].zero_()
+        self.grads["irr"].zero_()
+        return losses

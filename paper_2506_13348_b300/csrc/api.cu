@@ -634,6 +634,47 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   return TS_OK;
 }
 
+ts_status ts_scene_texels(ts_scene* s, void** texels, int* T, int* dtype) {
+  if (!s) return fail(TS_ERR_ARG, "ts_scene_texels: scene is NULL");
+  if (!s->texels) return fail(TS_ERR_STATE, "ts_scene_texels: atlas not uploaded");
+  if (texels) *texels = s->texels;
+  if (T) *T = s->T;
+  if (dtype) *dtype = s->tex_dtype;
+  return TS_OK;
+}
+
+ts_status ts_scene_set_geometry(ts_scene* s, const float* means, const float* quats, const float* scales,
+                                const float* opacity, void* stream) {
+  if (!s || !means || !quats || !scales || !opacity) return fail(TS_ERR_ARG, "ts_scene_set_geometry: NULL argument");
+  if (!s->means) return fail(TS_ERR_STATE, "ts_scene_set_geometry: geometry not uploaded");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(s->device));
+  const size_t n = (size_t)s->n;
+  if (n == 0) return TS_OK;
+  launch_pad4(means, 3, s->means, (long long)n, st);
+  TS_CHECK_LAUNCH();
+  TS_CUDA(cudaMemcpyAsync(s->quats, quats, n * 16, cudaMemcpyDeviceToDevice, st));
+  TS_CUDA(cudaMemcpyAsync(s->scales, scales, n * 8, cudaMemcpyDeviceToDevice, st));
+  TS_CUDA(cudaMemcpyAsync(s->opacity, opacity, n * 4, cudaMemcpyDeviceToDevice, st));
+  return TS_OK;
+}
+
+ts_status ts_adam_update(float* param, float* grad, float* m, float* v, int64_t n, const ts_adam* hp, void* shadow,
+                         ts_dtype shadow_dtype, int zero_grad, void* stream) {
+  if (!param || !grad || !m || !v || !hp || n < 0) return fail(TS_ERR_ARG, "ts_adam_update: bad argument");
+  const uintptr_t al = reinterpret_cast<uintptr_t>(param) | reinterpret_cast<uintptr_t>(grad) |
+                       reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v);
+  if (al & 15) return fail(TS_ERR_ARG, "ts_adam_update: arrays must be 16-byte aligned");
+  if (shadow && (reinterpret_cast<uintptr_t>(shadow) & 15)) return fail(TS_ERR_ARG, "ts_adam_update: shadow alignment");
+  if (hp->step < 1 || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) || !(hp->beta2 >= 0.f && hp->beta2 < 1.f))
+    return fail(TS_ERR_ARG, "ts_adam_update: bad hyper-parameters");
+  ProfScope p((cudaStream_t)stream, "adam");
+  launch_adam(param, grad, m, v, n, hp->lr, hp->beta1, hp->beta2, hp->eps, hp->step, shadow, (int)shadow_dtype,
+              zero_grad, (cudaStream_t)stream);
+  TS_CHECK_LAUNCH();
+  return TS_OK;
+}
+
 ts_status ts_scene_info(const ts_scene* s, int64_t* n, int* T, int* dtype) {
   if (!s) return fail(TS_ERR_ARG, "ts_scene_info: scene is NULL");
   if (!s->means || !s->texels) return fail(TS_ERR_STATE, "ts_scene_info: geometry or atlas missing");

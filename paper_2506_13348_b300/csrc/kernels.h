@@ -53,6 +53,10 @@ void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* p
 // shade_bwd.cu: per-pixel shading adjoint -> gxa [pixels][3] (dL/dX 0-3, 4-7, dL/dA)
 void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cudaStream_t st);
 
+// optim.cu
+void launch_adam(float* p, float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+                 long long step, void* shadow, int shadow_dtype, int zero_grad, cudaStream_t st);
+
 // misc.cu
 void launch_pack_texels(const float* src, void* dst, long long n, int dtype, cudaStream_t st);
 void launch_pack_f16(const float* src, __half* dst, long long n, cudaStream_t st);

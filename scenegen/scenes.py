@@ -107,6 +107,23 @@ def _texels(rng, n, T):
     return tex
 
 
+def texels_torch(n: int, T: int, seed: int, device="cuda"):
+    """The texel distributions of :func:`_texels` drawn with torch's seeded
+    generator on ``device`` (for multi-GB scenes; a different random stream
+    than the numpy version)."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    tex = torch.empty(n, T, T, 8, dtype=torch.float32, device=device)
+    tex[..., 0:4].uniform_(0.0, 1.0, generator=g)
+    tex[..., 4].uniform_(0.05, 1.0, generator=g)
+    nxy = torch.empty(n, T, T, 2, dtype=torch.float32, device=device).normal_(0.0, 0.2, generator=g)
+    nrm = torch.sqrt(nxy[..., 0] ** 2 + nxy[..., 1] ** 2 + 1.0)
+    tex[..., 5] = nxy[..., 0] / nrm
+    tex[..., 6] = nxy[..., 1] / nrm
+    tex[..., 7] = 1.0 / nrm
+    return tex
+
+
 def _common_params(rng, n):
     scales = np.exp(rng.normal(LOG_SCALE_MEAN, LOG_SCALE_SD, size=(n, 2)))
     opacity = 1.0 / (1.0 + np.exp(-rng.normal(size=n)))

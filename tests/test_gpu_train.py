@@ -1,0 +1,55 @@
+"""Optimiser step and multi-view training step."""
+import numpy as np
+import pytest
+import torch
+
+import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2506_13348_b300 as P
+    return P
+
+
+@pytest.mark.parametrize("n,shadow", [(1 << 20, "bf16"), (1000003, "f16"), (4099, "f32"), (7, None)])
+def test_adam_matches_reference_formula(P, n, shadow):
+    g = torch.Generator(device="cpu").manual_seed(n)
+    p = torch.randn(n, generator=g).cuda()
+    gr = torch.randn(n, generator=g).cuda()
+    m = torch.randn(n, generator=g).cuda() * 0.1
+    v = torch.rand(n, generator=g).cuda() * 0.1
+    p0, g0, m0, v0 = p.double(), gr.double(), m.double(), v.double()
+    lr, b1, b2, eps, step = 1e-2, 0.9, 0.999, 1e-8, 7
+    sh = {"bf16": torch.bfloat16, "f16": torch.float16, "f32": torch.float32}
+    out = torch.empty(n, dtype=sh[shadow], device="cuda") if shadow else None
+    P.adam_update(p, gr, m, v, step, lr, b1, b2, eps, shadow_ptr=out.data_ptr() if shadow else 0,
+                  shadow_dtype=shadow or "f32", zero_grad=True)
+    torch.cuda.synchronize()
+    m1 = b1 * m0 + (1 - b1) * g0
+    v1 = b2 * v0 + (1 - b2) * g0 * g0
+    p1 = p0 - lr * (m1 / (1 - b1 ** step)) / ((v1 / (1 - b2 ** step)).sqrt() + eps)
+    np.testing.assert_allclose(m.double().cpu(), m1.cpu(), rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(v.double().cpu(), v1.cpu(), rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(p.double().cpu(), p1.cpu(), rtol=1e-5, atol=1e-6)
+    assert torch.count_nonzero(gr).item() == 0
+    if shadow:
+        assert torch.equal(out, p.to(sh[shadow]))  # round to nearest even of the master
+
+
+def test_training_steps_reduce_loss(P):
+    scene = sg.make_scene(1, n=4000, T=8, seed=40)
+    env = sg.make_env(4, cube_res=16, irr_res=8, lut_res=32)
+    sc = P.Scene.from_arrays(scene, env, store="bf16")
+    cams = [sg.look_at_camera(e, 96, 96) for e in [(3.0, 0.5, 0.5), (0.5, 3.0, 0.2), (-2.0, -2.0, 1.0),
+                                                   (0.3, -0.4, 3.2)]]
+    # targets: the renders of a perturbed-texture copy of the scene
+    tgt_scene = dict(scene, texels=np.clip(scene["texels"] * 0.5 + 0.25, 0, 1).astype(np.float32))
+    tsc = P.Scene.from_arrays(tgt_scene, env)
+    targets = [P.render(tsc, c)[0].clone() for c in cams]
+    tr = P.Trainer(sc, scene, store="bf16", lr_tex=2e-2)
+    losses = [tr.step(cams, targets).sum().item() for _ in range(30)]
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.8 * losses[0], losses

@@ -41,7 +41,7 @@ import numpy as np
 import torch
 
 from . import keys as K
-from .shading import shade, shading_ambiguity
+from .shading import shade, shading_ambiguity, shading_kinks
 
 F64 = torch.float64
 ALPHA_MIN = float(K.ALPHA_MIN)
@@ -183,7 +183,33 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
             amb |= valid & ((T_after / T_MIN - 1.0).abs() <= m_t)
             amb |= inside & (num.abs() <= m_f * torch.linalg.vector_norm(po, dim=-1))
             out["ambiguous"] = (amb & maybe_eval).any(1)
+            # derivative kinks of blended fragments (value continuous, slope
+            # not): bilinear cell boundaries at texel centres (incl. the
+            # clamp edges) and the 0.99 opacity clamp
+            m_k = KINK_TEX
+            kink = torch.zeros_like(blended)
+            for coord in (s * T - 0.5, t * T - 0.5):
+                fr_ = coord - torch.floor(coord)
+                near = (fr_ <= m_k) | (fr_ >= 1.0 - m_k)
+                kink |= near & (coord >= -m_k) & (coord <= T - 1 + m_k)
+            kink |= (oG - ALPHA_MAX).abs() <= m_a * ALPHA_MAX
+            # nearly edge-on splats (|n . d| <= 0.03 |d|, within ~1.7 deg):
+            # d(u,v)/d(params) grows like 1/cos^2 and an FP32 evaluation
+            # keeps only a few correct digits of those gradients
+            kink |= den.abs() <= EDGE_ON_COS * dnorm
+            out["kink"] = (kink & blended).any(1)
     return out
+
+
+# Half-widths (in texel units) of the bands around texture-lookup kinks that
+# the gradient comparison excludes: FP32 (u, v) error ~1e-6 relative maps to
+# ~4e-6 texel at T = 8.
+KINK_TEX = 1e-5
+# |cos| between view ray and splat normal below which gradients are excluded
+# (~1.7 deg from edge-on; isolated splats match to ~1e-6 up to 85 deg tilt,
+# but inside deep pixels the FP32 error of the 1/cos^2-amplified geometry
+# gradients of near-edge-on splats exceeds 1e-3 of the group maximum)
+EDGE_ON_COS = 0.03
 
 
 def tile_candidates(keylist: dict, tile: int) -> np.ndarray:
@@ -198,7 +224,13 @@ def brute_candidates(view: dict) -> np.ndarray:
     return vis[order].astype(np.int64)
 
 
-DEFAULT_MARGINS = (1e-4, 1e-4, 1e-3, 1e-6)
+# Margins of the ambiguity mask, chosen from FP32 error bounds of a renderer
+# that evaluates the same definition in single precision: (u, v) carry ~1e-6
+# relative error (band 3e-5 in u around the support edge), alpha ~1e-6
+# relative (band 1e-5), the transmittance after tens of blends ~1e-5
+# relative (band 2e-4 around the 1e-4 threshold), and the orientation test
+# d.n changes sign only for splats seen within 1e-7 of edge-on.
+DEFAULT_MARGINS = (3e-5, 1e-5, 2e-4, 1e-7)
 
 
 def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=False,
@@ -225,6 +257,7 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
     Ab = torch.zeros(H, W, dtype=F64)
     Tb = torch.ones(H, W, dtype=F64)
     amb = torch.zeros(H, W, dtype=torch.bool)
+    gamb = torch.zeros(H, W, dtype=torch.bool)
     n_eval = torch.zeros(H, W, dtype=torch.long)
     n_con = torch.zeros(H, W, dtype=torch.long)
     last = torch.full((H, W), -1, dtype=torch.long)
@@ -264,6 +297,7 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         if margins is not None:
             a2 = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
             amb[pyt, pxt] = a2
+            gamb[pyt, pxt] = a2 | fr["kink"] | shading_kinks(fr["X"].detach(), fr["A"].detach(), fr["ray_d"], envp)
 
     chunk, size = [], 0
     for tl in tile_list:
@@ -276,7 +310,7 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         size += ent
     if chunk:
         run_chunk(chunk)
-    return dict(rgba=rgba, X=Xb, A=Ab, T=Tb, ambiguous=amb, n_eval=n_eval, n_contrib=n_con,
+    return dict(rgba=rgba, X=Xb, A=Ab, T=Tb, ambiguous=amb, grad_ambiguous=gamb, n_eval=n_eval, n_contrib=n_con,
                 last=last, covered=covered, keys=kl)
 
 
@@ -298,7 +332,8 @@ def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, pa
     fr = fragments(params, cam, px, py, torch.from_numpy(cm), margins)
     col = shade(fr["X"], fr["A"], fr["ray_d"], envp)
     amb = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
-    return dict(rgba=col, X=fr["X"], A=fr["A"], T=fr["T"], ambiguous=amb, n_eval=fr["n_eval"],
+    gamb = amb | fr["kink"] | shading_kinks(fr["X"].detach(), fr["A"].detach(), fr["ray_d"], envp)
+    return dict(rgba=col, X=fr["X"], A=fr["A"], T=fr["T"], ambiguous=amb, grad_ambiguous=gamb, n_eval=fr["n_eval"],
                 n_contrib=fr["n_contrib"], last=fr["last"])
 
 

@@ -151,7 +151,59 @@ def shade(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, env: dict):
     return torch.cat([col, A[:, None]], -1).reshape(P, 4)
 
 
-def shading_ambiguity(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, m_face=1e-5,
+def normal_conditioning(X: torch.Tensor, A: torch.Tensor) -> torch.Tensor:
+    """A / |N| (at least 1): how much the blended normal's direction amplifies
+    rounding errors of its layers.  Layers whose normals partly cancel leave a
+    short N whose direction an FP32 sum knows to fewer digits, so the margins
+    of the shading's discrete decisions scale with it."""
+    nlen = torch.linalg.vector_norm(X[:, 5:8], dim=-1)
+    return torch.clamp(A / nlen.clamp_min(1e-30), min=1.0)
+
+
+def shading_kinks(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, env: dict, m_lut=2e-4, m_cube=2e-4,
+                  m_clamp=1e-5):
+    """Pixels whose shading gradient sits on a kink within FP32 error: a
+    bilinear cell boundary of the BRDF table (N.w_o, roughness), of the
+    specular cube (w_r, each sampled level) or of the irradiance cube (N),
+    a mip-level boundary, or the N.w_o / roughness clamps.  Values are
+    continuous there but derivatives jump, so FP32 and FP64 gradients may
+    legitimately differ at such pixels."""
+    with torch.no_grad():
+        ok = A >= A_MIN
+        A_s = torch.where(ok, A, torch.ones_like(A))
+        rough = X[:, 4] / A_s
+        N = X[:, 5:8]
+        cond = normal_conditioning(X, A)
+        m_lut, m_cube = m_lut * cond, m_cube * cond
+        wo = -ray_d / torch.linalg.vector_norm(ray_d, dim=-1, keepdim=True)
+        Nh = N / torch.linalg.vector_norm(N, dim=-1, keepdim=True).clamp_min(1e-300)
+        nv = (Nh * wo).sum(-1)
+        wr = 2.0 * nv[:, None] * Nh - wo
+        rc = rough.clamp(0.0, 1.0)
+        ndv = nv.clamp(NDOTV_MIN, 1.0)
+
+        def near_kink(coord, size, m):
+            fr = coord - torch.floor(coord)
+            return ((fr <= m) | (fr >= 1.0 - m)) & (coord >= -m) & (coord <= size - 1 + m)
+
+        Rl = env["lut"].shape[0]
+        k = near_kink(ndv * Rl - 0.5, Rl, m_lut) | near_kink(rc * Rl - 0.5, Rl, m_lut)
+        k |= ((nv - NDOTV_MIN).abs() <= m_clamp) | (rough.abs() <= m_clamp) | ((rough - 1.0).abs() <= m_clamp)
+        L = len(env["spec"])
+        _, s, t, _ = cube_face_coords(wr)
+        for lv in range(L):
+            R = env["spec"][lv].shape[1]
+            k |= near_kink(s * R - 0.5, R, m_cube) | near_kink(t * R - 0.5, R, m_cube)
+        if L > 1:
+            lod = rc * float(L - 1)
+            k |= near_kink(lod, L, m_cube)
+        _, s, t, _ = cube_face_coords(Nh)
+        R = env["irr"].shape[1]
+        k |= near_kink(s * R - 0.5, R, m_cube) | near_kink(t * R - 0.5, R, m_cube)
+    return k & ok
+
+
+def shading_ambiguity(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, m_face=3e-5,
                       m_small=1e-6):
     """Pixels whose shading takes a discrete decision within a hair of its
     switching point (cube face choice of w_r or N, the |N| fallback, the
@@ -164,9 +216,11 @@ def shading_ambiguity(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, m_f
         nv = (Nh * wo).sum(-1)
         wr = 2.0 * nv[:, None] * Nh - wo
 
+        m_eff = m_face * normal_conditioning(X, A)
+
         def face_tie(d):
             a = d.abs().sort(-1, descending=True).values
-            return (a[:, 0] - a[:, 1]) <= m_face * a[:, 0]
+            return (a[:, 0] - a[:, 1]) <= m_eff * a[:, 0]
 
         shaded = A >= A_MIN
         amb = shaded & (face_tie(wr) | face_tie(Nh) | (nlen < 1e-6))

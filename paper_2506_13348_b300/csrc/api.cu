@@ -475,6 +475,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
       const size_t np = (size_t)V.W * V.H;
       TS_CUDA_K(salloc((void**)&V.gbuf, np * 2 * sizeof(float4)));
       TS_CUDA_K(salloc((void**)&V.trans, np * sizeof(float)));
+      TS_CUDA_K(salloc((void**)&V.acc, np * sizeof(float)));
       TS_CUDA_K(salloc((void**)&V.last, np * sizeof(int)));
     }
   }
@@ -545,13 +546,13 @@ ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, c
     for (int l = 0; l < s->levels; ++l) g.spec[l] = grads->spec + s->spec_off[l];
   }
   Scratch tmp(st);
-  float* g_items = nullptr;
+  double* g_items = nullptr;
   float4* gxa = nullptr;
   long long n_pix = 0;
   for (int i = 0; i < vt.n_views; ++i) n_pix += (long long)vt.v[i].W * vt.v[i].H;
-  TS_CUDA(tmp.alloc((void**)&g_items, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(float)));
+  TS_CUDA(tmp.alloc((void**)&g_items, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(double)));
   TS_CUDA(tmp.alloc((void**)&gxa, (size_t)std::max(n_pix, 1ll) * 3 * sizeof(float4)));
-  TS_CUDA(cudaMemsetAsync(g_items, 0, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(float), st));
+  TS_CUDA(cudaMemsetAsync(g_items, 0, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(double), st));
   {
     ProfScope p(st, "shade_bwd");
     launch_shade_bwd(vt, gxa, g, st);

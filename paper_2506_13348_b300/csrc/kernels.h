@@ -22,7 +22,7 @@ int set_error(int code, const std::string& msg);
 // preprocess.cu
 void launch_preprocess(const ViewTable& vt, Record* rec, uint32_t* counts, uint64_t* depth_keys,
                        uint32_t* item_ids, int4* rects, cudaStream_t st);
-void launch_preprocess_bwd(const ViewTable& vt, const float* g_items, const GradTable& g, cudaStream_t st);
+void launch_preprocess_bwd(const ViewTable& vt, const double* g_items, const GradTable& g, cudaStream_t st);
 
 // sort.cu
 size_t scan_temp_bytes(int n);
@@ -48,7 +48,7 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats,
                        cudaStream_t st);
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, const float4* gxa, float* g_items,
+                       const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
                        const GradTable& g, cudaStream_t st);
 // shade_bwd.cu: per-pixel shading adjoint -> gxa [pixels][3] (dL/dX 0-3, 4-7, dL/dA)
 void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cudaStream_t st);

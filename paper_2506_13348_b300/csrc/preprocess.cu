@@ -164,58 +164,69 @@ void launch_preprocess(const ViewTable& vt, Record* rec, uint32_t* counts, uint6
 // ---------------------------------------------------------------------------
 // Adjoint.  g_items[item][20]: 0-2 d/dh_u, 3-5 d/dh_v, 6-8 d/dh_w (centred
 // pixel rows), 9 d/do, 10-12 d/dt_u, 13-15 d/dt_v, 16-18 d/dn_f (world).
-__global__ void __launch_bounds__(256) k_preprocess_bwd(ViewTable vt, const float* __restrict__ g_items,
+// The per-splat sums arrive in float64 (accumulated across warps without
+// FP32 cancellation); the chain itself runs in float32 (a float64 chain was
+// measured: no accuracy change, 10x the time on this part).
+__global__ void __launch_bounds__(256) k_preprocess_bwd(ViewTable vt, const double* __restrict__ g_items,
                                                          GradTable g) {
+  using R_t = float;
   const int item = blockIdx.x * blockDim.x + threadIdx.x;
   if (item >= vt.n_items) return;
   const int v = find_view_item(vt, item);
   const ViewDesc& V = vt.v[v];
   const int k = item - V.item_off;
   if (k >= V.n_splats) return;
-  const float4* gp4 = reinterpret_cast<const float4*>(g_items + (size_t)item * 20);
-  float gi[20];
+  const double2* gp2 = reinterpret_cast<const double2*>(g_items + (size_t)item * 20);
+  R_t gi[20];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    float4 a = gp4[i];
-    gi[4 * i] = a.x; gi[4 * i + 1] = a.y; gi[4 * i + 2] = a.z; gi[4 * i + 3] = a.w;
+  for (int i = 0; i < 10; ++i) {
+    const double2 a = gp2[i];
+    gi[2 * i] = a.x;
+    gi[2 * i + 1] = a.y;
   }
   bool any = false;
 #pragma unroll
-  for (int i = 0; i < 19; ++i) any |= (gi[i] != 0.f);
+  for (int i = 0; i < 19; ++i) any |= (gi[i] != 0.0);
   if (!any) return;
 
   const float4 p4 = V.means[k];
   const float4 q = V.quats[k];
   const float2 s = V.scales[k];
-  const float p[3] = {p4.x, p4.y, p4.z};
-  float tu[3], tv[3], n[3];
-  rot_cols_spec(q, tu, tv, n);
-  const float* R = V.R;
-  float pc[3], tuc[3], tvc[3], nc[3];
+  const R_t p[3] = {p4.x, p4.y, p4.z};
+  const R_t qn = sqrt((R_t)q.x * q.x + (R_t)q.y * q.y + (R_t)q.z * q.z + (R_t)q.w * q.w);
+  const R_t iq = R_t(1) / qn;
+  const R_t w = q.x * iq, x = q.y * iq, y = q.z * iq, z = q.w * iq;
+  const R_t tu[3] = {1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)};
+  const R_t tv[3] = {2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)};
+  const R_t n[3] = {2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y)};
+  R_t Rm[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Rm[i] = V.R[i];
+  R_t pc[3], tuc[3], tvc[3], nc[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    pc[r] = R[3 * r] * p[0] + R[3 * r + 1] * p[1] + R[3 * r + 2] * p[2] + V.t[r];
-    tuc[r] = R[3 * r] * tu[0] + R[3 * r + 1] * tu[1] + R[3 * r + 2] * tu[2];
-    tvc[r] = R[3 * r] * tv[0] + R[3 * r + 1] * tv[1] + R[3 * r + 2] * tv[2];
-    nc[r] = R[3 * r] * n[0] + R[3 * r + 1] * n[1] + R[3 * r + 2] * n[2];
+    pc[r] = Rm[3 * r] * p[0] + Rm[3 * r + 1] * p[1] + Rm[3 * r + 2] * p[2] + (R_t)V.t[r];
+    tuc[r] = Rm[3 * r] * tu[0] + Rm[3 * r + 1] * tu[1] + Rm[3 * r + 2] * tu[2];
+    tvc[r] = Rm[3 * r] * tv[0] + Rm[3 * r + 1] * tv[1] + Rm[3 * r + 2] * tv[2];
+    nc[r] = Rm[3 * r] * n[0] + Rm[3 * r + 1] * n[1] + Rm[3 * r + 2] * n[2];
   }
-  const float D = pc[0] * nc[0] + pc[1] * nc[1] + pc[2] * nc[2];
-  const float Pu = pc[0] * tuc[0] + pc[1] * tuc[1] + pc[2] * tuc[2];
-  const float Pv = pc[0] * tvc[0] + pc[1] * tvc[1] + pc[2] * tvc[2];
-  const float isu = 1.f / s.x, isv = 1.f / s.y;
-  const float ifx = 1.f / V.fx, ify = 1.f / V.fy;
+  const R_t D = pc[0] * nc[0] + pc[1] * nc[1] + pc[2] * nc[2];
+  const R_t Pu = pc[0] * tuc[0] + pc[1] * tuc[1] + pc[2] * tuc[2];
+  const R_t Pv = pc[0] * tvc[0] + pc[1] * tvc[1] + pc[2] * tvc[2];
+  const R_t isu = R_t(1) / (R_t)s.x, isv = R_t(1) / (R_t)s.y;
+  const R_t ifx = R_t(1) / (R_t)V.fx, ify = R_t(1) / (R_t)V.fy;
   // centred pixel rows -> d-space rows
-  const float ghu[3] = {gi[0] * ifx, gi[1] * ify, gi[2]};
-  const float ghv[3] = {gi[3] * ifx, gi[4] * ify, gi[5]};
-  const float ghw[3] = {gi[6] * ifx, gi[7] * ify, gi[8]};
-  float gpc[3] = {0.f, 0.f, 0.f}, gtuc[3] = {0.f, 0.f, 0.f}, gtvc[3] = {0.f, 0.f, 0.f};
-  float gnc[3] = {ghw[0], ghw[1], ghw[2]};
-  // h_u = (D t_u - P_u n)/s_u
-  float gD = 0.f, gPu = 0.f, gPv = 0.f, gsu = 0.f, gsv = 0.f;
+  const R_t ghu[3] = {gi[0] * ifx, gi[1] * ify, gi[2]};
+  const R_t ghv[3] = {gi[3] * ifx, gi[4] * ify, gi[5]};
+  const R_t ghw[3] = {gi[6] * ifx, gi[7] * ify, gi[8]};
+  R_t gpc[3] = {0, 0, 0}, gtuc[3] = {0, 0, 0}, gtvc[3] = {0, 0, 0};
+  R_t gnc[3] = {ghw[0], ghw[1], ghw[2]};
+  // h_u = (D t_u - P_u n)/s_u, h_v likewise, h_w = n
+  R_t gD = 0, gPu = 0, gPv = 0, gsu = 0, gsv = 0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const float hu = (D * tuc[i] - Pu * nc[i]) * isu;
-    const float hv = (D * tvc[i] - Pv * nc[i]) * isv;
+    const R_t hu = (D * tuc[i] - Pu * nc[i]) * isu;
+    const R_t hv = (D * tvc[i] - Pv * nc[i]) * isv;
     gD += (ghu[i] * tuc[i]) * isu + (ghv[i] * tvc[i]) * isv;
     gtuc[i] += D * ghu[i] * isu;
     gtvc[i] += D * ghv[i] * isv;
@@ -233,45 +244,43 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(ViewTable vt, const floa
     gtvc[i] += gPv * pc[i];
   }
   // camera -> world (R^T), plus the normal-mapping frame gradients
-  const float sg = (D > 0.f) ? -1.f : 1.f;
-  float gpw[3], gtu[3], gtv[3], gn[3];
+  const R_t sg = (D > 0) ? R_t(-1) : R_t(1);
+  R_t gpw[3], gtu[3], gtv[3], gn[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    gpw[i] = R[i] * gpc[0] + R[3 + i] * gpc[1] + R[6 + i] * gpc[2];
-    gtu[i] = R[i] * gtuc[0] + R[3 + i] * gtuc[1] + R[6 + i] * gtuc[2] + gi[10 + i];
-    gtv[i] = R[i] * gtvc[0] + R[3 + i] * gtvc[1] + R[6 + i] * gtvc[2] + gi[13 + i];
-    gn[i] = R[i] * gnc[0] + R[3 + i] * gnc[1] + R[6 + i] * gnc[2] + sg * gi[16 + i];
+    gpw[i] = Rm[i] * gpc[0] + Rm[3 + i] * gpc[1] + Rm[6 + i] * gpc[2];
+    gtu[i] = Rm[i] * gtuc[0] + Rm[3 + i] * gtuc[1] + Rm[6 + i] * gtuc[2] + gi[10 + i];
+    gtv[i] = Rm[i] * gtvc[0] + Rm[3 + i] * gtvc[1] + Rm[6 + i] * gtvc[2] + gi[13 + i];
+    gn[i] = Rm[i] * gnc[0] + Rm[3 + i] * gnc[1] + Rm[6 + i] * gnc[2] + sg * gi[16 + i];
   }
   // rotation matrix of the unit quaternion -> quaternion
-  const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-  const float iq = 1.f / qn;
-  const float w = q.x * iq, x = q.y * iq, y = q.z * iq, z = q.w * iq;
-  const float gw = 2.f * (z * gtu[1] - y * gtu[2] - z * gtv[0] + x * gtv[2] + y * gn[0] - x * gn[1]);
-  const float gx = 2.f * (y * gtu[1] + z * gtu[2] + y * gtv[0] - 2.f * x * gtv[1] + w * gtv[2] + z * gn[0] -
-                          w * gn[1] - 2.f * x * gn[2]);
-  const float gy = 2.f * (-2.f * y * gtu[0] + x * gtu[1] - w * gtu[2] + x * gtv[0] + z * gtv[2] + w * gn[0] +
-                          z * gn[1] - 2.f * y * gn[2]);
-  const float gz = 2.f * (-2.f * z * gtu[0] + w * gtu[1] + x * gtu[2] - w * gtv[0] - 2.f * z * gtv[1] +
-                          y * gtv[2] + x * gn[0] + y * gn[1]);
-  const float dp = w * gw + x * gx + y * gy + z * gz;
+  const R_t gw = 2 * (z * gtu[1] - y * gtu[2] - z * gtv[0] + x * gtv[2] + y * gn[0] - x * gn[1]);
+  const R_t gx = 2 * (y * gtu[1] + z * gtu[2] + y * gtv[0] - 2 * x * gtv[1] + w * gtv[2] + z * gn[0] - w * gn[1] -
+                      2 * x * gn[2]);
+  const R_t gy = 2 * (-2 * y * gtu[0] + x * gtu[1] - w * gtu[2] + x * gtv[0] + z * gtv[2] + w * gn[0] + z * gn[1] -
+                      2 * y * gn[2]);
+  const R_t gz = 2 * (-2 * z * gtu[0] + w * gtu[1] + x * gtu[2] - w * gtv[0] - 2 * z * gtv[1] + y * gtv[2] +
+                      x * gn[0] + y * gn[1]);
+  const R_t dp = w * gw + x * gx + y * gy + z * gz;
   if (g.quats) {
     float* gq = g.quats + (size_t)k * 4;
-    red_add_v4(gq, (gw - w * dp) * iq, (gx - x * dp) * iq, (gy - y * dp) * iq, (gz - z * dp) * iq);
+    red_add_v4(gq, (float)((gw - w * dp) * iq), (float)((gx - x * dp) * iq), (float)((gy - y * dp) * iq),
+               (float)((gz - z * dp) * iq));
   }
   if (g.means) {
     float* gm = g.means + (size_t)k * 3;
-    red_add(gm, gpw[0]);
-    red_add(gm + 1, gpw[1]);
-    red_add(gm + 2, gpw[2]);
+    red_add(gm, (float)gpw[0]);
+    red_add(gm + 1, (float)gpw[1]);
+    red_add(gm + 2, (float)gpw[2]);
   }
   if (g.scales) {
-    red_add(g.scales + (size_t)k * 2, gsu);
-    red_add(g.scales + (size_t)k * 2 + 1, gsv);
+    red_add(g.scales + (size_t)k * 2, (float)gsu);
+    red_add(g.scales + (size_t)k * 2 + 1, (float)gsv);
   }
-  if (g.opacity) red_add(g.opacity + k, gi[9]);
+  if (g.opacity) red_add(g.opacity + k, (float)gi[9]);
 }
 
-void launch_preprocess_bwd(const ViewTable& vt, const float* g_items, const GradTable& g, cudaStream_t st) {
+void launch_preprocess_bwd(const ViewTable& vt, const double* g_items, const GradTable& g, cudaStream_t st) {
   if (vt.n_items == 0) return;
   k_preprocess_bwd<<<(vt.n_items + 255) / 256, 256, 0, st>>>(vt, g_items, g);
   note_launches(1);

@@ -25,7 +25,7 @@ template <int DT>
 __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
                                                         const uint32_t* __restrict__ pair_items,
                                                         const uint2* __restrict__ ranges,
-                                                        const float4* __restrict__ gxa, float* __restrict__ g_items,
+                                                        const float4* __restrict__ gxa, double* __restrict__ g_items,
                                                         GradTable g) {
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ __align__(16) float s_gi[8][19][36];  // record gradients, value-major, per warp
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         a[0].x += a[2].x; a[0].y += a[2].y; a[0].z += a[2].z; a[0].w += a[2].w;
         a[1].x += a[3].x; a[1].y += a[3].y; a[1].z += a[3].z; a[1].w += a[3].w;
         const float s = (a[0].x + a[1].x) + (a[0].y + a[1].y) + (a[0].z + a[1].z) + (a[0].w + a[1].w);
-        if (s != 0.f) red_add(g_items + (size_t)item * 20 + lane, s);
+        if (s != 0.f) atomicAdd(g_items + (size_t)item * 20 + lane, (double)s);
       }
       __syncwarp();
       // texel gradients: pixels of a 2x2 quad that use the same bilinear cell
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
 }
 
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, const float4* gxa, float* g_items,
+                       const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
                        const GradTable& g, cudaStream_t st) {
   dim3 grid(vt.n_tiles), block(256);
   if (tex_dtype == DT_F32)

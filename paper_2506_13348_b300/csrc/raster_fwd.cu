@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
   const float by0 = (float)(py - (lane >> 3)) + 0.5f - V.cy, by1 = by0 + 3.f;
 
   float Tr = 1.f;
+  float Acc = 0.f;  // coverage as the blended sum (Eq. 3 with a = 1): exact where 1 - T cancels
   float X[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) X[c] = 0.f;
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
         const float w = f.alpha * Tr;
 #pragma unroll
         for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
+        Acc += w;
         Tr = Tr * (1.f - f.alpha);
         last = (int)(base + c0 + t);
         if (STATS) ++n_blend;
@@ -106,13 +108,14 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
 
   if (inside) {
     const int pix = py * V.W + px;
-    const float A = 1.f - Tr;
+    const float A = Acc;
     float3 d = world_ray(V, xp, yp);
     V.rgba[pix] = shade_pixel(V.env, X, A, d, nullptr);
     if (SAVE) {
       V.gbuf[2 * pix] = make_float4(X[0], X[1], X[2], X[3]);
       V.gbuf[2 * pix + 1] = make_float4(X[4], X[5], X[6], X[7]);
       V.trans[pix] = Tr;
+      V.acc[pix] = Acc;
       V.last[pix] = last;
     }
   }

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(SB_THREADS) k_shade_bwd(ViewTable vt, long lon
     const float xp = (float)px + 0.5f - V.cx, yp = (float)py + 0.5f - V.cy;
     const float4 a = V.gbuf[2 * pix], b = V.gbuf[2 * pix + 1];
     const float X[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    const float A = 1.f - V.trans[pix];
+    const float A = V.acc[pix];
     const float3 d = world_ray(V, xp, yp);
     const float4 dl = V.dl[pix];
     float gX[8], gA;

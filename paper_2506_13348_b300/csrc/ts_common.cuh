@@ -66,6 +66,7 @@ struct ViewDesc {
   float4* rgba;   // [H][W]
   float4* gbuf;   // [H][W][2] (X of Eq. 9, 8 channels)
   float* trans;   // [H][W]
+  float* acc;     // [H][W] blended coverage A = sum alpha_i T_i (not 1 - T: no cancellation)
   int* last;      // [H][W]
   const float4* dl;  // backward input dL/drgba [H][W]
 };

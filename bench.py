@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--large-only", action="store_true")
     ap.add_argument("--large-steps", type=int, default=10)
     ap.add_argument("--large-warmup", type=int, default=3)
+    ap.add_argument("--no-precision", action="store_true", help="skip the reduced-precision atlas measurement")
+    ap.add_argument("--precision-only", action="store_true")
+    ap.add_argument("--precision-samples", type=int, default=64)
     return ap.parse_args()
 
 
@@ -298,6 +301,8 @@ def run_ours(args):
         line["serving"] = run_serving(args, local)
     if rank == 0 and not args.no_large:
         line["large_scene"] = run_large_scene(args, local)
+    if rank == 0 and not args.no_precision:
+        line["precision"] = run_precision(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, thr, px = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -392,6 +397,72 @@ def run_serving(args, device):
             "served_saturated_mean_batch": s_sat["mean_batch"],
             "plain_fp32_one_at_a_time": {k: p[k] for k in keep},
             "served_bf16_batched": {k: s[k] for k in keep}}
+
+
+def run_precision(args, device):
+    """Reduced-precision atlas: 500k sphere splats, 16x16 texels x 8
+    channels, 1920x1080, 6-level 128 FP16 cube.  Per stored dtype (f32,
+    bf16, f16): forward Mpix/s over 10 views and the storage error of the
+    image against the FP64 oracle fed the float32 texels (sampled pixels of
+    2 views; the oracle uses the same FP16 cube, so only the atlas differs)."""
+    import numpy as np
+    import torch
+
+    import paper_2506_13348_b300 as P
+    import scenegen as sg
+    from oracle import keys as K
+    from oracle import render as R
+
+    dev = torch.device("cuda", device)
+    geo = sg.make_scene(2, with_texels=False)
+    tex = sg.scenes.texels_torch(len(geo["opacity"]), 16, seed=2, device="cpu")
+    env = sg.make_env(2, cube_res=128, levels=6, irr_res=16, lut_res=128)
+    env16 = dict(env, spec=[m.astype(np.float16).astype(np.float32) for m in env["spec"]],
+                 irr=env["irr"].astype(np.float16).astype(np.float32))
+    W, H = 1920, 1080
+    cams = sg.fibonacci_cameras(10, 4.0, W, H)
+    scene64 = dict(geo, texels=tex.numpy(), T=16)
+    rng = np.random.default_rng(22)
+    samples = []
+    for ci in (0, 5):
+        px, py = rng.integers(0, W, args.precision_samples), rng.integers(0, H, args.precision_samples)
+        kl = K.build_keys(scene64, cams[ci])
+        ref = R.render_pixels(scene64, cams[ci], env16, px, py, keylist=kl)
+        samples.append((ci, px, py, ref["rgba"].detach().numpy(), ref["ambiguous"].numpy()))
+    out = {"workload": "cfg2: 500k splats, 16x16 texels x 8 ch, 1920x1080, 6-level 128 FP16 cube, 10 views",
+           "error_samples": f"{args.precision_samples} random pixels of views 0 and 5 vs the FP64 oracle with FP32 texels"}
+    img = torch.empty(H, W, 4, device=dev)
+    for store in ("f32", "bf16", "f16"):
+        sc = P.Scene(device)
+        sc.upload_gaussians(geo["means"], geo["quats"], geo["scales"], geo["opacity"])
+        sc.upload_atlas(tex, store)
+        sc.upload_envmap(env, "f16")
+        errs = []
+        for ci, px, py, ref, amb in samples:
+            P.render(sc, cams[ci], out=img)
+            torch.cuda.synchronize()
+            g = img.cpu().numpy()[py, px].astype(np.float64)
+            e = np.abs(g - ref)[~amb][:, :3]
+            errs.append(e)
+        e = np.concatenate(errs)
+        for i in range(2):
+            P.render(sc, cams[i], out=img)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(len(cams)):
+            P.render(sc, cams[i], out=img)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / len(cams)
+        mse = float((e ** 2).mean())
+        out[store] = {"fwd_ms_per_view": ms, "fwd_mpix_per_s": W * H / 1e6 / (ms / 1e3),
+                      "max_abs_err": float(e.max()), "mean_abs_err": float(e.mean()),
+                      "psnr_db": float(10 * np.log10(1.0 / mse)) if mse > 0 else None}
+        sc.close()
+    del tex
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_large_scene(args, device):
@@ -513,7 +584,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.serve_only or args.large_only:
+    if args.serve_only or args.large_only or args.precision_only:
         import torch
         torch.cuda.set_device(dist_env()[2])
         res = {}
@@ -521,6 +592,8 @@ def main():
             res["serving"] = run_serving(args, dist_env()[2])
         if args.large_only:
             res["large_scene"] = run_large_scene(args, dist_env()[2])
+        if args.precision_only:
+            res["precision"] = run_precision(args, dist_env()[2])
         print(json.dumps(res))
         return 0
     return run_ours(args)

@@ -12,8 +12,9 @@
 //   * the 19 record gradients of the fragment are transposed through shared
 //     memory and lane L < 19 sums value L over the warp (independent loads,
 //     tree add), adding it once per warp;
-//   * texel gradients go out as 16-byte vector reductions per lane (L2
-//     absorbs them; grouping lanes by bilinear cell first measured slower).
+//   * texel gradients are summed per bilinear cell over the warp (a
+//     reduce-scatter through shuffles) before one reduction per cell; lanes
+//     whose cell few others share add their own values directly.
 #include "raster.cuh"
 #include "shading.cuh"
 #include "kernels.h"
@@ -201,50 +202,71 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         if (s != 0.f) atomicAdd(g_items + (size_t)item * 20 + lane, (double)s);
       }
       __syncwarp();
-      // texel gradients: pixels of a 2x2 quad that use the same bilinear cell
-      // (the four texels) are summed first -- horizontal pairs (lane ^ 1),
-      // then vertical pairs (lane ^ 8) -- and one lane per merged group
-      // issues the 16-byte vector reductions (L2 atomic throughput bounds this
-      // part, so fewer, fuller reductions pay for the shuffles)
+      // texel gradients: lanes are grouped by bilinear cell (the four texels
+      // they interpolate).  A lane whose cell at most kDirect live lanes share
+      // adds its own four corners (16-byte vector reductions); each larger
+      // group is summed over the warp by one halving reduce-scatter of its
+      // 32 values (4 corners x 8 channels, 31 shuffles), after which lane L
+      // holds corner L >> 3, channel L & 7 and all 32 lanes issue one
+      // reduction covering the cell's four texels.  A warp's live lanes
+      // usually share one to three cells.
       if (g.texels) {
-        const unsigned key = ok ? (unsigned)((ts_.ja * T + ts_.ia) | ((ts_.jb * T + ts_.ib) << 10)) : FULL;
-        // merge decisions (identical for the four corners), butterfly over
-        // lane bits 0 (x) and 3 (y): at each level two lanes that still hold
-        // values and share the cell combine into the lower lane.  (Merging
-        // 4x4 pixel groups as well measured slower: the extra shuffles cost
-        // more than the reductions they save.)  Every lane takes part in
-        // every shuffle.
-        constexpr int NLVL = 2;
-        const int offs[NLVL] = {1, 8};
-        bool mrg[NLVL];
-        bool issue = ok;
-#pragma unroll
-        for (int l = 0; l < NLVL; ++l) {
-          const unsigned kl = issue ? key : FULL - 1u;
-          const unsigned pk = __shfl_xor_sync(FULL, kl, offs[l]);
-          mrg[l] = issue && pk == kl;  // same live key implies the partner is live too
-          if (mrg[l] && (lane & offs[l])) issue = false;
-        }
+        constexpr int kDirect = 8;
+        const unsigned key = ok ? (unsigned)(ts_.ia | (ts_.ib << 8) | (ts_.ja << 16) | (ts_.jb << 24)) : FULL;
         float* gtex = g.texels + splat * (long long)T * T * 8;
+        if (!ok) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float vt[8];
+          for (int c = 0; c < 8; ++c) t8[c] = 0.f;
+        }
+        const unsigned live = __ballot_sync(FULL, ok);
+        const unsigned same = __match_any_sync(FULL, key) & live;
+        const bool direct = ok && __popc(same) <= kDirect;
+        if (__any_sync(FULL, direct) && direct) {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            float x = ok ? w4[k] * t8[c] : 0.f;
-#pragma unroll
-            for (int l = 0; l < NLVL; ++l) {
-              const float p = __shfl_xor_sync(FULL, x, offs[l]);
-              if (mrg[l] && !(lane & offs[l])) x += p;
-            }
-            vt[c] = x;
-          }
-          if (issue) {
+          for (int k = 0; k < 4; ++k) {
             const int jj = (k & 2) ? ts_.jb : ts_.ja, ii = (k & 1) ? ts_.ib : ts_.ia;
             float* p = gtex + (jj * T + ii) * 8;
-            red_add_v4(p, vt[0], vt[1], vt[2], vt[3]);
-            red_add_v4(p + 4, vt[4], vt[5], vt[6], vt[7]);
+            red_add_v4(p, w4[k] * t8[0], w4[k] * t8[1], w4[k] * t8[2], w4[k] * t8[3]);
+            red_add_v4(p + 4, w4[k] * t8[4], w4[k] * t8[5], w4[k] * t8[6], w4[k] * t8[7]);
           }
+        }
+        const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2, u1 = lane & 1;
+        unsigned pend = __ballot_sync(FULL, ok && !direct);
+        while (pend) {  // warp-uniform
+          const unsigned lk = __shfl_sync(FULL, key, __ffs(pend) - 1);
+          const bool mem = ((pend >> lane) & 1u) && key == lk;
+          pend &= ~__ballot_sync(FULL, mem);
+          const float m0 = mem ? w4[0] : 0.f, m1 = mem ? w4[1] : 0.f;
+          const float m2 = mem ? w4[2] : 0.f, m3 = mem ? w4[3] : 0.f;
+          // lane bit 4 <-> corner bit 1 (row jb), bit 3 <-> corner bit 0
+          // (column ib), bits 2..0 <-> channel; each step keeps the half
+          // selected by the lane's bit and adds the partner's copy of it
+          const float wk0 = u16 ? m2 : m0, wk1 = u16 ? m3 : m1, ws0 = u16 ? m0 : m2, ws1 = u16 ? m1 : m3;
+          float a[16];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            a[c] = fmaf(wk0, t8[c], __shfl_xor_sync(FULL, ws0 * t8[c], 16));
+            a[8 + c] = fmaf(wk1, t8[c], __shfl_xor_sync(FULL, ws1 * t8[c], 16));
+          }
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float snd = u8 ? a[c] : a[8 + c], kp = u8 ? a[8 + c] : a[c];
+            a[c] = kp + __shfl_xor_sync(FULL, snd, 8);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float snd = u4 ? a[c] : a[4 + c], kp = u4 ? a[4 + c] : a[c];
+            a[c] = kp + __shfl_xor_sync(FULL, snd, 4);
+          }
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const float snd = u2 ? a[c] : a[2 + c], kp = u2 ? a[2 + c] : a[c];
+            a[c] = kp + __shfl_xor_sync(FULL, snd, 2);
+          }
+          a[0] = (u1 ? a[1] : a[0]) + __shfl_xor_sync(FULL, u1 ? a[0] : a[1], 1);
+          const int ii = (int)((lk >> (u8 ? 8 : 0)) & 0xffu);
+          const int jj = (int)((lk >> (u16 ? 24 : 16)) & 0xffu);
+          red_add(gtex + (jj * T + ii) * 8 + (lane & 7), a[0]);
         }
       }
     }

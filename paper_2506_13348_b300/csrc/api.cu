@@ -550,9 +550,9 @@ ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, c
   float4* gxa = nullptr;
   long long n_pix = 0;
   for (int i = 0; i < vt.n_views; ++i) n_pix += (long long)vt.v[i].W * vt.v[i].H;
-  TS_CUDA(tmp.alloc((void**)&g_items, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(double)));
+  TS_CUDA(tmp.alloc((void**)&g_items, (size_t)std::max(vt.n_items, 1) * kRecGradStride * sizeof(double)));
   TS_CUDA(tmp.alloc((void**)&gxa, (size_t)std::max(n_pix, 1ll) * 3 * sizeof(float4)));
-  TS_CUDA(cudaMemsetAsync(g_items, 0, (size_t)std::max(vt.n_items, 1) * 20 * sizeof(double), st));
+  TS_CUDA(cudaMemsetAsync(g_items, 0, (size_t)std::max(vt.n_items, 1) * kRecGradStride * sizeof(double), st));
   {
     ProfScope p(st, "shade_bwd");
     launch_shade_bwd(vt, gxa, g, st);

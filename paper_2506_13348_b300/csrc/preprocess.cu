@@ -162,8 +162,9 @@ void launch_preprocess(const ViewTable& vt, Record* rec, uint32_t* counts, uint6
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint.  g_items[item][20]: 0-2 d/dh_u, 3-5 d/dh_v, 6-8 d/dh_w (centred
-// pixel rows), 9 d/do, 10-12 d/dt_u, 13-15 d/dt_v, 16-18 d/dn_f (world).
+// Adjoint.  g_items[item][14]: 0-2 d/dh_u, 3-5 d/dh_v, 6-8 d/dh_w (centred
+// pixel rows), 9 d/do, 10-12 the torque tau of the normal-mapping frame
+// (world): a rotation by a small angle vector w changes the loss by tau . w.
 // The per-splat sums arrive in float64 (accumulated across warps without
 // FP32 cancellation); the chain itself runs in float32 (a float64 chain was
 // measured: no accuracy change, 10x the time on this part).
@@ -176,17 +177,17 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(ViewTable vt, const doub
   const ViewDesc& V = vt.v[v];
   const int k = item - V.item_off;
   if (k >= V.n_splats) return;
-  const double2* gp2 = reinterpret_cast<const double2*>(g_items + (size_t)item * 20);
-  R_t gi[20];
+  const double2* gp2 = reinterpret_cast<const double2*>(g_items + (size_t)item * kRecGradStride);
+  R_t gi[kRecGradStride];
 #pragma unroll
-  for (int i = 0; i < 10; ++i) {
+  for (int i = 0; i < kRecGradStride / 2; ++i) {
     const double2 a = gp2[i];
     gi[2 * i] = a.x;
     gi[2 * i + 1] = a.y;
   }
   bool any = false;
 #pragma unroll
-  for (int i = 0; i < 19; ++i) any |= (gi[i] != 0.0);
+  for (int i = 0; i < kRecGrads; ++i) any |= (gi[i] != 0.0);
   if (!any) return;
 
   const float4 p4 = V.means[k];
@@ -243,15 +244,24 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(ViewTable vt, const doub
     gtuc[i] += gPu * pc[i];
     gtvc[i] += gPv * pc[i];
   }
-  // camera -> world (R^T), plus the normal-mapping frame gradients
-  const R_t sg = (D > 0) ? R_t(-1) : R_t(1);
+  // camera -> world (R^T), plus the normal-mapping frame: column gradients
+  // g_f = (tau x f) / 2 for the orthonormal columns f = t_u, t_v, n give
+  // sum_f f x g_f = tau, the same rotation gradient as the full 3x3 frame
+  // gradient (the camera-facing flip of n cancels: n_f = -n, g_n = -g_nf)
+  const R_t ta[3] = {gi[10], gi[11], gi[12]};
+  const R_t htu[3] = {R_t(0.5) * (ta[1] * tu[2] - ta[2] * tu[1]), R_t(0.5) * (ta[2] * tu[0] - ta[0] * tu[2]),
+                      R_t(0.5) * (ta[0] * tu[1] - ta[1] * tu[0])};
+  const R_t htv[3] = {R_t(0.5) * (ta[1] * tv[2] - ta[2] * tv[1]), R_t(0.5) * (ta[2] * tv[0] - ta[0] * tv[2]),
+                      R_t(0.5) * (ta[0] * tv[1] - ta[1] * tv[0])};
+  const R_t hn[3] = {R_t(0.5) * (ta[1] * n[2] - ta[2] * n[1]), R_t(0.5) * (ta[2] * n[0] - ta[0] * n[2]),
+                     R_t(0.5) * (ta[0] * n[1] - ta[1] * n[0])};
   R_t gpw[3], gtu[3], gtv[3], gn[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     gpw[i] = Rm[i] * gpc[0] + Rm[3 + i] * gpc[1] + Rm[6 + i] * gpc[2];
-    gtu[i] = Rm[i] * gtuc[0] + Rm[3 + i] * gtuc[1] + Rm[6 + i] * gtuc[2] + gi[10 + i];
-    gtv[i] = Rm[i] * gtvc[0] + Rm[3 + i] * gtvc[1] + Rm[6 + i] * gtvc[2] + gi[13 + i];
-    gn[i] = Rm[i] * gnc[0] + Rm[3 + i] * gnc[1] + Rm[6 + i] * gnc[2] + sg * gi[16 + i];
+    gtu[i] = Rm[i] * gtuc[0] + Rm[3 + i] * gtuc[1] + Rm[6 + i] * gtuc[2] + htu[i];
+    gtv[i] = Rm[i] * gtvc[0] + Rm[3 + i] * gtvc[1] + Rm[6 + i] * gtvc[2] + htv[i];
+    gn[i] = Rm[i] * gnc[0] + Rm[3 + i] * gnc[1] + Rm[6 + i] * gnc[2] + hn[i];
   }
   // rotation matrix of the unit quaternion -> quaternion
   const R_t gw = 2 * (z * gtu[1] - y * gtu[2] - z * gtv[0] + x * gtv[2] + y * gn[0] - x * gn[1]);

@@ -9,8 +9,8 @@
 // stored); the transmittance in front of it is recovered by division
 // (alpha <= 0.99) and the colour behind it by the usual recurrence.
 // Reductions (all lanes of a warp work on the same splat at a time):
-//   * the 19 record gradients of the fragment are transposed through shared
-//     memory and lane L < 19 sums value L over the warp (independent loads,
+//   * the 13 record gradients of the fragment are transposed through shared
+//     memory and lane L < 13 sums value L over the warp (independent loads,
 //     tree add), adding it once per warp;
 //   * texel gradients are summed per bilinear cell over the warp (a
 //     reduce-scatter through shuffles) before one reduction per cell; lanes
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
                                                         const float4* __restrict__ gxa, double* __restrict__ g_items,
                                                         GradTable g) {
   constexpr unsigned FULL = 0xffffffffu;
-  __shared__ __align__(16) float s_gi[8][19][36];  // record gradients, value-major, per warp
+  __shared__ __align__(16) float s_gi[8][kRecGrads][36];  // record gradients, value-major, per warp
   __shared__ float4 s_rec[8][32][3];               // first 48 bytes of the records of a chunk
   __shared__ uint32_t s_item[8][32];
   const int warp = threadIdx.x >> 5;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
       float t8[8], w4[4] = {0.f, 0.f, 0.f, 0.f};
       TexSample ts_;
       ts_.ia = ts_.ib = ts_.ja = ts_.jb = 0;
-      float gi[19];
+      float gi[kRecGrads];
       if (ok) {
         ts_ = tex_setup(f.u, f.v, T);
         const float om = 1.f - f.alpha;
@@ -172,22 +172,30 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         gi[3] = gvn * xp; gi[4] = gvn * yp; gi[5] = gvn;
         gi[6] = gden * xp; gi[7] = gden * yp; gi[8] = gden;
         gi[9] = go;
-        gi[10] = nt0 * gn0; gi[11] = nt0 * gn1; gi[12] = nt0 * gn2;
-        gi[13] = nt1 * gn0; gi[14] = nt1 * gn1; gi[15] = nt1 * gn2;
-        gi[16] = nt2 * gn0; gi[17] = nt2 * gn1; gi[18] = nt2 * gn2;
+        // normal-mapping frame [t_u t_v n_f]: its gradient is the outer
+        // product nt (x) gn per column, but only the frame's rotation reaches
+        // the parameters, so the sum over columns of f_a x (nt_a gn) -- the
+        // torque n_w x gn with n_w the fragment's world normal (Eq. 7) -- is
+        // all that is reduced
+        const float nw0 = fmaf(nt0, r.r2.z, fmaf(nt1, r.r3.y, nt2 * r.r4.x));
+        const float nw1 = fmaf(nt0, r.r2.w, fmaf(nt1, r.r3.z, nt2 * r.r4.y));
+        const float nw2 = fmaf(nt0, r.r3.x, fmaf(nt1, r.r3.w, nt2 * r.r4.z));
+        gi[10] = fmaf(nw1, gn2, -nw2 * gn1);
+        gi[11] = fmaf(nw2, gn0, -nw0 * gn2);
+        gi[12] = fmaf(nw0, gn1, -nw1 * gn0);
       }
-      // per-splat record gradients (19 values): transpose through shared
+      // per-splat record gradients (13 values): transpose through shared
       // memory (value-major, rows padded to 36 floats so the 16-byte reads
-      // below are conflict-free), then lane L < 19 adds up value L of all
+      // below are conflict-free), then lane L < 13 adds up value L of all
       // 32 lanes with a tree and issues one reduction per warp
       if (!ok) {
 #pragma unroll
-        for (int q = 0; q < 19; ++q) gi[q] = 0.f;
+        for (int q = 0; q < kRecGrads; ++q) gi[q] = 0.f;
       }
 #pragma unroll
-      for (int q = 0; q < 19; ++q) s_gi[warp][q][lane] = gi[q];
+      for (int q = 0; q < kRecGrads; ++q) s_gi[warp][q][lane] = gi[q];
       __syncwarp();
-      if (lane < 19) {
+      if (lane < kRecGrads) {
         const float4* col = reinterpret_cast<const float4*>(s_gi[warp][lane]);
         float4 a[8];
 #pragma unroll
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         a[0].x += a[2].x; a[0].y += a[2].y; a[0].z += a[2].z; a[0].w += a[2].w;
         a[1].x += a[3].x; a[1].y += a[3].y; a[1].z += a[3].z; a[1].w += a[3].w;
         const float s = (a[0].x + a[1].x) + (a[0].y + a[1].y) + (a[0].z + a[1].z) + (a[0].w + a[1].w);
-        if (s != 0.f) atomicAdd(g_items + (size_t)item * 20 + lane, (double)s);
+        if (s != 0.f) atomicAdd(g_items + (size_t)item * kRecGradStride + lane, (double)s);
       }
       __syncwarp();
       // texel gradients: lanes are grouped by bilinear cell (the four texels

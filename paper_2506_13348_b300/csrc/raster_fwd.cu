@@ -2,24 +2,22 @@
 //
 // The tile's depth-sorted splat list is walked front to back in batches of
 // 256 records staged in shared memory (one 80-byte record load per thread).
-// Each batch is processed in chunks of 32 entries in three phases:
+// Each batch is processed in chunks of 32 entries in two phases:
 //   0. lane t tests entry t of the chunk against the warp's whole 8x4 pixel
-//      block (conservative, see block_may_hit); typically most entries of a
-//      tile list miss a given block and are dropped here at ~2 instructions
-//      per entry;
-//   1. every lane tests the surviving entries for its pixel in lockstep (closed-form
-//      (u,v) of the splat, support cut, Gaussian, opacity -- Sec. 3.1,
-//      Eq. 2) and keeps a bitmask of the fragments that exist;
-//   2. every lane then blends its own set bits in list order: bilinear texel
-//      fetch from the splat's chart (Eq. 5-6), normal mapping (Eq. 7) and
-//      front-to-back compositing of the 8 G-buffer channels (Eq. 3, 8-9).
-// Phase 2 lets lanes work on different splats at the same time, so a warp
-// pays for max(fragments per lane) blends per chunk rather than for every
-// entry any lane blends.  Each pixel still blends exactly the fragments of
-// the definition, in order, with the same arithmetic.  The CTA leaves the list
-// once every pixel's transmittance fell below 1e-4.  Shading (Eq. 10-12) is
-// fused into the epilogue; the G-buffer is written only when the backward
-// needs it.
+//      block (conservative, see block_may_hit); typically about half of the
+//      entries of a tile list miss a given block and are dropped here at a
+//      few instructions per entry;
+//   1. the warp walks the surviving entries in order: every lane evaluates
+//      the entry at its pixel (closed-form (u,v) of the splat, support cut,
+//      Gaussian, opacity -- Sec. 3.1, Eq. 2) and the lanes it covers blend
+//      it: bilinear texel fetch from the splat's chart (Eq. 5-6), normal
+//      mapping (Eq. 7) and front-to-back compositing of the 8 G-buffer
+//      channels (Eq. 3, 8-9).  All lanes of a warp read the same record
+//      (a shared-memory broadcast) and mostly the same texels.
+// Each pixel blends exactly the fragments of the definition, in order, with
+// the same arithmetic.  The CTA leaves the list once every pixel's
+// transmittance fell below 1e-4.  Shading (Eq. 10-12) is fused into the
+// epilogue; the G-buffer is written only when the backward needs it.
 #include "raster.cuh"
 #include "shading.cuh"
 #include "kernels.h"
@@ -71,36 +69,29 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
       const int cn = min(32, nb - c0);
       const bool cand = lane < cn && block_may_hit(srec[c0 + lane], bx0, bx1, by0, by1);
       const unsigned cmask = __ballot_sync(FULL, cand);
-      // phase 1: which of the surviving entries make a fragment at this pixel
-      unsigned mask = 0;
-      if (!done) {
-        for (unsigned m = cmask; m; m &= m - 1) {
-          const int t = __ffs(m) - 1;
-          Frag f;
-          if (eval_frag(srec[c0 + t], xp, yp, f)) mask |= 1u << t;
-        }
-      }
-      // phase 2: blend them in order
-      while (mask && !done) {
-        const int t = __ffs(mask) - 1;
-        mask &= mask - 1;
+      // phase 1: the warp takes the surviving entries in list order; lanes
+      // whose pixel the entry covers blend it
+      for (unsigned m = cmask; m; m &= m - 1) {
+        const int t = __ffs(m) - 1;
         const Record r = srec[c0 + t];
         Frag f;
-        eval_frag(r, xp, yp, f);
-        const TexSample ts_ = tex_setup(f.u, f.v, T);
-        float x[8];
-        tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x, nullptr);
-        normal_map(r, x);
-        const float w = f.alpha * Tr;
+        const bool ok = !done && eval_frag(r, xp, yp, f);
+        if (__any_sync(FULL, ok) && ok) {
+          const TexSample ts_ = tex_setup(f.u, f.v, T);
+          float x[8];
+          tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x, nullptr);
+          normal_map(r, x);
+          const float w = f.alpha * Tr;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
-        Acc += w;
-        Tr = Tr * (1.f - f.alpha);
-        last = (int)(base + c0 + t);
-        if (STATS) ++n_blend;
-        if (Tr < kTMin()) {
-          done = true;
-          stop = last;
+          for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
+          Acc += w;
+          Tr = Tr * (1.f - f.alpha);
+          last = (int)(base + c0 + t);
+          if (STATS) ++n_blend;
+          if (Tr < kTMin()) {
+            done = true;
+            stop = last;
+          }
         }
       }
     }

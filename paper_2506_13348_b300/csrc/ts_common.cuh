@@ -29,6 +29,12 @@ __host__ __device__ constexpr float kTMin() { return 1e-4f; }
 __host__ __device__ constexpr float kAMin() { return 1e-7f; }
 __host__ __device__ constexpr float kNdotVMin() { return 1e-4f; }
 
+// Per-item record gradients summed by the backward rasteriser (float64):
+// 0-8 d/d(h_u, h_v, h_w), 9 d/do, 10-12 the torque of the normal-mapping
+// frame; stride 14 keeps rows 16-byte aligned.
+constexpr int kRecGrads = 13;
+constexpr int kRecGradStride = 14;
+
 enum Dtype : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
 
 // Environment light (Eq. 11-12): specular mip chain, irradiance cube, BRDF LUT.

@@ -97,38 +97,64 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t* out, int n, void* temp,
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits (fewer for the last pass).
-// A block owns RS_TILE consecutive keys; warp w of the block owns the
-// sub-range [w * RS_WARP, (w+1) * RS_WARP), processed in rounds of 32.
+// Stable LSD radix sort, digits of at most 8 bits.
+// A block owns 256 * R consecutive keys; warp w of the block owns the
+// sub-range [w * 32 R, (w+1) * 32 R), processed in R rounds of 32.  Small
+// sorts (the per-splat depth sort) take R = 4 so that enough blocks exist
+// to fill the GPU; the pair sort takes R = 16.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 16;
-constexpr int RS_WARP = 32 * RS_ROUNDS;
-constexpr int RS_TILE = RS_WARPS * RS_WARP;  // 4096
 constexpr int RADIX = 256;
+constexpr int RS_SMALL_N = 1 << 18;
+template <int R>
+struct RsTile {
+  static constexpr int WARP = 32 * R;
+  static constexpr int N = RS_WARPS * WARP;
+};
+static int rs_tile(int n) { return n <= RS_SMALL_N ? RsTile<4>::N : RsTile<16>::N; }
 
 template <typename K>
 __device__ __forceinline__ uint32_t digit_of(K key, int shift, uint32_t mask) {
   return (uint32_t)(key >> shift) & mask;
 }
 
-template <typename K>
+// Lanes of the warp holding the same digit (and a valid element): one ballot
+// per digit bit, cheaper than a general match for digits of <= 8 bits.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, int bits, bool ok) {
+  unsigned peers = __ballot_sync(0xffffffffu, ok);
+  for (int b = 0; b < bits; ++b) {
+    const bool set = (d >> b) & 1u;
+    const unsigned bb = __ballot_sync(0xffffffffu, set);
+    peers &= set ? bb : ~bb;
+  }
+  return peers;
+}
+
+template <typename K, int R>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__ keys, int n, int shift,
                                                             uint32_t mask, uint32_t* __restrict__ counts,
                                                             int nblocks) {
   __shared__ uint32_t hist[RADIX];
   for (int i = threadIdx.x; i < RADIX; i += RS_THREADS) hist[i] = 0;
   __syncthreads();
+  constexpr int RS_TILE = RsTile<R>::N;
   const int base = blockIdx.x * RS_TILE;
+  const int bits = 32 - __clz(mask);
+  const unsigned lt_mask = (1u << (threadIdx.x & 31)) - 1u;
   for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+    // one shared-memory atomic per distinct digit of the warp's 32 keys
+    // (neighbouring keys often share their high digits)
     const int idx = base + i;
-    if (idx < n) atomicAdd(&hist[digit_of(keys[idx], shift, mask)], 1u);
+    const bool ok = idx < n;
+    const uint32_t d = ok ? digit_of(keys[idx], shift, mask) : 0u;
+    const unsigned peers = digit_peers(d, bits, ok);
+    if (ok && (peers & lt_mask) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   for (int d = threadIdx.x; d <= (int)mask; d += RS_THREADS) counts[(size_t)d * nblocks + blockIdx.x] = hist[d];
 }
 
-template <typename K>
+template <typename K, int R>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                K* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -138,7 +164,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = lane; i < RADIX; i += 32) whist[warp][i] = 0;
   __syncwarp();
-  const int wbase = blockIdx.x * RS_TILE + warp * RS_WARP;
+  constexpr int RS_ROUNDS = R;
+  const int wbase = blockIdx.x * RsTile<R>::N + warp * RsTile<R>::WARP;
   K kr[RS_ROUNDS];
   uint32_t dg[RS_ROUNDS];
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -181,17 +208,113 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
   }
 }
 
+// Scatter with a block-local reorder (32-bit keys): the block first places
+// its RS_TILE elements in shared memory grouped by digit (stable), then
+// threads write consecutive slots, so each digit's run of the block goes out
+// as consecutive addresses instead of one scattered 4-byte store per element.
+template <int R>
+__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter_local(const uint32_t* __restrict__ kin,
+                                                                     const uint32_t* __restrict__ vin,
+                                                                     uint32_t* __restrict__ kout,
+                                                                     uint32_t* __restrict__ vout, int n, int shift,
+                                                                     int bits,
+                                                                     const uint32_t* __restrict__ offsets,
+                                                                     int nblocks) {
+  constexpr int RS_ROUNDS = R, RS_TILE = RsTile<R>::N;
+  __shared__ uint32_t whist[RS_WARPS][RADIX];
+  __shared__ uint32_t s_key[RS_TILE];
+  __shared__ uint32_t s_val[RS_TILE];
+  __shared__ uint32_t s_dstart[RADIX];
+  __shared__ uint32_t s_goff[RADIX];
+  __shared__ uint32_t s_wsum[RS_WARPS];
+  const uint32_t mask = (1u << bits) - 1u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = lane; i < RADIX; i += 32) whist[warp][i] = 0;
+  __syncwarp();
+  const int wbase = blockIdx.x * RS_TILE + warp * RsTile<R>::WARP;
+  // all loads of the warp's keys and values first (32 in flight per thread)
+  uint32_t kr[RS_ROUNDS], vr[RS_ROUNDS];
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    kr[r] = idx < n ? kin[idx] : 0u;
+    vr[r] = idx < n ? vin[idx] : 0u;
+  }
+  const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    const bool ok = idx < n;
+    const uint32_t d = digit_of(kr[r], shift, mask);
+    const unsigned peers = digit_peers(d, bits, ok);
+    if (ok && (peers & lt_mask) == 0) whist[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: warp runs inside the block's run (exclusive over warps), the
+  // block's count, then an exclusive scan of the counts over digits
+  const int dt = threadIdx.x;  // RS_THREADS == RADIX
+  uint32_t cnt = 0;
+  if (dt <= (int)mask) {
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const uint32_t c = whist[w][dt];
+      whist[w][dt] = cnt;
+      cnt += c;
+    }
+    s_goff[dt] = offsets[(size_t)dt * nblocks + blockIdx.x];
+  }
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0;
+#pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) before += (w < warp) ? s_wsum[w] : 0u;
+  s_dstart[dt] = before + incl - cnt;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    const bool ok = idx < n;
+    const uint32_t d = digit_of(kr[r], shift, mask);
+    const unsigned peers = digit_peers(d, bits, ok);
+    if (ok) {
+      const uint32_t slot = s_dstart[d] + whist[warp][d] + __popc(peers & lt_mask);
+      s_key[slot] = kr[r];
+      s_val[slot] = vr[r];
+    }
+    __syncwarp();
+    if (ok && (peers & lt_mask) == 0) whist[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  const int nblk = min(RS_TILE, n - (int)blockIdx.x * RS_TILE);
+  for (int sl = threadIdx.x; sl < nblk; sl += RS_THREADS) {
+    const uint32_t key = s_key[sl];
+    const uint32_t dd = digit_of(key, shift, mask);
+    const uint32_t pos = s_goff[dd] + ((uint32_t)sl - s_dstart[dd]);
+    kout[pos] = key;
+    vout[pos] = s_val[sl];
+  }
+}
+static_assert(RS_THREADS == RADIX, "one thread per digit in the local scan");
+
 size_t radix_temp_bytes(int n) {
-  const int nb = ceil_div(n > 0 ? n : 1, RS_TILE);
+  const int nb = ceil_div(n > 0 ? n : 1, rs_tile(n));
   const size_t cnt = (size_t)RADIX * nb;
   return 2 * cnt * sizeof(uint32_t) + 512 + scan_temp_bytes((int)cnt);
 }
 
-template <typename K>
-static int radix_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
+template <typename K, int R>
+static int radix_sort_r(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
                       cudaStream_t st) {
   if (n <= 1 || end_bit <= begin_bit) return 0;
-  const int nb = ceil_div(n, RS_TILE);
+  const int nb = ceil_div(n, RsTile<R>::N);
   const size_t cnt = (size_t)RADIX * nb;
   uint32_t* counts = reinterpret_cast<uint32_t*>(temp);
   uint32_t* offs = counts + cnt;
@@ -200,18 +323,34 @@ static int radix_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin
   int cur = 0;
   K* kb[2] = {k0, k1};
   uint32_t* vb[2] = {v0, v1};
-  for (int bit = begin_bit; bit < end_bit; bit += 8) {
-    const int bits = min(8, end_bit - bit);
+  // as few passes as 8-bit digits need, with the bits spread evenly over them
+  // (e.g. 12 bits -> 2 x 6: fewer digits per pass means longer runs per block)
+  const int passes = (end_bit - begin_bit + 7) / 8;
+  const int step = (end_bit - begin_bit + passes - 1) / passes;
+  for (int bit = begin_bit; bit < end_bit; bit += step) {
+    const int bits = min(step, end_bit - bit);
     const uint32_t mask = (1u << bits) - 1u;
     const int nd = 1 << bits;
-    k_radix_hist<K><<<nb, RS_THREADS, 0, st>>>(kb[cur], n, bit, mask, counts, nb);
+    k_radix_hist<K, R><<<nb, RS_THREADS, 0, st>>>(kb[cur], n, bit, mask, counts, nb);
     note_launches(1);
     launch_exclusive_scan(counts, offs, nd * nb, rest, st);
-    k_radix_scatter<K><<<nb, RS_THREADS, 0, st>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, bit, mask, offs, nb);
+    if constexpr (sizeof(K) == 4)
+      k_radix_scatter_local<R><<<nb, RS_THREADS, 0, st>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, bit, bits,
+                                                       offs, nb);
+    else
+      k_radix_scatter<K, R><<<nb, RS_THREADS, 0, st>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, bit, mask, offs,
+                                                    nb);
     note_launches(1);
     cur ^= 1;
   }
   return cur;
+}
+
+template <typename K>
+static int radix_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
+                      cudaStream_t st) {
+  if (n <= RS_SMALL_N) return radix_sort_r<K, 4>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
+  return radix_sort_r<K, 16>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
 }
 
 int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,

@@ -83,25 +83,6 @@ __device__ __forceinline__ float3 cube_bilinear(const void* cube, int dtype, int
   return make_float3(gy * top.x + b.fy * bot.x, gy * top.y + b.fy * bot.y, gy * top.z + b.fy * bot.z);
 }
 
-// Scatter g (3 channels) with bilinear weights into a float32 cube gradient.
-__device__ __forceinline__ void cube_scatter(float* gcube, int R, int face, const Bil& b, float3 g, float scale) {
-  if (!gcube) return;
-  long long fb = (long long)face * R * R;
-  float gx = 1.f - b.fx, gy = 1.f - b.fy;
-  float w[4] = {gx * gy * scale, b.fx * gy * scale, gx * b.fy * scale, b.fx * b.fy * scale};
-  long long idx[4] = {fb + (long long)b.ja * R + b.ia, fb + (long long)b.ja * R + b.ib,
-                      fb + (long long)b.jb * R + b.ia, fb + (long long)b.jb * R + b.ib};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (w[k] != 0.f) {
-      float* p = gcube + idx[k] * 3;
-      red_add(p, w[k] * g.x);
-      red_add(p + 1, w[k] * g.y);
-      red_add(p + 2, w[k] * g.z);
-    }
-  }
-}
-
 // d(s,t) of a cube lookup -> d(direction).
 __device__ __forceinline__ float3 cube_coord_grad(const CubeCoord& c, float gs, float gt) {
   float ima = 1.f / c.ma;
@@ -216,16 +197,27 @@ __device__ __forceinline__ float4 shade_pixel(const EnvDesc& E, const float X[8]
   return make_float4(col[0], col[1], col[2], A);
 }
 
+// What the environment maps receive from one pixel: gsp (3 channels) with
+// bilinear weights at level l0 (times w0) and l1 (times w1, when levels > 1)
+// of the specular chain, gir at the irradiance cube.
+struct EnvGrad {
+  bool ok;
+  int l0, l1, face_r, face_n;
+  Bil b0, b1, bi;
+  float w0, w1;
+  float3 gsp, gir;
+};
+
 // Adjoint of shade_pixel: given dL/drgba returns dL/dX (8) and dL/dA, and
-// scatters the environment gradients (spec levels, irradiance) if non-null.
+// the environment-map gradient of the pixel in `eg` (scattered by the caller).
 __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[8], float A, float3 d,
-                                                float4 g, float gX[8], float& gA, float* const* gspec,
-                                                float* girr) {
+                                                float4 g, float gX[8], float& gA, EnvGrad& eg) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) gX[c] = 0.f;
   ShadeState s;
   shade_pixel(E, X, A, d, &s);
   gA = g.w;
+  eg.ok = s.ok;
   if (!s.ok) return;
   const float inv_pi = 0.318309886183790672f;
   float gc[3] = {g.x, g.y, g.z};
@@ -272,7 +264,14 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
     float w0 = (L > 1) ? (1.f - s.f) : 1.f;
     float gs = w0 * R0 * (gsp.x * dx0.x + gsp.y * dx0.y + gsp.z * dx0.z);
     float gt = w0 * R0 * (gsp.x * dy0.x + gsp.y * dy0.y + gsp.z * dy0.z);
-    if (gspec) cube_scatter(gspec[s.l0], E.spec_res[s.l0], cr.face, b0, gsp, w0);
+    eg.l0 = s.l0;
+    eg.l1 = s.l1;
+    eg.face_r = cr.face;
+    eg.b0 = b0;
+    eg.b1 = b0;
+    eg.w0 = w0;
+    eg.w1 = 0.f;
+    eg.gsp = gsp;
     if (L > 1) {
       Bil b1;
       float3 dx1, dy1;
@@ -280,7 +279,8 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
       float3 c1 = cube_bilinear(E.spec[s.l1], E.cube_dtype, E.spec_res[s.l1], cr, b1, &dx1, &dy1);
       gs += s.f * R1 * (gsp.x * dx1.x + gsp.y * dx1.y + gsp.z * dx1.z);
       gt += s.f * R1 * (gsp.x * dy1.x + gsp.y * dy1.y + gsp.z * dy1.z);
-      if (gspec) cube_scatter(gspec[s.l1], E.spec_res[s.l1], cr.face, b1, gsp, s.f);
+      eg.b1 = b1;
+      eg.w1 = s.f;
       float glod = gsp.x * (c1.x - c0.x) + gsp.y * (c1.y - c0.y) + gsp.z * (c1.z - c0.z);
       grc += glod * (float)(L - 1);
     }
@@ -297,7 +297,9 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
     float Ri = (float)E.irr_res;
     float gs = Ri * (gi.x * dx.x + gi.y * dx.y + gi.z * dx.z);
     float gt = Ri * (gi.x * dy.x + gi.y * dy.y + gi.z * dy.z);
-    if (girr) cube_scatter(girr, E.irr_res, cn.face, bi, gi, 1.f);
+    eg.face_n = cn.face;
+    eg.bi = bi;
+    eg.gir = gi;
     gNh = cube_coord_grad(cn, gs, gt);
   }
   // w_r = 2 nv Nh - wo ; nv = Nh.wo ; ndv = clamp(nv)

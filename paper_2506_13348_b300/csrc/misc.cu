@@ -45,28 +45,45 @@ void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStre
 }
 
 // L1 over RGB: loss = mean |rgb - target|, dL/drgb = sign / (3 n), dL/dalpha = 0.
-__global__ void k_l1_loss(const float4* __restrict__ rgba, const float4* __restrict__ tgt, long long n,
-                          float* __restrict__ loss, float4* __restrict__ grad) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Grid-stride over pixels; one atomic per block (a single float receives
+// the loss, so per-warp atomics would serialise on it).
+constexpr int L1_THREADS = 256;
+
+__global__ void __launch_bounds__(L1_THREADS) k_l1_loss(const float4* __restrict__ rgba,
+                                                         const float4* __restrict__ tgt, long long n,
+                                                         float* __restrict__ loss, float4* __restrict__ grad) {
+  __shared__ float s_part[L1_THREADS / 32];
+  const float k = 1.f / (3.f * (float)n);
+  auto sgn = [](float d) { return d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f); };
   float s = 0.f;
-  if (i < n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float4 a = rgba[i], b = tgt[i];
     const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-    s = fabsf(dx) + fabsf(dy) + fabsf(dz);
-    const float k = 1.f / (3.f * (float)n);
-    auto sgn = [](float d) { return d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f); };
+    s += fabsf(dx) + fabsf(dy) + fabsf(dz);
     grad[i] = make_float4(sgn(dx) * k, sgn(dy) * k, sgn(dz) * k, 0.f);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(loss, s / (3.f * (float)n));
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < L1_THREADS / 32; ++w) t += s_part[w];
+    if (t != 0.f) atomicAdd(loss, t * k);
+  }
 }
 
 void launch_l1_loss(const float4* rgba, const float4* target, long long n, float* loss, float4* grad,
                     cudaStream_t st) {
   cudaMemsetAsync(loss, 0, sizeof(float), st);
   if (n > 0) {
-    k_l1_loss<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rgba, target, n, loss, grad);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (n + L1_THREADS - 1) / L1_THREADS;
+    const int grid = (int)(want < (long long)sms * 4 ? want : (long long)sms * 4);
+    k_l1_loss<<<grid, L1_THREADS, 0, st>>>(rgba, target, n, loss, grad);
     note_launches(1);
   }
 }

@@ -425,17 +425,36 @@ void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_
     note_launches(1);
 }
 
+// Tile ranges from the sorted tile ids: 4 keys per thread (one 16-byte
+// load plus the neighbours at both ends), a range boundary wherever the id
+// changes.
 __global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int K, uint2* __restrict__ ranges) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= K) return;
-  const uint32_t t = keys[i];
-  if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-  if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+  const long long i0 = 4ll * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= K) return;
+  uint32_t k[6];
+  k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+  if (i0 + 4 <= K) {
+    const uint4 q = *reinterpret_cast<const uint4*>(keys + i0);
+    k[1] = q.x; k[2] = q.y; k[3] = q.z; k[4] = q.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[1 + j] = (i0 + j < K) ? keys[i0 + j] : 0xffffffffu;
+  }
+  k[5] = (i0 + 4 < K) ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const long long i = i0 + j;
+    if (i >= K) break;
+    const uint32_t t = k[1 + j];
+    if (i == 0 || k[j] != t) ranges[t].x = (uint32_t)i;
+    if (i == K - 1 || k[2 + j] != t) ranges[t].y = (uint32_t)(i + 1);
+  }
 }
 
 void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStream_t st) {
   if (K > 0) {
-    k_tile_ranges<<<ceil_div(K, 256), 256, 0, st>>>(tile_keys, K, ranges);
+    const int threads = (int)((K + 3) / 4);
+    k_tile_ranges<<<ceil_div(threads, 256), 256, 0, st>>>(tile_keys, K, ranges);
     note_launches(1);
   }
 }

@@ -1,21 +1,22 @@
-// Forward rasteriser: one CTA per 16x16 tile, one thread per pixel.
+// Forward rasteriser: one CTA per 16x16 tile, one thread per pixel, one
+// warp per 8x4 pixel block.
 //
-// The tile's depth-sorted splat list is walked front to back in batches of
-// 256 records staged in shared memory (one 80-byte record load per thread).
-// Each batch is processed in chunks of 32 entries in two phases:
-//   0. lane t tests entry t of the chunk against the warp's whole 8x4 pixel
-//      block (conservative, see block_may_hit); typically about half of the
-//      entries of a tile list miss a given block and are dropped here at a
-//      few instructions per entry;
-//   1. the warp walks the surviving entries in order: every lane evaluates
+// Each warp walks the tile's depth-sorted splat list front to back on its
+// own (no block-wide barrier), 32 entries at a time:
+//   0. lane t loads the first 48 bytes of entry t's record (the homography
+//      rows and the opacity), stages them in shared memory and tests the
+//      entry against the warp's whole pixel block (conservative, see
+//      block_may_hit); typically about half of the entries of a tile list
+//      miss a given block and are dropped here;
+//   1. the warp takes the surviving entries in order: every lane evaluates
 //      the entry at its pixel (closed-form (u,v) of the splat, support cut,
 //      Gaussian, opacity -- Sec. 3.1, Eq. 2) and the lanes it covers blend
 //      it: bilinear texel fetch from the splat's chart (Eq. 5-6), normal
-//      mapping (Eq. 7) and front-to-back compositing of the 8 G-buffer
-//      channels (Eq. 3, 8-9).  All lanes of a warp read the same record
-//      (a shared-memory broadcast) and mostly the same texels.
+//      mapping (Eq. 7) with the rest of the record, and front-to-back
+//      compositing of the 8 G-buffer channels (Eq. 3, 8-9).  All lanes read
+//      the same record (a shared-memory broadcast) and mostly the same texels.
 // Each pixel blends exactly the fragments of the definition, in order, with
-// the same arithmetic.  The CTA leaves the list once every pixel's
+// the same arithmetic.  A warp leaves the list once all its pixels'
 // transmittance fell below 1e-4.  Shading (Eq. 10-12) is fused into the
 // epilogue; the G-buffer is written only when the backward needs it.
 #include "raster.cuh"
@@ -30,7 +31,6 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
                                                      const uint32_t* __restrict__ pair_items,
                                                      const uint2* __restrict__ ranges,
                                                      unsigned long long* __restrict__ stats) {
-  __shared__ Record srec[256];
   constexpr unsigned FULL = 0xffffffffu;
   const int tile = blockIdx.x;
   const int v = find_view(vt, tile);
@@ -57,43 +57,63 @@ __global__ void __launch_bounds__(256) k_raster_fwd(ViewTable vt, const Record* 
   bool done = !inside;
   unsigned n_blend = 0;
 
-  for (unsigned base = range.x; base < range.y; base += 256) {
-    if (__syncthreads_count(done) == 256) break;
-    const unsigned i = base + threadIdx.x;
-    if (i < range.y) srec[threadIdx.x] = rec[pair_items[i]];
-    __syncthreads();
-    const int nb = min(256u, range.y - base);
-    for (int c0 = 0; c0 < nb; c0 += 32) {
+  // per-warp walk: no CTA barrier; lane t stages entry c0 + t's first 48
+  // bytes in shared memory for the block test and the lockstep loop
+  {
+    __shared__ float4 s_r[8][32][3];
+    __shared__ uint32_t s_it[8][32];
+    const int warp = threadIdx.x >> 5;
+    for (unsigned c0 = range.x; c0 < range.y; c0 += 32) {
       if (__all_sync(FULL, done)) break;
-      // phase 0: lane t tests entry c0 + t against the warp's 8x4 block
-      const int cn = min(32, nb - c0);
-      const bool cand = lane < cn && block_may_hit(srec[c0 + lane], bx0, bx1, by0, by1);
+      const unsigned e = c0 + lane;
+      bool cand = false;
+      if (e < range.y) {
+        const uint32_t it = __ldg(pair_items + e);
+        const float4* rp = reinterpret_cast<const float4*>(rec + it);
+        Record c;
+        c.r0 = __ldg(rp);
+        c.r1 = __ldg(rp + 1);
+        c.r2 = __ldg(rp + 2);
+        cand = block_may_hit(c, bx0, bx1, by0, by1);
+        s_r[warp][lane][0] = c.r0;
+        s_r[warp][lane][1] = c.r1;
+        s_r[warp][lane][2] = c.r2;
+        s_it[warp][lane] = it;
+      }
       const unsigned cmask = __ballot_sync(FULL, cand);
-      // phase 1: the warp takes the surviving entries in list order; lanes
-      // whose pixel the entry covers blend it
+      __syncwarp();
       for (unsigned m = cmask; m; m &= m - 1) {
         const int t = __ffs(m) - 1;
-        const Record r = srec[c0 + t];
+        Record r;
+        r.r0 = s_r[warp][t][0];
+        r.r1 = s_r[warp][t][1];
+        r.r2 = s_r[warp][t][2];
         Frag f;
         const bool ok = !done && eval_frag(r, xp, yp, f);
-        if (__any_sync(FULL, ok) && ok) {
-          const TexSample ts_ = tex_setup(f.u, f.v, T);
-          float x[8];
-          tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x, nullptr);
-          normal_map(r, x);
-          const float w = f.alpha * Tr;
+        if (__any_sync(FULL, ok)) {
+          const float4* rp = reinterpret_cast<const float4*>(rec + s_it[warp][t]);
+          r.r3 = __ldg(rp + 3);
+          r.r4 = __ldg(rp + 4);
+          if (ok) {
+            const TexSample ts_ = tex_setup(f.u, f.v, T);
+            float x[8];
+            tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x, nullptr);
+            normal_map(r, x);
+            const float w = f.alpha * Tr;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
-          Acc += w;
-          Tr = Tr * (1.f - f.alpha);
-          last = (int)(base + c0 + t);
-          if (STATS) ++n_blend;
-          if (Tr < kTMin()) {
-            done = true;
-            stop = last;
+            for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
+            Acc += w;
+            Tr = Tr * (1.f - f.alpha);
+            last = (int)(c0 + t);
+            if (STATS) ++n_blend;
+            if (Tr < kTMin()) {
+              done = true;
+              stop = last;
+            }
           }
         }
       }
+      __syncwarp();
     }
   }
 

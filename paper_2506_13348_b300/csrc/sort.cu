@@ -390,11 +390,13 @@ __global__ void __launch_bounds__(256) k_emit_pairs(ViewTable vt, const uint32_t
   if (first >= n) return;
   const int my = first + lane;
   uint32_t my_item = 0, my_cnt = 0, my_off = 0;
+  int4 my_rc = make_int4(0, 0, 0, 0);
   if (my < n) {
     my_cnt = counts_sorted[my];
     if (my_cnt) {
       my_item = order[my];
       my_off = offsets[my];
+      my_rc = rects[my_item];  // loaded up front: the loop below has no dependent global loads
     }
   }
   unsigned todo = __ballot_sync(0xffffffffu, my_cnt != 0);
@@ -406,12 +408,25 @@ __global__ void __launch_bounds__(256) k_emit_pairs(ViewTable vt, const uint32_t
     const uint32_t off = __shfl_sync(0xffffffffu, my_off, src);
     const int v = find_view_item(vt, (int)item);
     const ViewDesc& V = vt.v[v];
-    const int4 rc = rects[item];
+    int4 rc;
+    rc.x = __shfl_sync(0xffffffffu, my_rc.x, src);
+    rc.y = __shfl_sync(0xffffffffu, my_rc.y, src);
+    rc.z = __shfl_sync(0xffffffffu, my_rc.z, src);
     const int w = rc.y - rc.x + 1;
+    // lane's tile (row, column) in the rect, advanced by 32 entries per step
+    // without a division per entry
+    int col = lane % w, row = lane / w;
+    const int dq = 32 / w, dr = 32 % w;
+    const uint32_t t0 = (uint32_t)(V.tile_off + rc.z * V.tiles_x + rc.x);
     for (uint32_t j = lane; j < cnt; j += 32) {
-      const int tx = rc.x + (int)(j % w), ty = rc.z + (int)(j / w);
-      tile_keys[off + j] = (uint32_t)(V.tile_off + ty * V.tiles_x + tx);
+      tile_keys[off + j] = t0 + (uint32_t)(row * V.tiles_x + col);
       pair_items[off + j] = item;
+      col += dr;
+      row += dq;
+      if (col >= w) {
+        col -= w;
+        ++row;
+      }
     }
   }
 }

@@ -139,16 +139,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* __restrict__
   __syncthreads();
   constexpr int RS_TILE = RsTile<R>::N;
   const int base = blockIdx.x * RS_TILE;
-  const int bits = 32 - __clz(mask);
-  const unsigned lt_mask = (1u << (threadIdx.x & 31)) - 1u;
   for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
-    // one shared-memory atomic per distinct digit of the warp's 32 keys
-    // (neighbouring keys often share their high digits)
+    // plain shared-memory atomics (aggregating equal digits per warp first
+    // with ballots or a match measured slower)
     const int idx = base + i;
-    const bool ok = idx < n;
-    const uint32_t d = ok ? digit_of(keys[idx], shift, mask) : 0u;
-    const unsigned peers = digit_peers(d, bits, ok);
-    if (ok && (peers & lt_mask) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    if (idx < n) atomicAdd(&hist[digit_of(keys[idx], shift, mask)], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d <= (int)mask; d += RS_THREADS) counts[(size_t)d * nblocks + blockIdx.x] = hist[d];

@@ -557,25 +557,34 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
             "h2d_bytes_per_step": RES * RES * 4 * 4, "d2h_bytes_per_step": 4}
 
 
+# Source files each profiled kernel is built from: a committed DRAM-traffic
+# figure is used only while all of them are unchanged.
+KERNEL_SOURCES = {
+    "raster_bwd": ["raster_bwd.cu", "raster.cuh", "shading.cuh", "ts_common.cuh"],
+    "raster_fwd": ["raster_fwd.cu", "raster.cuh", "shading.cuh", "ts_common.cuh"],
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    import hashlib
+    src = os.path.join(ROOT, "paper_2506_13348_b300", "csrc")
+    h = hashlib.sha256()
+    for fn in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(src, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def read_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
-    import hashlib
+    was taken on the current source of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     with open(path) as f:
         rec = json.load(f)
     ent = rec.get(kernel)
-    if not ent:
-        return None
-    src = os.path.join(ROOT, "paper_2506_13348_b300", "csrc")
-    h = hashlib.sha256()
-    for fn in sorted(os.listdir(src)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(src, fn), "rb") as f:
-                h.update(f.read())
-    if ent.get("source_sha256") != h.hexdigest():
+    if not ent or ent.get("source_sha256") != kernel_source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 

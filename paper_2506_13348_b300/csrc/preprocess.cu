@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(256) k_preprocess(ViewTable vt, Record* __rest
   // normal turned to face the camera: (p - o).n = p_c . n_c > 0 -> flip
   const float sg = (D > 0.f) ? -1.f : 1.f;
   Record r;
-  r.r0 = make_float4(hu[0], hu[1], hu[2], hv[0]);
-  r.r1 = make_float4(hv[1], hv[2], hw[0], hw[1]);
+  r.r0 = make_float4(hu[0], hv[0], hu[1], hv[1]);
+  r.r1 = make_float4(hu[2], hv[2], hw[0], hw[1]);
   r.r2 = make_float4(hw[2], o, tu[0], tu[1]);
   r.r3 = make_float4(tu[2], tv[0], tv[1], tv[2]);
   r.r4 = make_float4(sg * n[0], sg * n[1], sg * n[2], __int_as_float(k));

@@ -17,11 +17,12 @@ struct Frag {
 // (outside the 3-sigma support square or alpha < 1/255).
 __device__ __forceinline__ bool eval_frag(const Record& r, float xp, float yp, Frag& f) {
   float den = fmaf(r.r1.z, xp, fmaf(r.r1.w, yp, r.r2.x));
-  float un = fmaf(r.r0.x, xp, fmaf(r.r0.y, yp, r.r0.z));
-  float vn = fmaf(r.r0.w, xp, fmaf(r.r1.x, yp, r.r1.y));
+  // (un, vn) as one channel pair: same roundings as the scalar fmaf chains
+  const float2 uvn = fma2(f2(r.r0.x, r.r0.y), f2(xp, xp), fma2(f2(r.r0.z, r.r0.w), f2(yp, yp), f2(r.r1.x, r.r1.y)));
   f.rd = __fdividef(1.0f, den);
-  f.u = __fmul_rn(un, f.rd);
-  f.v = __fmul_rn(vn, f.rd);
+  const float2 uv = mul2(uvn, f2(f.rd, f.rd));
+  f.u = uv.x;
+  f.v = uv.y;
   if (!(fabsf(f.u) <= 3.0f && fabsf(f.v) <= 3.0f)) return false;
   float q = fmaf(f.u, f.u, __fmul_rn(f.v, f.v));
   f.G = __expf(__fmul_rn(-0.5f, q));
@@ -44,10 +45,10 @@ __device__ __forceinline__ bool block_may_hit(const Record& r, float x0, float x
   for (int c = 0; c < 4; ++c) {
     const float x = (c & 1) ? x1 : x0, y = (c & 2) ? y1 : y0;
     const float den = fmaf(r.r1.z, x, fmaf(r.r1.w, y, r.r2.x));
-    const float un = fmaf(r.r0.x, x, fmaf(r.r0.y, y, r.r0.z));
-    const float vn = fmaf(r.r0.w, x, fmaf(r.r1.x, y, r.r1.y));
+    const float2 uvn = fma2(f2(r.r0.x, r.r0.y), f2(x, x), fma2(f2(r.r0.z, r.r0.w), f2(y, y), f2(r.r1.x, r.r1.y)));
     const float rd = __fdividef(1.0f, den);
-    const float u = un * rd, v = vn * rd;
+    const float2 uv = mul2(uvn, f2(rd, rd));
+    const float u = uv.x, v = uv.y;
     umin = fminf(umin, u); umax = fmaxf(umax, u);
     vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
     dmin = fminf(dmin, den); dmax = fmaxf(dmax, den);
@@ -79,37 +80,35 @@ __device__ __forceinline__ TexSample tex_setup(float u, float v, int T) {
   return s;
 }
 
-// Bilinear texel fetch (Eq. 6) of the 8 channels; optionally returns the
-// four corner texels for the backward.
+// Bilinear texel fetch (Eq. 6) of the 8 channels, as 4 channel pairs.
 template <int DT>
 __device__ __forceinline__ void tex_fetch(const void* texels, long long splat, int T, const TexSample& s,
-                                          float out[8], float corners[4][8]) {
+                                          float out[8]) {
   long long base = splat * (long long)T * T;
   float t0[8], t1[8], t2[8], t3[8];
   load_texel(texels, DT, base + s.ja * T + s.ia, t0);
   load_texel(texels, DT, base + s.ja * T + s.ib, t1);
   load_texel(texels, DT, base + s.jb * T + s.ia, t2);
   load_texel(texels, DT, base + s.jb * T + s.ib, t3);
-  float gx = 1.f - s.fx, gy = 1.f - s.fy;
+  const float gx = 1.f - s.fx, gy = 1.f - s.fy;
+  const float2 FX = f2(s.fx, s.fx), GX = f2(gx, gx), FY = f2(s.fy, s.fy), GY = f2(gy, gy);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    float top = fmaf(s.fx, t1[c], gx * t0[c]);
-    float bot = fmaf(s.fx, t3[c], gx * t2[c]);
-    out[c] = fmaf(s.fy, bot, gy * top);
-    if (corners) {
-      corners[0][c] = t0[c];
-      corners[1][c] = t1[c];
-      corners[2][c] = t2[c];
-      corners[3][c] = t3[c];
-    }
+  for (int q = 0; q < 4; ++q) {
+    const int c = 2 * q;
+    const float2 top = fma2(FX, f2(t1[c], t1[c + 1]), mul2(GX, f2(t0[c], t0[c + 1])));
+    const float2 bot = fma2(FX, f2(t3[c], t3[c + 1]), mul2(GX, f2(t2[c], t2[c + 1])));
+    const float2 o = fma2(FY, bot, mul2(GY, top));
+    out[c] = o.x;
+    out[c + 1] = o.y;
   }
 }
 
 // Normal mapping (Eq. 7): n = [t_u, t_v, n_f] n^t, in place on x[5..7].
 __device__ __forceinline__ void normal_map(const Record& r, float x[8]) {
   float a = x[5], b = x[6], c = x[7];
-  x[5] = fmaf(a, r.r2.z, fmaf(b, r.r3.y, c * r.r4.x));
-  x[6] = fmaf(a, r.r2.w, fmaf(b, r.r3.z, c * r.r4.y));
+  const float2 n01 = fma2(f2(a, a), f2(r.r2.z, r.r2.w), fma2(f2(b, b), f2(r.r3.y, r.r3.z), mul2(f2(c, c), f2(r.r4.x, r.r4.y))));
+  x[5] = n01.x;
+  x[6] = n01.y;
   x[7] = fmaf(a, r.r3.x, fmaf(b, r.r3.w, c * r.r4.z));
 }
 

@@ -126,7 +126,9 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         // and the tangent normal are needed
         const float hx = 1.f - ts_.fx, hy = 1.f - ts_.fy;
         w4[0] = hx * hy; w4[1] = ts_.fx * hy; w4[2] = hx * ts_.fy; w4[3] = ts_.fx * ts_.fy;
-        float nt0 = 0.f, nt1 = 0.f, nt2 = 0.f, gxx = 0.f, dxs = 0.f, dys = 0.f;
+        float2 nt01 = f2(0.f, 0.f), dxy = f2(0.f, 0.f);
+        float nt2 = 0.f, gxx = 0.f;
+        const float2 g01 = f2(g8[0], g8[1]), g23 = f2(g8[2], g8[3]), g45 = f2(g8[4], g8[5]), g67 = f2(g8[6], g8[7]);
         const long long base = splat * (long long)T * T;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -134,26 +136,32 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
           const int ii = (k & 1) ? ts_.ib : ts_.ia;
           float cv[8];
           load_texel(V.texels, DT, base + jj * T + ii, cv);
-          float tdot = 0.f;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) tdot = fmaf(g8[c], cv[c], tdot);
-          nt0 = fmaf(w4[k], cv[5], nt0);
-          nt1 = fmaf(w4[k], cv[6], nt1);
+          float2 acc = mul2(g01, f2(cv[0], cv[1]));
+          acc = fma2(g23, f2(cv[2], cv[3]), acc);
+          acc = fma2(g45, f2(cv[4], cv[5]), acc);
+          acc = fma2(g67, f2(cv[6], cv[7]), acc);
+          const float tdot = acc.x + acc.y;
+          nt01 = fma2(f2(w4[k], w4[k]), f2(cv[5], cv[6]), nt01);
           nt2 = fmaf(w4[k], cv[7], nt2);
           gxx = fmaf(w4[k], tdot, gxx);
           const float wyk = (k & 2) ? ts_.fy : hy;
           const float wxk = (k & 1) ? ts_.fx : hx;
-          dxs += ((k & 1) ? wyk : -wyk) * tdot;
-          dys += ((k & 2) ? wxk : -wxk) * tdot;
+          dxy = fma2(f2((k & 1) ? wyk : -wyk, (k & 2) ? wxk : -wxk), f2(tdot, tdot), dxy);
         }
+        const float nt0 = nt01.x, nt1 = nt01.y;
+        float dxs = dxy.x, dys = dxy.y;
         // dL/dalpha = T_before (Q - P): Q = gX.x + gA of this fragment, P the
         // same projection of everything blended behind it (P <- a Q + (1-a) P)
         const float Q = gxx + gA;
         const float ga = (Q - P) * Tb;
         P = fmaf(f.alpha, Q, om * P);
         Tcur = Tb;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) t8[c] = wgt * g8[c];
+        {
+          const float2 W = f2(wgt, wgt);
+          float2 p0 = mul2(W, g01), p1 = mul2(W, g23), p2 = mul2(W, g45), p3 = mul2(W, g67);
+          t8[0] = p0.x; t8[1] = p0.y; t8[2] = p1.x; t8[3] = p1.y;
+          t8[4] = p2.x; t8[5] = p2.y; t8[6] = p3.x; t8[7] = p3.y;
+        }
         dxs *= wgt;
         dys *= wgt;
         const float gn0 = wgt * gX[5], gn1 = wgt * gX[6], gn2 = wgt * gX[7];
@@ -168,9 +176,13 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         // u = un / den, v = vn / den
         const float gun = gu * f.rd, gvn = gv * f.rd;
         const float gden = -(gu * f.u + gv * f.v) * f.rd;
-        gi[0] = gun * xp; gi[1] = gun * yp; gi[2] = gun;
-        gi[3] = gvn * xp; gi[4] = gvn * yp; gi[5] = gvn;
-        gi[6] = gden * xp; gi[7] = gden * yp; gi[8] = gden;
+        {
+          const float2 XY = f2(xp, yp);
+          const float2 a0 = mul2(f2(gun, gun), XY), a1 = mul2(f2(gvn, gvn), XY), a2 = mul2(f2(gden, gden), XY);
+          gi[0] = a0.x; gi[1] = a0.y; gi[2] = gun;
+          gi[3] = a1.x; gi[4] = a1.y; gi[5] = gvn;
+          gi[6] = a2.x; gi[7] = a2.y; gi[8] = gden;
+        }
         gi[9] = go;
         // normal-mapping frame [t_u t_v n_f]: its gradient is the outer
         // product nt (x) gn per column, but only the frame's rotation reaches
@@ -200,13 +212,16 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         float4 a[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) a[q] = col[q];
+        float2 lo[4], hi[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          a[q].x += a[q + 4].x; a[q].y += a[q + 4].y; a[q].z += a[q + 4].z; a[q].w += a[q + 4].w;
+          lo[q] = add2(f2(a[q].x, a[q].y), f2(a[q + 4].x, a[q + 4].y));
+          hi[q] = add2(f2(a[q].z, a[q].w), f2(a[q + 4].z, a[q + 4].w));
         }
-        a[0].x += a[2].x; a[0].y += a[2].y; a[0].z += a[2].z; a[0].w += a[2].w;
-        a[1].x += a[3].x; a[1].y += a[3].y; a[1].z += a[3].z; a[1].w += a[3].w;
-        const float s = (a[0].x + a[1].x) + (a[0].y + a[1].y) + (a[0].z + a[1].z) + (a[0].w + a[1].w);
+        lo[0] = add2(lo[0], lo[2]); lo[1] = add2(lo[1], lo[3]);
+        hi[0] = add2(hi[0], hi[2]); hi[1] = add2(hi[1], hi[3]);
+        lo[0] = add2(add2(lo[0], lo[1]), add2(hi[0], hi[1]));
+        const float s = lo[0].x + lo[0].y;
         if (s != 0.f) atomicAdd(g_items + (size_t)item * kRecGradStride + lane, (double)s);
       }
       __syncwarp();
@@ -234,8 +249,11 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
           for (int k = 0; k < 4; ++k) {
             const int jj = (k & 2) ? ts_.jb : ts_.ja, ii = (k & 1) ? ts_.ib : ts_.ia;
             float* p = gtex + (jj * T + ii) * 8;
-            red_add_v4(p, w4[k] * t8[0], w4[k] * t8[1], w4[k] * t8[2], w4[k] * t8[3]);
-            red_add_v4(p + 4, w4[k] * t8[4], w4[k] * t8[5], w4[k] * t8[6], w4[k] * t8[7]);
+            const float2 Wk = f2(w4[k], w4[k]);
+            const float2 v0 = mul2(Wk, f2(t8[0], t8[1])), v1 = mul2(Wk, f2(t8[2], t8[3]));
+            const float2 v2 = mul2(Wk, f2(t8[4], t8[5])), v3 = mul2(Wk, f2(t8[6], t8[7]));
+            red_add_v4(p, v0.x, v0.y, v1.x, v1.y);
+            red_add_v4(p + 4, v2.x, v2.y, v3.x, v3.y);
           }
         }
         const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2, u1 = lane & 1;
@@ -250,31 +268,33 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
           // (column ib), bits 2..0 <-> channel; each step keeps the half
           // selected by the lane's bit and adds the partner's copy of it
           const float wk0 = u16 ? m2 : m0, wk1 = u16 ? m3 : m1, ws0 = u16 ? m0 : m2, ws1 = u16 ? m1 : m3;
-          float a[16];
+          const float2 WK0 = f2(wk0, wk0), WK1 = f2(wk1, wk1), WS0 = f2(ws0, ws0), WS1 = f2(ws1, ws1);
+          float2 a[8];  // channel pairs: a[q] = channels (2q, 2q+1) of column 0, a[4+q] of column 1
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            a[c] = fmaf(wk0, t8[c], __shfl_xor_sync(FULL, ws0 * t8[c], 16));
-            a[8 + c] = fmaf(wk1, t8[c], __shfl_xor_sync(FULL, ws1 * t8[c], 16));
+          for (int q = 0; q < 4; ++q) {
+            const float2 t = f2(t8[2 * q], t8[2 * q + 1]);
+            const float2 s0 = mul2(WS0, t), s1 = mul2(WS1, t);
+            a[q] = fma2(WK0, t, f2(__shfl_xor_sync(FULL, s0.x, 16), __shfl_xor_sync(FULL, s0.y, 16)));
+            a[4 + q] = fma2(WK1, t, f2(__shfl_xor_sync(FULL, s1.x, 16), __shfl_xor_sync(FULL, s1.y, 16)));
           }
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float snd = u8 ? a[c] : a[8 + c], kp = u8 ? a[8 + c] : a[c];
-            a[c] = kp + __shfl_xor_sync(FULL, snd, 8);
+          for (int q = 0; q < 4; ++q) {
+            const float2 snd = u8 ? a[q] : a[4 + q], kp = u8 ? a[4 + q] : a[q];
+            a[q] = add2(kp, f2(__shfl_xor_sync(FULL, snd.x, 8), __shfl_xor_sync(FULL, snd.y, 8)));
           }
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float snd = u4 ? a[c] : a[4 + c], kp = u4 ? a[4 + c] : a[c];
-            a[c] = kp + __shfl_xor_sync(FULL, snd, 4);
+          for (int q = 0; q < 2; ++q) {
+            const float2 snd = u4 ? a[q] : a[2 + q], kp = u4 ? a[2 + q] : a[q];
+            a[q] = add2(kp, f2(__shfl_xor_sync(FULL, snd.x, 4), __shfl_xor_sync(FULL, snd.y, 4)));
           }
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const float snd = u2 ? a[c] : a[2 + c], kp = u2 ? a[2 + c] : a[c];
-            a[c] = kp + __shfl_xor_sync(FULL, snd, 2);
+          {
+            const float2 snd = u2 ? a[0] : a[1], kp = u2 ? a[1] : a[0];
+            a[0] = add2(kp, f2(__shfl_xor_sync(FULL, snd.x, 2), __shfl_xor_sync(FULL, snd.y, 2)));
           }
-          a[0] = (u1 ? a[1] : a[0]) + __shfl_xor_sync(FULL, u1 ? a[0] : a[1], 1);
+          const float res = (u1 ? a[0].y : a[0].x) + __shfl_xor_sync(FULL, u1 ? a[0].x : a[0].y, 1);
           const int ii = (int)((lk >> (u8 ? 8 : 0)) & 0xffu);
           const int jj = (int)((lk >> (u16 ? 24 : 16)) & 0xffu);
-          red_add(gtex + (jj * T + ii) * 8 + (lane & 7), a[0]);
+          red_add(gtex + (jj * T + ii) * 8 + (lane & 7), res);
         }
       }
     }

@@ -97,11 +97,16 @@ __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Recor
           if (ok) {
             const TexSample ts_ = tex_setup(f.u, f.v, T);
             float x[8];
-            tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x, nullptr);
+            tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x);
             normal_map(r, x);
             const float w = f.alpha * Tr;
+            const float2 W2 = f2(w, w);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) X[c] = fmaf(w, x[c], X[c]);
+            for (int q = 0; q < 4; ++q) {
+              const float2 o = fma2(W2, f2(x[2 * q], x[2 * q + 1]), f2(X[2 * q], X[2 * q + 1]));
+              X[2 * q] = o.x;
+              X[2 * q + 1] = o.y;
+            }
             Acc += w;
             Tr = Tr * (1.f - f.alpha);
             last = (int)(c0 + t);

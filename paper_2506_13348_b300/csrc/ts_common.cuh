@@ -89,10 +89,12 @@ struct ViewTable {
 // coordinates (x' = x + 0.5 - cx, y' = y + 0.5 - cy): u = h_u.x / h_w.x,
 // v = h_v.x / h_w.x with x = (x', y', 1) (closed-form ray-splat
 // intersection, Sec. 3.1).  tu, tv, nf: world-space tangent frame with the
-// normal turned towards the camera (for normal mapping, Eq. 7).
+// normal turned towards the camera (for normal mapping, Eq. 7).  The h_u and
+// h_v coefficients are interleaved so that (u, v) numerators evaluate as
+// channel pairs from adjacent registers.
 struct Record {
-  float4 r0;  // hu0 hu1 hu2 hv0
-  float4 r1;  // hv1 hv2 hw0 hw1
+  float4 r0;  // hu0 hv0 hu1 hv1
+  float4 r1;  // hu2 hv2 hw0 hw1
   float4 r2;  // hw2 opacity tu0 tu1
   float4 r3;  // tu2 tv0 tv1 tv2
   float4 r4;  // nf0 nf1 nf2 (splat id bits)
@@ -109,6 +111,15 @@ __device__ __forceinline__ int find_view_item(const ViewTable& vt, int item) {
   while (v + 1 < vt.n_views && vt.v[v + 1].item_off <= item) ++v;
   return v;
 }
+
+// ---- paired FP32 (sm_100+ float2 ops) -----------------------------------------
+// One instruction for two lanes of arithmetic; per component the rounding is
+// that of the scalar fmaf / __fmul_rn / __fadd_rn, so a paired expression gives
+// bit-identical results to the same scalar expression.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // ---- texel loads (stored dtype -> float32) ----------------------------------
 __device__ __forceinline__ void load_texel(const void* base, int dtype, long long idx, float out[8]) {

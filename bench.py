@@ -274,6 +274,9 @@ def run_ours(args):
     dom_flops = flops_bwd if dom == "raster_bwd" else flops_fwd
     achieved = dom_flops / (dom_ms / 1e3) / 1e12
     traffic = read_traffic(dom)
+    # measured FP32 FMA rate of this GPU (after the timed region): context for
+    # the derived peak above
+    meas_scalar, meas_paired = _lib.measure_fp32_peak(local)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -287,7 +290,10 @@ def run_ours(args):
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                          "peak_note": f"FP32 FMA peak {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                       f"(clock from {peak_kind} peaks)",
-                         "flops_per_launch": dom_flops, "ms_per_launch": dom_ms},
+                         "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
+                         "peak_measured": {"scalar_fma_tflops": round(meas_scalar, 2),
+                                           "paired_fma_tflops": round(meas_paired, 2),
+                                           "frac_of_measured_scalar": achieved / meas_scalar}},
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "fragments_per_view": {k: int(v) for k, v in fr.items()},
             "gpu_launches": int(launches),

@@ -296,14 +296,25 @@ int64_t ts_launch_count(void);
 
 /* Turns per-stage CUDA-event timing on (1) or off (0).  While on, each
  * pipeline stage (preprocess, sort_splats, scan_counts, emit_pairs,
- * sort_pairs, tile_ranges, raster_fwd, raster_bwd, preprocess_bwd, l1_loss)
- * records an event pair on the stream it runs on. */
+ * sort_pairs, tile_ranges, raster_fwd, shade_bwd, raster_bwd,
+ * preprocess_bwd, l1_loss, adam) records an event pair on the stream it
+ * runs on. */
 ts_status ts_profile_enable(int on);
 
 /* Waits for the recorded events, writes one line per stage
  * "name launches total_ms\n" into buf (NUL-terminated, truncated to buflen)
  * and clears the records. */
 ts_status ts_profile_report(char* buf, size_t buflen);
+
+/* Measures the device's FP32 FMA rate in TFLOP/s (2 FLOP per FMA), the
+ * denominator of the rasterisers' arithmetic roofline: independent fmaf
+ * chains (*scalar_tflops) and float2 fma pairs (*paired_tflops) on every
+ * lane of a full-occupancy grid, best of three ~10 ms runs after a warm-up.
+ * Runs on the legacy default stream of `device` and synchronises it;
+ * allocates and frees a small device buffer.  Not part of the paper's
+ * method: a measurement utility.  Returns TS_ERR_ARG for null outputs,
+ * TS_ERR_CUDA on any CUDA error. */
+ts_status ts_measure_fp32_peak(int device, double* scalar_tflops, double* paired_tflops);
 
 /* ---- errors ---------------------------------------------------------------- */
 

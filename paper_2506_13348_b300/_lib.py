@@ -22,7 +22,7 @@ EXPORTED = [
     "ts_launch_count", "ts_profile_enable", "ts_profile_report", "ts_last_error", "ts_version",
     "ts_render_noalloc", "ts_scene_info", "ts_server_create", "ts_server_destroy", "ts_server_submit",
     "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
-    "ts_adam_update",
+    "ts_adam_update", "ts_measure_fp32_peak",
 ]
 
 
@@ -97,6 +97,7 @@ def lib() -> C.CDLL:
         "ts_server_wait": [vp, C.c_uint64, vp, i32, C.c_double],
         "ts_server_stats": [vp, C.POINTER(TsServeStats)],
         "ts_server_reset_stats": [vp],
+        "ts_measure_fp32_peak": [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -136,3 +137,10 @@ def profile_report() -> dict:
         name, n, ms = line.split()
         out[name] = (int(n), float(ms))
     return out
+
+
+def measure_fp32_peak(device: int = 0) -> tuple[float, float]:
+    """(scalar, paired) FP32 FMA rate of the device in TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    check(lib().ts_measure_fp32_peak(device, C.byref(a), C.byref(b)), "ts_measure_fp32_peak")
+    return a.value, b.value

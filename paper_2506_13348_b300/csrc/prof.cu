@@ -60,7 +60,99 @@ ProfScope::~ProfScope() {
 
 using namespace ts;
 
+// FP32 FMA-rate probe: eight independent fmaf chains per thread (scalar) or
+// four float2 chains (paired), on a grid of 8 CTAs x 256 threads per SM.
+// The chains converge to a fixed point, so values stay finite; the final
+// store is conditional on a value the chains never reach, which keeps the
+// compiler from removing them.
+constexpr int FP_THREADS = 256;
+constexpr int FP_UNROLL = 16;
+
+__global__ void __launch_bounds__(FP_THREADS) k_fma_scalar(float* out, int iters, float seed) {
+  float a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = seed * (float)(threadIdx.x + i);
+  const float m = 0.999999f, c = 1e-7f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < FP_UNROLL; ++u) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = fmaf(a[i], m, c);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += a[i];
+  if (s == -1.0f) out[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(FP_THREADS) k_fma_paired(float* out, int iters, float seed) {
+  float2 a[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] = f2(seed * (float)(threadIdx.x + i), seed * (float)(threadIdx.x + 4 + i));
+  const float2 m = f2(0.999999f, 0.999999f), c = f2(1e-7f, 1e-7f);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < FP_UNROLL; ++u) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = fma2(a[i], m, c);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s += a[i].x + a[i].y;
+  if (s == -1.0f) out[blockIdx.x] = s;
+}
+
 extern "C" {
+
+ts_status ts_measure_fp32_peak(int device, double* scalar_tflops, double* paired_tflops) {
+  if (!scalar_tflops || !paired_tflops) return TS_ERR_ARG;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return TS_ERR_CUDA;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const int grid = sms * 8, iters = 2048;
+  const double flops = 2.0 * grid * FP_THREADS * (double)iters * FP_UNROLL * 8;
+  float* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ts_status st = TS_OK;
+  if (cudaMalloc(&out, grid * sizeof(float)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    st = TS_ERR_CUDA;
+  } else {
+    for (int kind = 0; kind < 2 && st == TS_OK; ++kind) {
+      float best = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {  // first run warms up
+        cudaEventRecord(e0, 0);
+        if (kind == 0)
+          k_fma_scalar<<<grid, FP_THREADS>>>(out, iters, 1e-3f);
+        else
+          k_fma_paired<<<grid, FP_THREADS>>>(out, iters, 1e-3f);
+        cudaEventRecord(e1, 0);
+        note_launches(1);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          st = TS_ERR_CUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+      }
+      const double tf = flops / (best * 1e-3) / 1e12;
+      if (kind == 0)
+        *scalar_tflops = tf;
+      else
+        *paired_tflops = tf;
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) st = TS_ERR_CUDA;
+  if (out) cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaSetDevice(prev);
+  return st;
+}
 
 int64_t ts_launch_count(void) { return g_launches.load(); }
 

@@ -37,3 +37,5 @@ def test_error_path_without_gpu_or_bad_args():
     assert L.ts_create_scene(None, 0) == 1
     assert L.ts_last_error()
     assert L.ts_render(None, None, None, None, None) != 0
+    # null outputs of the FP32 rate probe are rejected before any device work
+    assert L.ts_measure_fp32_peak(0, None, None) == 1

@@ -133,3 +133,39 @@ def test_reduced_precision_atlas_pipeline_parity(P, store):
     sc, out, saved = gpu_render(P, scene, env, cam, store=store)
     ref = R.render(dict(scene, texels=rounded), cam, env)
     compare_image(out, ref)
+
+
+def test_fragment_counts_match_oracle(P):
+    """The counting pass behind the bench's FLOP model (E evaluated, C blended
+    fragments) counts what the oracle's definition counts."""
+    scene = sg.make_scene(0)
+    env = sg.make_env(0)
+    cam = sg.look_at_camera((4.0, 0.0, 0.0), 128, 128)
+    kl = K.build_keys(scene, cam)
+    sc, out, saved = gpu_render(P, scene, env, cam)
+    st = saved.frag_stats()
+    ref = R.render(scene, cam, env, keylist=kl)
+    amb = ref["ambiguous"].numpy()
+    tiles_x = kl["view"]["tiles_x"]
+    yy, xx = np.meshgrid(np.arange(128), np.arange(128), indexing="ij")
+    rng = kl["tile_ranges"][(yy // 16) * tiles_x + xx // 16]
+    list_len = rng[..., 1] - rng[..., 0]
+    slack = int(list_len[amb].sum())  # ambiguous pixels may count differently
+    e_ref = int(ref["n_eval"].sum())
+    c_ref = int(ref["n_contrib"].sum())
+    assert st["n_pairs"] == kl["ids"].size
+    assert st["n_visible"] == int(kl["view"]["visible"].sum())
+    assert e_ref > 1000 and c_ref > 1000
+    assert abs(st["n_evaluated"] - e_ref) <= slack, (st, e_ref, slack)
+    assert abs(st["n_blended"] - c_ref) <= slack, (st, c_ref, slack)
+    e_ok = int(ref["n_eval"].numpy()[~amb].sum())
+    assert e_ok <= st["n_evaluated"] <= e_ok + slack
+
+
+def test_fp32_rate_probe(P):
+    """The measured FP32 FMA rate (roofline denominator) is plausible for one
+    B300-class GPU: 128 FP32 lanes x 148 SMs x ~2 GHz ~ 77 TFLOP/s."""
+    from paper_2506_13348_b300 import _lib
+    scalar, paired = _lib.measure_fp32_peak(0)
+    assert 20.0 < scalar < 120.0, scalar
+    assert 20.0 < paired < 240.0, paired

@@ -1,7 +1,8 @@
 // Backward rasteriser: one CTA per 16x16 tile, one thread per pixel.
 //
-// Prologue: the shading adjoint (Eq. 10-12) turns dL/drgba into dL/dX (the
-// 8 G-buffer channels) and dL/dA, scattering environment gradients.
+// Input: dL/dX (the 8 G-buffer channels) and dL/dA per pixel, written by the
+// shading adjoint (Eq. 10-12, k_shade_bwd), plus the forward's saved
+// transmittance and last blended index per pixel.
 // Main loop: each warp (an 8x4 pixel block) walks the tile's list back to
 // front on its own, from the last fragment any of its pixels blended, with
 // no block-wide barrier.  Each fragment's (u,v), alpha and texel value are

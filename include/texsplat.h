@@ -200,6 +200,42 @@ ts_status ts_adam_update(float* param, float* grad, float* m, float* v, int64_t 
  * ([n][T][T][8] in that dtype); valid until the atlas is re-uploaded. */
 ts_status ts_scene_texels(ts_scene* scene, void** texels, int* T, int* dtype);
 
+/* ---- hardware-texture atlas (test-time sampling) ------------------------- */
+
+/* Texture samplers of the forward render (ts_scene_set_sampler). */
+enum { TS_SAMPLER_SOFTWARE = 0, TS_SAMPLER_HW_ATLAS = 1, TS_SAMPLER_FLAT = 2 };
+
+/* Builds the 2-D texture atlases of supplementary Sec. 1 ("Texture Atlas"):
+ * the scene's T x T charts packed row-major by splat id into two 4-channel
+ * 2-D textures (channels 0-3: albedo, metallic; 4-7: roughness, tangent
+ * normal), each a CUDA array sampled through a texture object with linear
+ * filtering and clamp addressing, plus the indirection buffer splat -> chart
+ * origin.  The atlas is near square with a power-of-two width (so texel
+ * coordinates stay small and exact in FP32).  store: TS_F32 (16 B per texel
+ * per atlas) or TS_F16 (8 B).  Reads the stored texels as they are now: an
+ * atlas upload invalidates it (TS_ERR_STATE on a hardware-sampled render
+ * until rebuilt); in-place texel updates through ts_scene_texels do not, so
+ * rebuild after them.  Synchronises `stream`.  Errors: TS_ERR_ARG (NULL
+ * scene, other store), TS_ERR_STATE (no or stale texels), TS_ERR_CAPACITY
+ * (more charts than the device's largest 2-D surface holds), TS_ERR_OOM,
+ * TS_ERR_CUDA.  Library-owned; freed with the scene. */
+ts_status ts_scene_build_atlas2d(ts_scene* scene, ts_dtype store, void* stream);
+
+/* Selects how forward renders of `scene` sample its textures:
+ *   TS_SAMPLER_SOFTWARE (default): bilinear filter (Eq. 6) in FP32 from the
+ *     per-splat chart layout -- the parity path, with backward;
+ *   TS_SAMPLER_HW_ATLAS: tex2D on the 2-D atlases (needs
+ *     ts_scene_build_atlas2d); the texture unit's bilinear weights have 8
+ *     fractional bits, so results differ from the definition by up to about
+ *     2^-9 of the texel differences per axis (a reported-error path);
+ *   TS_SAMPLER_FLAT: one attribute vector per splat (texel (0, 0) of its
+ *     chart) without texture lookup: the untextured baseline the paper's
+ *     Table 3 compares against.
+ * The hardware and flat samplers are inference-only: a render that asks for
+ * saved state returns TS_ERR_STATE, as does a batch whose scenes use
+ * different samplers (TS_ERR_ARG).  Returns TS_ERR_ARG for an unknown value. */
+ts_status ts_scene_set_sampler(ts_scene* scene, int sampler);
+
 /* Overwrites the scene's geometry (same n as uploaded) from device arrays,
  * stream-ordered without synchronisation (for updates between training
  * steps).  Layouts as in ts_upload_gaussians. */

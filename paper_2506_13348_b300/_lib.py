@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtexsplat.so")
 
 TS_F32, TS_BF16, TS_F16 = 0, 1, 2
+SAMPLERS = {"software": 0, "hw_atlas": 1, "flat": 2}
 STATUS = {0: "TS_OK", 1: "TS_ERR_ARG", 2: "TS_ERR_OOM", 3: "TS_ERR_CAPACITY", 4: "TS_ERR_CUDA",
           5: "TS_ERR_TIMEOUT", 6: "TS_ERR_STATE"}
 
@@ -22,7 +23,7 @@ EXPORTED = [
     "ts_launch_count", "ts_profile_enable", "ts_profile_report", "ts_last_error", "ts_version",
     "ts_render_noalloc", "ts_scene_info", "ts_server_create", "ts_server_destroy", "ts_server_submit",
     "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
-    "ts_adam_update", "ts_measure_fp32_peak",
+    "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
 ]
 
 
@@ -98,6 +99,8 @@ def lib() -> C.CDLL:
         "ts_server_stats": [vp, C.POINTER(TsServeStats)],
         "ts_server_reset_stats": [vp],
         "ts_measure_fp32_peak": [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "ts_scene_build_atlas2d": [vp, i32, vp],
+        "ts_scene_set_sampler": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)

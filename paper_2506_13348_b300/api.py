@@ -88,6 +88,16 @@ class Scene:
               "ts_upload_atlas")
         self.T = T
 
+    def build_atlas2d(self, store="f32", stream=None):
+        """Packs the charts into the 2-D hardware-texture atlases (supplementary Sec. 1)."""
+        check(lib().ts_scene_build_atlas2d(self.handle, DTYPES[store], _stream(stream)), "ts_scene_build_atlas2d")
+
+    def set_sampler(self, sampler: str):
+        """'software' (default), 'hw_atlas' (tex2D on the 2-D atlases) or 'flat'
+        (one attribute vector per splat, the untextured baseline)."""
+        from ._lib import SAMPLERS
+        check(lib().ts_scene_set_sampler(self.handle, SAMPLERS[sampler]), "ts_scene_set_sampler")
+
     def upload_envmap(self, env: dict, store="f32", stream=None):
         dev = torch.device("cuda", self.device)
         spec = [_dev_f32(m, dev) for m in env["spec"]]

@@ -99,6 +99,14 @@ struct ts_scene {
   int cube_dtype = 0;
   float* lut = nullptr;
   int lut_res = 0;
+  int64_t tex_version = 0;  // bumped by every ts_upload_atlas
+  // 2-D hardware-texture atlases (supplementary Sec. 1) and the indirection buffer
+  cudaArray_t a2d[2] = {nullptr, nullptr};
+  cudaTextureObject_t a2d_tex[2] = {0, 0};
+  uint2* chart = nullptr;
+  int64_t a2d_version = -1;  // tex_version the 2-D atlases were built from
+  int64_t a2d_n = -1;
+  int sampler = SMP_SOFTWARE;
 };
 
 struct ts_saved {
@@ -117,10 +125,24 @@ struct ts_saved {
 
 int ts::set_error(int code, const std::string& msg) { return fail(code, msg); }
 
+static void free_atlas2d(ts_scene* s) {
+  for (int i = 0; i < 2; ++i) {
+    if (s->a2d_tex[i]) cudaDestroyTextureObject(s->a2d_tex[i]);
+    if (s->a2d[i]) cudaFreeArray(s->a2d[i]);
+    s->a2d_tex[i] = 0;
+    s->a2d[i] = nullptr;
+  }
+  if (s->chart) cudaFree(s->chart);
+  s->chart = nullptr;
+  s->a2d_version = -1;
+  s->a2d_n = -1;
+}
+
 static void free_scene_buffers(ts_scene* s) {
   void* ptrs[] = {s->means, s->quats, s->scales, s->opacity, s->texels, s->spec, s->irr, s->lut};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  free_atlas2d(s);
 }
 
 extern "C" {
@@ -204,6 +226,7 @@ ts_status ts_upload_atlas(ts_scene* s, int T, int C, ts_dtype store, const float
   TS_CUDA(cudaStreamSynchronize(st));
   if (s->texels) cudaFree(s->texels);
   s->texels = nullptr;
+  s->tex_version += 1;  // any 2-D atlas built from the old texels is stale
   const long long count = (long long)s->n * T * T * 8;
   const size_t esz = store == TS_F32 ? 4 : 2;
   TS_CUDA(cudaMalloc(&s->texels, std::max<size_t>((size_t)count * esz, 16)));
@@ -324,7 +347,15 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     if (scenes[i]->device != device) return fail(TS_ERR_ARG, "ts_render_views: scenes on different devices");
     if (scenes[i]->tex_dtype != scenes[0]->tex_dtype)
       return fail(TS_ERR_ARG, "ts_render_views: views of one batch must share the atlas dtype");
+    if (scenes[i]->sampler != scenes[0]->sampler)
+      return fail(TS_ERR_ARG, "ts_render_views: views of one batch must share the texture sampler");
+    if (scenes[i]->sampler == SMP_HW_ATLAS &&
+        (!scenes[i]->a2d_tex[0] || scenes[i]->a2d_version != scenes[i]->tex_version || scenes[i]->a2d_n != scenes[i]->n))
+      return fail(TS_ERR_STATE, "ts_render_views: hardware sampler selected but the 2-D atlas is missing or stale");
   }
+  const int sampler = scenes[0]->sampler;
+  if (sampler != SMP_SOFTWARE && saved_out)
+    return fail(TS_ERR_STATE, "ts_render_views: the hardware-atlas and flat samplers are inference-only (no saved state)");
   cudaStream_t st = (cudaStream_t)stream;
   TS_CUDA(cudaSetDevice(device));
 
@@ -348,6 +379,9 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     V.n_splats = (int)s->n;
     V.means = s->means; V.quats = s->quats; V.scales = s->scales; V.opacity = s->opacity;
     V.texels = s->texels; V.T = s->T; V.tex_dtype = s->tex_dtype;
+    V.atlas2d[0] = s->a2d_tex[0];
+    V.atlas2d[1] = s->a2d_tex[1];
+    V.chart = s->chart;
     fill_env(s, V.env);
     V.rgba = reinterpret_cast<float4*>(out_rgba[i]);
     tiles += (long long)V.tiles_x * V.tiles_y;
@@ -481,7 +515,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   }
   {
     ProfScope p(st, "raster_fwd");
-    launch_raster_fwd(vt, rec, pitems, ranges, scenes[0]->tex_dtype, saved_out != nullptr, nullptr, st);
+    launch_raster_fwd(vt, rec, pitems, ranges, scenes[0]->tex_dtype, saved_out != nullptr, nullptr, sampler, st);
   }
   TS_CHECK_LAUNCH();
 
@@ -616,7 +650,7 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   unsigned long long* d = nullptr;
   TS_CUDA(tmp.alloc((void**)&d, 2 * sizeof(unsigned long long)));
   TS_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st));
-  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, st);
+  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, SMP_SOFTWARE, st);
   TS_CHECK_LAUNCH();
   unsigned long long h[2] = {0, 0};
   TS_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -632,6 +666,84 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   int64_t vis = 0;
   for (uint32_t b : hb) vis += (b != 0xffffffffu);
   out->n_visible = vis;
+  return TS_OK;
+}
+
+ts_status ts_scene_build_atlas2d(ts_scene* s, ts_dtype store, void* stream) {
+  if (!s) return fail(TS_ERR_ARG, "ts_scene_build_atlas2d: scene is NULL");
+  if (store != TS_F32 && store != TS_F16) return fail(TS_ERR_ARG, "ts_scene_build_atlas2d: store must be TS_F32 or TS_F16");
+  if (!s->texels || s->tex_n != s->n) return fail(TS_ERR_STATE, "ts_scene_build_atlas2d: atlas missing or stale");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(s->device));
+  TS_CUDA(cudaStreamSynchronize(st));
+  free_atlas2d(s);
+  const int T = s->T;
+  const long long n = std::max<long long>(s->n, 1);
+  int max_w = 0, max_h = 0;
+  TS_CUDA(cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxSurface2DWidth, s->device));
+  TS_CUDA(cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxSurface2DHeight, s->device));
+  // near-square atlas (power-of-two width): small texel coordinates keep FP32
+  // sub-texel precision well below the filter's 1/256 weight step
+  long long w = T;
+  while (w * 2 <= max_w && w * w < n * T * T) w *= 2;
+  long long charts_x = w / T, rows = (n + charts_x - 1) / charts_x;
+  while (rows * T > max_h && w * 2 <= max_w) {
+    w *= 2;
+    charts_x = w / T;
+    rows = (n + charts_x - 1) / charts_x;
+  }
+  if (rows * T > max_h) return fail(TS_ERR_CAPACITY, "ts_scene_build_atlas2d: too many charts for one 2-D texture");
+  const int W = (int)w, H = (int)(rows * T);
+  const cudaChannelFormatDesc desc =
+      store == TS_F32 ? cudaCreateChannelDesc<float4>() : cudaCreateChannelDescHalf4();
+  cudaSurfaceObject_t surf[2] = {0, 0};
+  ts_status r = TS_OK;
+  for (int i = 0; i < 2 && r == TS_OK; ++i) {
+    if (cudaMallocArray(&s->a2d[i], &desc, W, H, cudaArraySurfaceLoadStore) != cudaSuccess) {
+      r = fail(TS_ERR_OOM, "ts_scene_build_atlas2d: array allocation failed");
+      break;
+    }
+    cudaResourceDesc res;
+    memset(&res, 0, sizeof(res));
+    res.resType = cudaResourceTypeArray;
+    res.res.array.array = s->a2d[i];
+    if (cudaCreateSurfaceObject(&surf[i], &res) != cudaSuccess) {
+      r = fail(TS_ERR_CUDA, "ts_scene_build_atlas2d: surface creation failed");
+      break;
+    }
+    cudaTextureDesc td;
+    memset(&td, 0, sizeof(td));
+    td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModeLinear;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    if (cudaCreateTextureObject(&s->a2d_tex[i], &res, &td, nullptr) != cudaSuccess)
+      r = fail(TS_ERR_CUDA, "ts_scene_build_atlas2d: texture creation failed");
+  }
+  if (r == TS_OK && cudaMalloc(&s->chart, (size_t)n * sizeof(uint2)) != cudaSuccess)
+    r = fail(TS_ERR_OOM, "ts_scene_build_atlas2d: indirection buffer allocation failed");
+  if (r == TS_OK && s->n > 0) {
+    launch_pack_atlas2d(s->texels, s->tex_dtype, s->n, T, (int)charts_x, surf[0], surf[1], s->chart,
+                        store == TS_F16 ? 1 : 0, st);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      r = fail(TS_ERR_CUDA, "ts_scene_build_atlas2d: packing failed");
+  }
+  for (int i = 0; i < 2; ++i)
+    if (surf[i]) cudaDestroySurfaceObject(surf[i]);
+  if (r != TS_OK) {
+    free_atlas2d(s);
+    return r;
+  }
+  s->a2d_version = s->tex_version;
+  s->a2d_n = s->n;
+  return TS_OK;
+}
+
+ts_status ts_scene_set_sampler(ts_scene* s, int sampler) {
+  if (!s) return fail(TS_ERR_ARG, "ts_scene_set_sampler: scene is NULL");
+  if (sampler != SMP_SOFTWARE && sampler != SMP_HW_ATLAS && sampler != SMP_FLAT)
+    return fail(TS_ERR_ARG, "ts_scene_set_sampler: unknown sampler");
+  s->sampler = sampler;
   return TS_OK;
 }
 

@@ -45,8 +45,10 @@ void launch_depth_bits(const uint64_t* depth_keys_unsorted, uint32_t* out, int n
 
 // raster_fwd.cu / raster_bwd.cu
 void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats,
+                       const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
                        cudaStream_t st);
+void launch_pack_atlas2d(const void* texels, int dtype, long long n, int T, int charts_x, cudaSurfaceObject_t s0,
+                         cudaSurfaceObject_t s1, uint2* chart, int half_store, cudaStream_t st);
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
                        const GradTable& g, cudaStream_t st);

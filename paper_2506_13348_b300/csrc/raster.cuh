@@ -103,6 +103,27 @@ __device__ __forceinline__ void tex_fetch(const void* texels, long long splat, i
   }
 }
 
+// Hardware-filtered fetch (supplementary Sec. 1): the texel-centre coordinate
+// of Eq. 5 inside the splat's chart, clamped to the chart's outer texel
+// centres (clamp-to-edge as in the software path, instead of the paper's
+// formula, which bleeds half a texel into the neighbouring chart at s, t in
+// {0, 1}), offset by the chart origin from the indirection buffer and sampled
+// by tex2D with linear filtering from the two 4-channel atlases.  The texture
+// unit computes the bilinear weights in fixed point (8 fractional bits).
+__device__ __forceinline__ void tex_fetch_hw(const ViewDesc& V, long long splat, int T, float u, float v,
+                                             float out[8]) {
+  const uint2 ch = V.chart[splat];
+  const float Ts6 = (float)T * (1.0f / 6.0f);
+  const float hi = (float)(T - 1);
+  const float xs = fminf(fmaxf(fmaf(u + 3.0f, Ts6, -0.5f), 0.f), hi);
+  const float ys = fminf(fmaxf(fmaf(v + 3.0f, Ts6, -0.5f), 0.f), hi);
+  const float x = (float)ch.x + 0.5f + xs, y = (float)ch.y + 0.5f + ys;
+  const float4 a = tex2D<float4>(V.atlas2d[0], x, y);
+  const float4 b = tex2D<float4>(V.atlas2d[1], x, y);
+  out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+  out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+}
+
 // Normal mapping (Eq. 7): n = [t_u, t_v, n_f] n^t, in place on x[5..7].
 __device__ __forceinline__ void normal_map(const Record& r, float x[8]) {
   float a = x[5], b = x[6], c = x[7];

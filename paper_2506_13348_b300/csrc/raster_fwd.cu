@@ -26,7 +26,7 @@
 
 namespace ts {
 
-template <int DT, bool SAVE, bool STATS>
+template <int DT, bool SAVE, bool STATS, int SMP>
 __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
                                                      const uint32_t* __restrict__ pair_items,
                                                      const uint2* __restrict__ ranges,
@@ -95,9 +95,16 @@ __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Recor
           r.r3 = __ldg(rp + 3);
           r.r4 = __ldg(rp + 4);
           if (ok) {
-            const TexSample ts_ = tex_setup(f.u, f.v, T);
+            const long long splat = (long long)__float_as_int(r.r4.w);
             float x[8];
-            tex_fetch<DT>(V.texels, (long long)__float_as_int(r.r4.w), T, ts_, x);
+            if (SMP == SMP_SOFTWARE) {
+              const TexSample ts_ = tex_setup(f.u, f.v, T);
+              tex_fetch<DT>(V.texels, splat, T, ts_, x);
+            } else if (SMP == SMP_HW_ATLAS) {
+              tex_fetch_hw(V, splat, T, f.u, f.v, x);
+            } else {
+              load_texel(V.texels, DT, splat * (long long)T * T, x);
+            }
             normal_map(r, x);
             const float w = f.alpha * Tr;
             const float2 W2 = f2(w, w);
@@ -153,16 +160,23 @@ __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Recor
 }
 
 void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats,
+                       const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
                        cudaStream_t st) {
   dim3 grid(vt.n_tiles), block(256);
-#define TS_LAUNCH(DTV)                                                                          \
-  if (stats)                                                                                    \
-    k_raster_fwd<DTV, false, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);  \
-  else if (save)                                                                                \
-    k_raster_fwd<DTV, true, false><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);  \
-  else                                                                                          \
-    k_raster_fwd<DTV, false, false><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+  if (sampler == SMP_HW_ATLAS) {  // inference only; the atlas dtype is the texture's
+    k_raster_fwd<DT_F32, false, false, SMP_HW_ATLAS><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+    note_launches(1);
+    return;
+  }
+#define TS_LAUNCH(DTV)                                                                                    \
+  if (sampler == SMP_FLAT)                                                                                \
+    k_raster_fwd<DTV, false, false, SMP_FLAT><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
+  else if (stats)                                                                                         \
+    k_raster_fwd<DTV, false, true, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
+  else if (save)                                                                                          \
+    k_raster_fwd<DTV, true, false, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
+  else                                                                                                    \
+    k_raster_fwd<DTV, false, false, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
   if (tex_dtype == DT_F32) {
     TS_LAUNCH(DT_F32)
   } else if (tex_dtype == DT_BF16) {
@@ -171,6 +185,44 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
     TS_LAUNCH(DT_F16)
   }
 #undef TS_LAUNCH
+  note_launches(1);
+}
+
+// Packs the stored charts ([n][T][T][8], any dtype) into the two 4-channel
+// 2-D atlases: chart k at texel origin ((k mod charts_x) T, (k div charts_x) T),
+// rows indexing t (v) and columns s (u), and records the origin per splat.
+__global__ void k_pack_atlas2d(const void* __restrict__ texels, int dtype, long long n, int T, int charts_x,
+                               cudaSurfaceObject_t s0, cudaSurfaceObject_t s1, uint2* __restrict__ chart,
+                               int half_store) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tt = (long long)T * T;
+  if (i >= n * tt) return;
+  const long long k = i / tt;
+  const int r = (int)(i - k * tt), jj = r / T, ii = r - jj * T;
+  float v[8];
+  load_texel(texels, dtype, i, v);
+  const int cx = (int)(k % charts_x) * T, cy = (int)(k / charts_x) * T;
+  const int x = cx + ii, y = cy + jj;
+  if (half_store) {
+    const ushort4 a = make_ushort4(__half_as_ushort(__float2half_rn(v[0])), __half_as_ushort(__float2half_rn(v[1])),
+                                   __half_as_ushort(__float2half_rn(v[2])), __half_as_ushort(__float2half_rn(v[3])));
+    const ushort4 b = make_ushort4(__half_as_ushort(__float2half_rn(v[4])), __half_as_ushort(__float2half_rn(v[5])),
+                                   __half_as_ushort(__float2half_rn(v[6])), __half_as_ushort(__float2half_rn(v[7])));
+    surf2Dwrite(a, s0, x * (int)sizeof(ushort4), y);
+    surf2Dwrite(b, s1, x * (int)sizeof(ushort4), y);
+  } else {
+    surf2Dwrite(make_float4(v[0], v[1], v[2], v[3]), s0, x * (int)sizeof(float4), y);
+    surf2Dwrite(make_float4(v[4], v[5], v[6], v[7]), s1, x * (int)sizeof(float4), y);
+  }
+  if (r == 0) chart[k] = make_uint2((unsigned)cx, (unsigned)cy);
+}
+
+void launch_pack_atlas2d(const void* texels, int dtype, long long n, int T, int charts_x, cudaSurfaceObject_t s0,
+                         cudaSurfaceObject_t s1, uint2* chart, int half_store, cudaStream_t st) {
+  const long long total = n * (long long)T * T;
+  if (total <= 0) return;
+  k_pack_atlas2d<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(texels, dtype, n, T, charts_x, s0, s1, chart,
+                                                                   half_store);
   note_launches(1);
 }
 

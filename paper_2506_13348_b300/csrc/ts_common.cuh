@@ -37,6 +37,13 @@ constexpr int kRecGradStride = 14;
 
 enum Dtype : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
 
+// Texture sampler of the forward rasteriser.
+//   SMP_SOFTWARE: bilinear filter (Eq. 6) in FP32 from the per-splat chart layout;
+//   SMP_HW_ATLAS: tex2D on 2-D hardware-texture atlases (supplementary Sec. 1);
+//   SMP_FLAT:     one attribute vector per splat (texel (0, 0) of its chart), no
+//                 texture lookup -- the untextured baseline of the paper's Table 3.
+enum Sampler : int { SMP_SOFTWARE = 0, SMP_HW_ATLAS = 1, SMP_FLAT = 2 };
+
 // Environment light (Eq. 11-12): specular mip chain, irradiance cube, BRDF LUT.
 struct EnvDesc {
   const void* spec[MAX_LEVELS];  // [6][R_l][R_l][3]
@@ -67,6 +74,10 @@ struct ViewDesc {
   const void* texels;
   int T;
   int tex_dtype;
+  // 2-D atlases for SMP_HW_ATLAS: channels 0-3 and 4-7, and each splat's
+  // chart origin (texels) -- the indirection buffer of supplementary Sec. 1
+  cudaTextureObject_t atlas2d[2];
+  const uint2* chart;
   EnvDesc env;
   // outputs / saved state
   float4* rgba;   // [H][W]

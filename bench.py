@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the reduced-precision atlas measurement")
     ap.add_argument("--precision-only", action="store_true")
     ap.add_argument("--precision-samples", type=int, default=64)
+    ap.add_argument("--no-sampling", action="store_true", help="skip the texture-sampler comparison (Table 3 shape)")
+    ap.add_argument("--sampling-only", action="store_true")
+    ap.add_argument("--sampling-views", type=int, default=40)
     return ap.parse_args()
 
 
@@ -309,6 +312,8 @@ def run_ours(args):
         line["large_scene"] = run_large_scene(args, local)
     if rank == 0 and not args.no_precision:
         line["precision"] = run_precision(args, local)
+    if rank == 0 and not args.no_sampling:
+        line["texture_sampling"] = run_sampling(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, thr, px = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -595,11 +600,75 @@ def read_traffic(kernel: str):
     return ent.get("dram_bytes_per_launch")
 
 
+def run_sampling(args, device):
+    """The shape of the paper's Table 3: forward-render throughput of textured
+    splats relative to the same splats without textures, for T = 2, 4, 8, 16,
+    with the software bilinear filter (FP32 charts) and with the hardware
+    texture units (FP32 2-D atlases, tex2D).  Geometry, environment and
+    cameras of the 200k-splat 800x800 workload; the untextured baseline
+    renders one attribute vector per splat (flat sampler, T = 1).  Each
+    figure is views per second over the same views."""
+    import torch
+
+    import paper_2506_13348_b300 as P
+    import scenegen as sg
+
+    dev = torch.device("cuda", device)
+    geo = sg.make_scene(1, with_texels=False)
+    env = sg.make_env(1, cube_res=32, levels=1, irr_res=8, lut_res=128)
+    cams = sg.fibonacci_cameras(N_CAMS, 4.0, RES, RES)
+    nv = max(4, args.sampling_views)
+    img = torch.empty(RES, RES, 4, device=dev)
+
+    def fps(sc):
+        for i in range(3):
+            P.render(sc, cams[i], out=img)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(nv):
+            P.render(sc, cams[i % N_CAMS], out=img)
+        e1.record()
+        torch.cuda.synchronize()
+        return nv / (e0.elapsed_time(e1) / 1e3)
+
+    def scene_with(T):
+        sc = P.Scene(device)
+        sc.upload_gaussians(geo["means"], geo["quats"], geo["scales"], geo["opacity"])
+        sc.upload_atlas(sg.scenes.texels_torch(len(geo["opacity"]), T, seed=1, device=dev), "f32")
+        sc.upload_envmap(env, "f32")
+        return sc
+
+    sc = scene_with(1)
+    sc.set_sampler("flat")
+    base = fps(sc)
+    sc.close()
+    out = {"workload": "200k splats (cfg1 geometry), 800x800, forward render, views/s over "
+                       f"{nv} views; FP32 charts (software) vs FP32 2-D atlases (tex2D)",
+           "untextured_fps": base,
+           "paper_table3_ratios": {"software": [0.90, 0.86, 0.85, 0.79], "hardware": [0.92, 0.93, 0.94, 0.91]}}
+    for T in (2, 4, 8, 16):
+        sc = scene_with(T)
+        sw = fps(sc)
+        P.render(sc, cams[0], out=img)
+        ref = img.clone()
+        sc.build_atlas2d("f32")
+        sc.set_sampler("hw_atlas")
+        hw = fps(sc)
+        P.render(sc, cams[0], out=img)
+        d = (img - ref).abs()[..., :3]
+        sc.close()
+        torch.cuda.empty_cache()
+        out[f"T{T}"] = {"software_fps": sw, "hardware_fps": hw, "software_ratio": sw / base, "hardware_ratio": hw / base,
+                        "hw_vs_software_rgb": {"max_abs": float(d.max()), "mean_abs": float(d.mean())}}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.serve_only or args.large_only or args.precision_only:
+    if args.serve_only or args.large_only or args.precision_only or args.sampling_only:
         import torch
         torch.cuda.set_device(dist_env()[2])
         res = {}
@@ -609,6 +678,8 @@ def main():
             res["large_scene"] = run_large_scene(args, dist_env()[2])
         if args.precision_only:
             res["precision"] = run_precision(args, dist_env()[2])
+        if args.sampling_only:
+            res["texture_sampling"] = run_sampling(args, dist_env()[2])
         print(json.dumps(res))
         return 0
     return run_ours(args)

@@ -17,6 +17,9 @@ Modules
   shading.py FP64 cube-map / LUT sampling and the shading function.
   grad.py    gradients of the forward by autograd (FP64) and central
              finite differences.
+  loss.py    the image term of the training loss (Sec. 3.6): 0.8 L1 +
+             0.2 (1 - SSIM), SSIM written out with an 11x11 Gaussian window,
+             and its gradient by autograd.
 
 Parity status per function is stated in each module header.
 """

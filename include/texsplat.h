@@ -200,6 +200,19 @@ ts_status ts_adam_update(float* param, float* grad, float* m, float* v, int64_t 
  * ([n][T][T][8] in that dtype); valid until the atlas is re-uploaded. */
 ts_status ts_scene_texels(ts_scene* scene, void** texels, int* T, int* dtype);
 
+/* Image term of the training loss (Sec. 3.6) over the RGB channels of
+ * [height][width][4] float32 device images (alpha ignored):
+ *   *loss = (1 - lambda) L1 + lambda (1 - SSIM),
+ * L1 = mean |rgba - target|, SSIM = mean structural similarity under an
+ * 11x11 Gaussian window (sigma 1.5, zero padding, C1 = 0.01^2,
+ * C2 = 0.03^2); the paper uses lambda = 0.2.  Writes the scalar to the
+ * device float `loss` and dL/drgba (alpha column 0) to `grad` (overwritten,
+ * not accumulated).  Stream-ordered; allocates its 36 B/pixel scratch with
+ * cudaMallocAsync on `stream`.  Errors: TS_ERR_ARG (NULL pointers, empty or
+ * > 2^28-pixel image, lambda outside [0, 1]), TS_ERR_CUDA. */
+ts_status ts_image_loss(const float* rgba, const float* target, int width, int height, float lambda_dssim,
+                        float* loss, float* grad, void* stream);
+
 /* ---- hardware-texture atlas (test-time sampling) ------------------------- */
 
 /* Texture samplers of the forward render (ts_scene_set_sampler). */

@@ -7,7 +7,7 @@ import importlib
 
 from ._lib import TexSplatError, lib  # noqa: F401
 
-_API = ("Scene", "Saved", "render", "render_views", "render_backward", "zero_grads", "l1_loss", "make_camera",
+_API = ("Scene", "Saved", "render", "render_views", "render_backward", "zero_grads", "l1_loss", "image_loss", "make_camera",
         "split_spec", "TexSplatRender", "Server", "Trainer", "adam_update", "scene_texels")
 
 

@@ -24,6 +24,7 @@ EXPORTED = [
     "ts_render_noalloc", "ts_scene_info", "ts_server_create", "ts_server_destroy", "ts_server_submit",
     "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
     "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
+    "ts_image_loss",
 ]
 
 
@@ -101,6 +102,7 @@ def lib() -> C.CDLL:
         "ts_measure_fp32_peak": [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ts_scene_build_atlas2d": [vp, i32, vp],
         "ts_scene_set_sampler": [vp, i32],
+        "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

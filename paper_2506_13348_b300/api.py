@@ -220,6 +220,15 @@ def l1_loss(rgba: torch.Tensor, target: torch.Tensor, loss: torch.Tensor, grad: 
     check(lib().ts_l1_loss(_ptr(rgba), _ptr(target), n, _ptr(loss), _ptr(grad), _stream(stream)), "ts_l1_loss")
 
 
+def image_loss(rgba: torch.Tensor, target: torch.Tensor, loss: torch.Tensor, grad: torch.Tensor,
+               lambda_dssim: float = 0.2, stream=None):
+    """(1 - lambda) L1 + lambda (1 - SSIM) of [H, W, 4] CUDA images into the
+    device scalar ``loss``; dL/drgba into ``grad`` (Sec. 3.6)."""
+    H, W = rgba.shape[0], rgba.shape[1]
+    check(lib().ts_image_loss(_ptr(rgba), _ptr(target), W, H, float(lambda_dssim), _ptr(loss), _ptr(grad),
+                              _stream(stream)), "ts_image_loss")
+
+
 def split_spec(scene: Scene, flat: torch.Tensor):
     """Split a concatenated specular-mip gradient into per-level tensors."""
     out, o = [], 0

@@ -747,6 +747,29 @@ ts_status ts_scene_set_sampler(ts_scene* s, int sampler) {
   return TS_OK;
 }
 
+ts_status ts_image_loss(const float* rgba, const float* target, int width, int height, float lambda_dssim,
+                        float* loss, float* grad, void* stream) {
+  if (!rgba || !target || !loss || !grad) return fail(TS_ERR_ARG, "ts_image_loss: NULL argument");
+  if (width < 1 || height < 1 || (long long)width * height > (1ll << 28))
+    return fail(TS_ERR_ARG, "ts_image_loss: image size out of range");
+  if (!(lambda_dssim >= 0.f && lambda_dssim <= 1.f)) return fail(TS_ERR_ARG, "ts_image_loss: lambda not in [0, 1]");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  if (set_gauss_window(dev) != 0) return fail(TS_ERR_CUDA, "ts_image_loss: window upload failed");
+  void* temp = nullptr;
+  TS_CUDA(cudaMallocAsync(&temp, image_loss_temp_bytes(width, height), st));
+  {
+    ProfScope p(st, "image_loss");
+    launch_image_loss(reinterpret_cast<const float4*>(rgba), reinterpret_cast<const float4*>(target), width, height,
+                      lambda_dssim, loss, reinterpret_cast<float4*>(grad), temp, st);
+  }
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(temp, st);
+  if (e != cudaSuccess) return fail(TS_ERR_CUDA, std::string("ts_image_loss: ") + cudaGetErrorString(e));
+  return TS_OK;
+}
+
 ts_status ts_scene_texels(ts_scene* s, void** texels, int* T, int* dtype) {
   if (!s) return fail(TS_ERR_ARG, "ts_scene_texels: scene is NULL");
   if (!s->texels) return fail(TS_ERR_STATE, "ts_scene_texels: atlas not uploaded");

@@ -66,4 +66,10 @@ void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStre
 void launch_l1_loss(const float4* rgba, const float4* target, long long n, float* loss, float4* grad,
                     cudaStream_t st);
 
+// loss.cu: image term of the training loss (L1 + D-SSIM)
+int set_gauss_window(int device);
+size_t image_loss_temp_bytes(int W, int H);
+void launch_image_loss(const float4* img, const float4* tgt, int W, int H, float lam, float* loss, float4* grad,
+                       void* temp, cudaStream_t st);
+
 }  // namespace ts

@@ -218,21 +218,30 @@ ts_status ts_image_loss(const float* rgba, const float* target, int width, int h
 /* Texture samplers of the forward render (ts_scene_set_sampler). */
 enum { TS_SAMPLER_SOFTWARE = 0, TS_SAMPLER_HW_ATLAS = 1, TS_SAMPLER_FLAT = 2 };
 
+/* Chart orders of ts_scene_build_atlas2d. */
+enum { TS_PACK_SPLAT_ID = 0, TS_PACK_MORTON = 1 };
+
 /* Builds the 2-D texture atlases of supplementary Sec. 1 ("Texture Atlas"):
- * the scene's T x T charts packed row-major by splat id into two 4-channel
+ * the scene's T x T charts packed row-major into two 4-channel
  * 2-D textures (channels 0-3: albedo, metallic; 4-7: roughness, tangent
  * normal), each a CUDA array sampled through a texture object with linear
  * filtering and clamp addressing, plus the indirection buffer splat -> chart
  * origin.  The atlas is near square with a power-of-two width (so texel
  * coordinates stay small and exact in FP32).  store: TS_F32 (16 B per texel
- * per atlas) or TS_F16 (8 B).  Reads the stored texels as they are now: an
+ * per atlas) or TS_F16 (8 B).  packing: TS_PACK_SPLAT_ID places charts in
+ * splat id order (the paper's unordered packing); TS_PACK_MORTON in the
+ * Morton order of the splat centres (30-bit code in the centres' bounding
+ * box), so splats near each other in space get neighbouring charts -- the
+ * locality-aware packing the paper names as future work.  Reads the stored
+ * texels as they are now: an
  * atlas upload invalidates it (TS_ERR_STATE on a hardware-sampled render
  * until rebuilt); in-place texel updates through ts_scene_texels do not, so
  * rebuild after them.  Synchronises `stream`.  Errors: TS_ERR_ARG (NULL
  * scene, other store), TS_ERR_STATE (no or stale texels), TS_ERR_CAPACITY
  * (more charts than the device's largest 2-D surface holds), TS_ERR_OOM,
+ * unknown packing TS_ERR_ARG,
  * TS_ERR_CUDA.  Library-owned; freed with the scene. */
-ts_status ts_scene_build_atlas2d(ts_scene* scene, ts_dtype store, void* stream);
+ts_status ts_scene_build_atlas2d(ts_scene* scene, ts_dtype store, int packing, void* stream);
 
 /* Selects how forward renders of `scene` sample its textures:
  *   TS_SAMPLER_SOFTWARE (default): bilinear filter (Eq. 6) in FP32 from the

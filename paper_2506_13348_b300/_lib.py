@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libtexsplat.so")
 
 TS_F32, TS_BF16, TS_F16 = 0, 1, 2
 SAMPLERS = {"software": 0, "hw_atlas": 1, "flat": 2}
+PACKINGS = {"splat_id": 0, "morton": 1}
 STATUS = {0: "TS_OK", 1: "TS_ERR_ARG", 2: "TS_ERR_OOM", 3: "TS_ERR_CAPACITY", 4: "TS_ERR_CUDA",
           5: "TS_ERR_TIMEOUT", 6: "TS_ERR_STATE"}
 
@@ -100,7 +101,7 @@ def lib() -> C.CDLL:
         "ts_server_stats": [vp, C.POINTER(TsServeStats)],
         "ts_server_reset_stats": [vp],
         "ts_measure_fp32_peak": [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
-        "ts_scene_build_atlas2d": [vp, i32, vp],
+        "ts_scene_build_atlas2d": [vp, i32, i32, vp],
         "ts_scene_set_sampler": [vp, i32],
         "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
     }

@@ -88,9 +88,12 @@ class Scene:
               "ts_upload_atlas")
         self.T = T
 
-    def build_atlas2d(self, store="f32", stream=None):
-        """Packs the charts into the 2-D hardware-texture atlases (supplementary Sec. 1)."""
-        check(lib().ts_scene_build_atlas2d(self.handle, DTYPES[store], _stream(stream)), "ts_scene_build_atlas2d")
+    def build_atlas2d(self, store="f32", packing="splat_id", stream=None):
+        """Packs the charts into the 2-D hardware-texture atlases (supplementary
+        Sec. 1), in splat id order or the Morton order of the splat centres."""
+        from ._lib import PACKINGS
+        check(lib().ts_scene_build_atlas2d(self.handle, DTYPES[store], PACKINGS[packing], _stream(stream)),
+              "ts_scene_build_atlas2d")
 
     def set_sampler(self, sampler: str):
         """'software' (default), 'hw_atlas' (tex2D on the 2-D atlases) or 'flat'

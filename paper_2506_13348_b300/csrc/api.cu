@@ -669,8 +669,10 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   return TS_OK;
 }
 
-ts_status ts_scene_build_atlas2d(ts_scene* s, ts_dtype store, void* stream) {
+ts_status ts_scene_build_atlas2d(ts_scene* s, ts_dtype store, int packing, void* stream) {
   if (!s) return fail(TS_ERR_ARG, "ts_scene_build_atlas2d: scene is NULL");
+  if (packing != TS_PACK_SPLAT_ID && packing != TS_PACK_MORTON)
+    return fail(TS_ERR_ARG, "ts_scene_build_atlas2d: unknown packing");
   if (store != TS_F32 && store != TS_F16) return fail(TS_ERR_ARG, "ts_scene_build_atlas2d: store must be TS_F32 or TS_F16");
   if (!s->texels || s->tex_n != s->n) return fail(TS_ERR_STATE, "ts_scene_build_atlas2d: atlas missing or stale");
   cudaStream_t st = (cudaStream_t)stream;
@@ -722,11 +724,41 @@ ts_status ts_scene_build_atlas2d(ts_scene* s, ts_dtype store, void* stream) {
   }
   if (r == TS_OK && cudaMalloc(&s->chart, (size_t)n * sizeof(uint2)) != cudaSuccess)
     r = fail(TS_ERR_OOM, "ts_scene_build_atlas2d: indirection buffer allocation failed");
+  // chart order: splat id (the paper's packing) or the Morton order of the
+  // splat centres, so that splats near each other in space get neighbouring
+  // charts (the locality-aware packing the paper leaves to future work)
+  uint32_t* chart_of = nullptr;
+  void* mtemp = nullptr;
+  if (r == TS_OK && s->n > 0 && packing == TS_PACK_MORTON) {
+    const size_t nn = (size_t)s->n;
+    const size_t rt = radix_temp_bytes((int)s->n);
+    const size_t bytes = 256 + 5 * ((nn * 4 + 255) & ~size_t(255)) + rt;
+    if (cudaMalloc(&mtemp, bytes) != cudaSuccess) {
+      r = fail(TS_ERR_OOM, "ts_scene_build_atlas2d: scratch allocation failed");
+    } else {
+      char* b = reinterpret_cast<char*>(mtemp);
+      const size_t seg = (nn * 4 + 255) & ~size_t(255);
+      uint32_t* bbox = reinterpret_cast<uint32_t*>(b);
+      uint32_t* k0 = reinterpret_cast<uint32_t*>(b + 256);
+      uint32_t* v0 = reinterpret_cast<uint32_t*>(b + 256 + seg);
+      uint32_t* k1 = reinterpret_cast<uint32_t*>(b + 256 + 2 * seg);
+      uint32_t* v1 = reinterpret_cast<uint32_t*>(b + 256 + 3 * seg);
+      chart_of = reinterpret_cast<uint32_t*>(b + 256 + 4 * seg);
+      void* rtemp = b + 256 + 5 * seg;
+      launch_morton_order(s->means, s->n, bbox, k0, v0, st);
+      const int w = radix_sort_u32(k0, v0, k1, v1, (int)s->n, 0, 30, rtemp, st);
+      launch_chart_of(w ? v1 : v0, s->n, chart_of, st);
+    }
+  }
   if (r == TS_OK && s->n > 0) {
-    launch_pack_atlas2d(s->texels, s->tex_dtype, s->n, T, (int)charts_x, surf[0], surf[1], s->chart,
+    launch_pack_atlas2d(s->texels, s->tex_dtype, s->n, T, (int)charts_x, surf[0], surf[1], s->chart, chart_of,
                         store == TS_F16 ? 1 : 0, st);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
       r = fail(TS_ERR_CUDA, "ts_scene_build_atlas2d: packing failed");
+  }
+  if (mtemp) {
+    cudaStreamSynchronize(st);
+    cudaFree(mtemp);
   }
   for (int i = 0; i < 2; ++i)
     if (surf[i]) cudaDestroySurfaceObject(surf[i]);

@@ -48,7 +48,11 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
                        cudaStream_t st);
 void launch_pack_atlas2d(const void* texels, int dtype, long long n, int T, int charts_x, cudaSurfaceObject_t s0,
-                         cudaSurfaceObject_t s1, uint2* chart, int half_store, cudaStream_t st);
+                         cudaSurfaceObject_t s1, uint2* chart, const uint32_t* chart_of, int half_store,
+                         cudaStream_t st);
+void launch_morton_order(const float4* means, long long n, uint32_t* bbox, uint32_t* codes, uint32_t* ids,
+                         cudaStream_t st);
+void launch_chart_of(const uint32_t* ids_sorted, long long n, uint32_t* chart_of, cudaStream_t st);
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
                        const GradTable& g, cudaStream_t st);

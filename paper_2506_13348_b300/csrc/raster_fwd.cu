@@ -193,7 +193,7 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
 // rows indexing t (v) and columns s (u), and records the origin per splat.
 __global__ void k_pack_atlas2d(const void* __restrict__ texels, int dtype, long long n, int T, int charts_x,
                                cudaSurfaceObject_t s0, cudaSurfaceObject_t s1, uint2* __restrict__ chart,
-                               int half_store) {
+                               const uint32_t* __restrict__ chart_of, int half_store) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tt = (long long)T * T;
   if (i >= n * tt) return;
@@ -201,7 +201,8 @@ __global__ void k_pack_atlas2d(const void* __restrict__ texels, int dtype, long 
   const int r = (int)(i - k * tt), jj = r / T, ii = r - jj * T;
   float v[8];
   load_texel(texels, dtype, i, v);
-  const int cx = (int)(k % charts_x) * T, cy = (int)(k / charts_x) * T;
+  const long long slot = chart_of ? (long long)chart_of[k] : k;  // chart position of splat k
+  const int cx = (int)(slot % charts_x) * T, cy = (int)(slot / charts_x) * T;
   const int x = cx + ii, y = cy + jj;
   if (half_store) {
     const ushort4 a = make_ushort4(__half_as_ushort(__float2half_rn(v[0])), __half_as_ushort(__float2half_rn(v[1])),
@@ -218,11 +219,97 @@ __global__ void k_pack_atlas2d(const void* __restrict__ texels, int dtype, long 
 }
 
 void launch_pack_atlas2d(const void* texels, int dtype, long long n, int T, int charts_x, cudaSurfaceObject_t s0,
-                         cudaSurfaceObject_t s1, uint2* chart, int half_store, cudaStream_t st) {
+                         cudaSurfaceObject_t s1, uint2* chart, const uint32_t* chart_of, int half_store,
+                         cudaStream_t st) {
   const long long total = n * (long long)T * T;
   if (total <= 0) return;
   k_pack_atlas2d<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(texels, dtype, n, T, charts_x, s0, s1, chart,
-                                                                   half_store);
+                                                                   chart_of, half_store);
+  note_launches(1);
+}
+
+// ---- locality-aware chart order: Morton codes of the splat centres ----------
+// Order-preserving float <-> uint32 map for atomic min / max of floats.
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// bbox[0..2] = min, bbox[3..5] = max of the centres, as ordered uints
+// (initialised to max / min by the caller).
+__global__ void k_centre_bbox(const float4* __restrict__ means, long long n, uint32_t* __restrict__ bbox) {
+  uint32_t lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float4 p = means[i];
+    const float v[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = min(lo[a], f2ord(v[a]));
+      hi[a] = max(hi[a], f2ord(v[a]));
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+    hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(bbox + a, lo[a]);
+      atomicMax(bbox + 3 + a, hi[a]);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 bits -> every third bit
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// 30-bit Morton code of each centre in its bounding box, and the splat id.
+__global__ void k_morton(const float4* __restrict__ means, long long n, const uint32_t* __restrict__ bbox,
+                         uint32_t* __restrict__ codes, uint32_t* __restrict__ ids) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = means[i];
+  const float v[3] = {p.x, p.y, p.z};
+  uint32_t q[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float lo = ord2f(bbox[a]), hi = ord2f(bbox[3 + a]);
+    const float t = hi > lo ? (v[a] - lo) / (hi - lo) : 0.f;
+    q[a] = (uint32_t)fminf(fmaxf(t * 1024.f, 0.f), 1023.f);
+  }
+  codes[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+  ids[i] = (uint32_t)i;
+}
+
+__global__ void k_chart_of(const uint32_t* __restrict__ ids_sorted, long long n, uint32_t* __restrict__ chart_of) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) chart_of[ids_sorted[r]] = (uint32_t)r;
+}
+
+void launch_morton_order(const float4* means, long long n, uint32_t* bbox, uint32_t* codes, uint32_t* ids,
+                         cudaStream_t st) {
+  if (n <= 0) return;
+  const uint32_t init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+  cudaMemcpyAsync(bbox, init, sizeof(init), cudaMemcpyHostToDevice, st);
+  k_centre_bbox<<<148 * 4, 256, 0, st>>>(means, n, bbox);
+  k_morton<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(means, n, bbox, codes, ids);
+  note_launches(2);
+}
+
+void launch_chart_of(const uint32_t* ids_sorted, long long n, uint32_t* chart_of, cudaStream_t st) {
+  if (n <= 0) return;
+  k_chart_of<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ids_sorted, n, chart_of);
   note_launches(1);
 }
 

@@ -135,3 +135,27 @@ def test_sampler_state_errors(P):
     _, saved = P.render(sc, CAM, save=True)
     saved.release()
     torch.cuda.synchronize()
+
+
+def test_morton_packing_samples_the_same_texels(P):
+    """Charts placed in the Morton order of the splat centres: the same texels
+    are sampled (constant charts equal the software path; the albedo-linear
+    scene stays within the fixed-point bound of the software path)."""
+    env = sg.make_env(0)
+    scene = scene_1k(const=True, n=1500)
+    sc = P.Scene.from_arrays(scene, env)
+    sc.build_atlas2d("f32", packing="morton")
+    sw = render(P, sc, "software")
+    hw = render(P, sc, "hw_atlas")
+    assert np.abs(hw - sw).max() <= 1e-5
+    c = 0.8
+    scene = scene_1k(metal_zero=True, n=1500)
+    sc = P.Scene.from_arrays(scene, sg.constant_env((c, c, c)))
+    sw = render(P, sc, "software")
+    sc.build_atlas2d("f32", packing="morton")
+    hw_m = render(P, sc, "hw_atlas")
+    sc.build_atlas2d("f32", packing="splat_id")
+    hw_i = render(P, sc, "hw_atlas")
+    for hw in (hw_m, hw_i):
+        np.testing.assert_array_equal(hw[..., 3], sw[..., 3])
+        assert np.abs(hw[..., :3] - sw[..., :3]).max() <= c * 2.0 ** -7

@@ -554,25 +554,37 @@ def time_image_loss(P, img, target, dev, reps=50):
 
 
 def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
-    """Same step through the public API with host buffers: the target image
-    goes host->device from pinned memory and the loss comes back each step."""
-    import numpy as np
+    """Same step through the public API with host buffers: each step's target
+    image goes host->device from pinned memory and its loss comes back.  The
+    copy runs on a side stream into one of two device buffers and overlaps the
+    render; the loss kernel waits for it.  Every copy is issued after the
+    start event and consumed before the end event, so all of them are inside
+    the timed region."""
     import torch
 
     import scenegen as sg
     host_t = [torch.from_numpy(sg.make_target(i, RES, RES)).pin_memory() for i in range(min(8, n_needed))]
-    dev_t = torch.empty(RES, RES, 4, dtype=torch.float32, device=dev)
-    out = torch.empty_like(dev_t)
-    dl = torch.empty_like(dev_t)
+    dev_t = [torch.empty(RES, RES, 4, dtype=torch.float32, device=dev) for _ in range(2)]
+    out = torch.empty_like(dev_t[0])
+    dl = torch.empty_like(dev_t[0])
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     loss_h = torch.zeros(1, dtype=torch.float32).pin_memory()
     grads = P.zero_grads(sc)
     stream = torch.cuda.current_stream()
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
 
     def step(i):
-        dev_t.copy_(host_t[i % len(host_t)], non_blocking=True)
+        b = i % 2
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(used[b])  # the buffer's previous loss read is done
+            dev_t[b].copy_(host_t[i % len(host_t)], non_blocking=True)
+            copied[b].record(copy_stream)
         _, saved = P.render(sc, cams[i % n_needed], out=out, save=True)
-        P.l1_loss(out, dev_t, loss, dl)
+        stream.wait_event(copied[b])
+        P.l1_loss(out, dev_t[b], loss, dl)
+        used[b].record(stream)
         P.render_backward(saved, dl, grads)
         saved.release()
         loss_h.copy_(loss, non_blocking=True)
@@ -584,6 +596,7 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
         pg.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    copy_stream.wait_event(e0)
     for i in range(args.steps):
         step(args.warmup + i)
     e1.record(stream)
@@ -593,7 +606,8 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
     ms = float(t.item())
     return {"value": world * args.steps * RES * RES / 1e6 / (ms / 1e3), "unit": UNIT,
-            "h2d_bytes_per_step": RES * RES * 4 * 4, "d2h_bytes_per_step": 4}
+            "h2d_bytes_per_step": RES * RES * 4 * 4, "d2h_bytes_per_step": 4,
+            "note": "target H2D on a side stream overlapping the render (double-buffered)"}
 
 
 # Source files each profiled kernel is built from: a committed DRAM-traffic

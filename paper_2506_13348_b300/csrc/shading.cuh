@@ -124,6 +124,12 @@ struct ShadeState {
   float lod, f;
   int l0, l1;
   bool ok, nz;
+  // lookups kept for the adjoint (filled when shade_pixel is asked for them)
+  CubeCoord cr, cn;
+  Bil b0, b1, bi;
+  float2 ldx, ldy;          // d LUT / d (NdotV, roughness) texel units
+  float3 c0, c1;            // specular samples at levels l0, l1
+  float3 dx0, dy0, dx1, dy1, idx, idy;  // their texel-unit derivatives
 };
 
 __device__ __forceinline__ float3 world_ray(const ViewDesc& V, float xp, float yp) {
@@ -133,6 +139,7 @@ __device__ __forceinline__ float3 world_ray(const ViewDesc& V, float xp, float y
                      V.R[2] * a + V.R[5] * b + V.R[8]);
 }
 
+template <bool GRAD = false>
 __device__ __forceinline__ float4 shade_pixel(const EnvDesc& E, const float X[8], float A, float3 d,
                                               ShadeState* st) {
   ShadeState s;
@@ -163,26 +170,28 @@ __device__ __forceinline__ float4 shade_pixel(const EnvDesc& E, const float X[8]
   for (int c = 0; c < 3; ++c) s.F0[c] = 0.04f * (1.f - s.met) + s.lam[c] * s.met;
   s.rc = fminf(fmaxf(s.rough, 0.f), 1.f);
   Bil bl;
-  s.lt = lut_bilinear(E.lut, E.lut_res, s.ndv, s.rc, bl, nullptr, nullptr);
-  CubeCoord cr = cube_coord(s.wr);
+  s.lt = lut_bilinear(E.lut, E.lut_res, s.ndv, s.rc, bl, GRAD ? &s.ldx : nullptr, GRAD ? &s.ldy : nullptr);
+  s.cr = cube_coord(s.wr);
   int L = E.levels;
   s.lod = s.rc * (float)(L - 1);
   float l0f = fminf(floorf(s.lod), (float)(L - 1));
   s.f = s.lod - l0f;
   s.l0 = (int)l0f;
   s.l1 = min(s.l0 + 1, L - 1);
-  Bil b0, b1;
-  float3 c0 = cube_bilinear(E.spec[s.l0], E.cube_dtype, E.spec_res[s.l0], cr, b0, nullptr, nullptr);
+  s.c0 = cube_bilinear(E.spec[s.l0], E.cube_dtype, E.spec_res[s.l0], s.cr, s.b0, GRAD ? &s.dx0 : nullptr,
+                       GRAD ? &s.dy0 : nullptr);
+  const float3 c0 = s.c0;
   if (L > 1) {
-    float3 c1 = cube_bilinear(E.spec[s.l1], E.cube_dtype, E.spec_res[s.l1], cr, b1, nullptr, nullptr);
+    s.c1 = cube_bilinear(E.spec[s.l1], E.cube_dtype, E.spec_res[s.l1], s.cr, s.b1, GRAD ? &s.dx1 : nullptr,
+                         GRAD ? &s.dy1 : nullptr);
+    const float3 c1 = s.c1;
     float g = 1.f - s.f;
     s.spec = make_float3(g * c0.x + s.f * c1.x, g * c0.y + s.f * c1.y, g * c0.z + s.f * c1.z);
   } else {
     s.spec = c0;
   }
-  CubeCoord cn = cube_coord(s.Nh);
-  Bil bi;
-  s.irr = cube_bilinear(E.irr, E.cube_dtype, E.irr_res, cn, bi, nullptr, nullptr);
+  s.cn = cube_coord(s.Nh);
+  s.irr = cube_bilinear(E.irr, E.cube_dtype, E.irr_res, s.cn, s.bi, GRAD ? &s.idx : nullptr, GRAD ? &s.idy : nullptr);
   const float inv_pi = 0.318309886183790672f;
   float spec3[3] = {s.spec.x, s.spec.y, s.spec.z};
   float irr3[3] = {s.irr.x, s.irr.y, s.irr.z};
@@ -215,7 +224,7 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
 #pragma unroll
   for (int c = 0; c < 8; ++c) gX[c] = 0.f;
   ShadeState s;
-  shade_pixel(E, X, A, d, &s);
+  shade_pixel<true>(E, X, A, d, &s);
   gA = g.w;
   eg.ok = s.ok;
   if (!s.ok) return;
@@ -246,21 +255,18 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
     gmet += (s.lam[c] - 0.04f) * gF0[c];
   }
   // LUT (not learnable): gradient to NdotV and roughness
-  Bil bl;
-  float2 ldx, ldy;
-  lut_bilinear(E.lut, E.lut_res, s.ndv, s.rc, bl, &ldx, &ldy);
+  const float2 ldx = s.ldx, ldy = s.ldy;
   float gndv = (float)E.lut_res * (gLA * ldx.x + gLB * ldx.y);
   float grc = (float)E.lut_res * (gLA * ldy.x + gLB * ldy.y);
   // specular cube, trilinear
-  CubeCoord cr = cube_coord(s.wr);
+  const CubeCoord& cr = s.cr;
   int L = E.levels;
   float3 gwr = make_float3(0.f, 0.f, 0.f);
   float3 gsp = make_float3(gspec3[0], gspec3[1], gspec3[2]);
   {
-    Bil b0;
-    float3 dx0, dy0;
+    const Bil b0 = s.b0;
+    const float3 dx0 = s.dx0, dy0 = s.dy0, c0 = s.c0;
     float R0 = (float)E.spec_res[s.l0];
-    float3 c0 = cube_bilinear(E.spec[s.l0], E.cube_dtype, E.spec_res[s.l0], cr, b0, &dx0, &dy0);
     float w0 = (L > 1) ? (1.f - s.f) : 1.f;
     float gs = w0 * R0 * (gsp.x * dx0.x + gsp.y * dx0.y + gsp.z * dx0.z);
     float gt = w0 * R0 * (gsp.x * dy0.x + gsp.y * dy0.y + gsp.z * dy0.z);
@@ -273,10 +279,9 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
     eg.w1 = 0.f;
     eg.gsp = gsp;
     if (L > 1) {
-      Bil b1;
-      float3 dx1, dy1;
+      const Bil b1 = s.b1;
+      const float3 dx1 = s.dx1, dy1 = s.dy1, c1 = s.c1;
       float R1 = (float)E.spec_res[s.l1];
-      float3 c1 = cube_bilinear(E.spec[s.l1], E.cube_dtype, E.spec_res[s.l1], cr, b1, &dx1, &dy1);
       gs += s.f * R1 * (gsp.x * dx1.x + gsp.y * dx1.y + gsp.z * dx1.z);
       gt += s.f * R1 * (gsp.x * dy1.x + gsp.y * dy1.y + gsp.z * dy1.z);
       eg.b1 = b1;
@@ -289,10 +294,9 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
   // irradiance cube at N
   float3 gNh = make_float3(0.f, 0.f, 0.f);
   {
-    CubeCoord cn = cube_coord(s.Nh);
-    Bil bi;
-    float3 dx, dy;
-    cube_bilinear(E.irr, E.cube_dtype, E.irr_res, cn, bi, &dx, &dy);
+    const CubeCoord& cn = s.cn;
+    const Bil bi = s.bi;
+    const float3 dx = s.idx, dy = s.idy;
     float3 gi = make_float3(girr3[0], girr3[1], girr3[2]);
     float Ri = (float)E.irr_res;
     float gs = Ri * (gi.x * dx.x + gi.y * dx.y + gi.z * dx.z);

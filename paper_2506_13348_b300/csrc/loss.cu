@@ -5,7 +5,8 @@
 //
 // Two tiled passes over 32x32 output tiles (42x42 inputs with the 5-pixel
 // halo in shared memory, separable blur: a horizontal pass into shared
-// memory, then a vertical pass per output pixel), one channel at a time:
+// memory, then a vertical pass per output pixel):
+// One CTA per tile and channel.
 //   k_ssim_fwd: the five blurred moments per pixel -> SSIM, the L1 and SSIM
 //     sums (float64 atomics, one per CTA), and per pixel and channel the
 //     loss derivatives w.r.t. the three moments the image enters
@@ -44,7 +45,8 @@ __global__ void __launch_bounds__(SS_THREADS) k_ssim_fwd(const float4* __restric
   const int tid = threadIdx.x;
   const long long N = (long long)W * H;
   float l1 = 0.f, ss = 0.f;
-  for (int ch = 0; ch < 3; ++ch) {
+  const int ch = blockIdx.z;  // one RGB channel per CTA
+  {
     for (int i = tid; i < SS_IN * SS_IN; i += SS_THREADS) {
       const int r = i / SS_IN, c = i - r * SS_IN;
       const int gx = ox - SS_HALO + c, gy = oy - SS_HALO + r;
@@ -135,60 +137,49 @@ __global__ void __launch_bounds__(SS_THREADS) k_ssim_bwd(const float4* __restric
   const int tid = threadIdx.x;
   const long long N = (long long)W * H;
   constexpr int PER = SS_TO * SS_TO / SS_THREADS;  // output pixels per thread
-  float out[PER][3];
+  const int ch = blockIdx.z;  // one RGB channel per CTA
+  for (int i = tid; i < SS_IN * SS_IN; i += SS_THREADS) {
+    const int r = i / SS_IN, c = i - r * SS_IN;
+    const int gx = ox - SS_HALO + c, gy = oy - SS_HALO + r;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+    const long long p = (long long)gy * W + gx;
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    for (int i = tid; i < SS_IN * SS_IN; i += SS_THREADS) {
-      const int r = i / SS_IN, c = i - r * SS_IN;
-      const int gx = ox - SS_HALO + c, gy = oy - SS_HALO + r;
-      const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-      const long long p = (long long)gy * W + gx;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) sp[j][r][c] = in ? part[(3 * ch + j) * N + p] : 0.f;
-    }
-    __syncthreads();
-    for (int i = tid; i < SS_IN * SS_TO; i += SS_THREADS) {
-      const int r = i / SS_TO, c = i - r * SS_TO;
-      float m[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < 11; ++k) {
-        const float g = c_gauss[k];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) m[j] = fmaf(g, sp[j][r][c + k], m[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < 3; ++j) hs[j][r][c] = m[j];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const int i = tid + e * SS_THREADS;
-      const int r = i / SS_TO, c = i - r * SS_TO;
-      float m[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < 11; ++k) {
-        const float g = c_gauss[k];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) m[j] = fmaf(g, hs[j][r + k][c], m[j]);
-      }
-      out[e][ch] = 0.f;
-      const int gx = ox + c, gy = oy + r;
-      if (gx < W && gy < H) {
-        const long long p = (long long)gy * W + gx;
-        const float x = chan(img[p], ch), y = chan(tgt[p], ch);
-        const float d = x - y;
-        const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        out[e][ch] = m[0] + 2.f * x * m[1] + y * m[2] + l1w * sgn;
-      }
-    }
-    __syncthreads();
+    for (int j = 0; j < 3; ++j) sp[j][r][c] = in ? part[(3 * ch + j) * N + p] : 0.f;
   }
+  __syncthreads();
+  for (int i = tid; i < SS_IN * SS_TO; i += SS_THREADS) {
+    const int r = i / SS_TO, c = i - r * SS_TO;
+    float m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 11; ++k) {
+      const float g = c_gauss[k];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) m[j] = fmaf(g, sp[j][r][c + k], m[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) hs[j][r][c] = m[j];
+  }
+  __syncthreads();
+  float* gout = reinterpret_cast<float*>(grad);
 #pragma unroll
   for (int e = 0; e < PER; ++e) {
     const int i = tid + e * SS_THREADS;
     const int r = i / SS_TO, c = i - r * SS_TO;
     const int gx = ox + c, gy = oy + r;
-    if (gx < W && gy < H) grad[(long long)gy * W + gx] = make_float4(out[e][0], out[e][1], out[e][2], 0.f);
+    if (gx >= W || gy >= H) continue;
+    float m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 11; ++k) {
+      const float g = c_gauss[k];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) m[j] = fmaf(g, hs[j][r + k][c], m[j]);
+    }
+    const long long p = (long long)gy * W + gx;
+    const float x = chan(img[p], ch), y = chan(tgt[p], ch);
+    const float d = x - y;
+    const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+    gout[4 * p + ch] = m[0] + 2.f * x * m[1] + y * m[2] + l1w * sgn;
+    if (ch == 0) gout[4 * p + 3] = 0.f;
   }
 }
 
@@ -224,7 +215,7 @@ void launch_image_loss(const float4* img, const float4* tgt, int W, int H, float
   float* part = reinterpret_cast<float*>(reinterpret_cast<char*>(temp) + 256);
   const double n3 = 3.0 * (double)W * (double)H;
   cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
-  dim3 grid((W + SS_TO - 1) / SS_TO, (H + SS_TO - 1) / SS_TO), block(SS_THREADS);
+  dim3 grid((W + SS_TO - 1) / SS_TO, (H + SS_TO - 1) / SS_TO, 3), block(SS_THREADS);
   k_ssim_fwd<<<grid, block, 0, st>>>(img, tgt, W, H, (float)(-lam / n3), part, acc);
   k_ssim_bwd<<<grid, block, 0, st>>>(img, tgt, W, H, part, (float)((1.0 - lam) / n3), grad);
   k_loss_finish<<<1, 1, 0, st>>>(acc, n3, lam, loss);

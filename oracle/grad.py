@@ -24,9 +24,11 @@ PARAM_NAMES = ("means", "quats", "scales", "opacity", "texels")
 
 
 def render_grads(scene: dict, cam: dict, env: dict, dL_drgba: np.ndarray, *, tiles=None,
-                 keylist=None, max_entries=2_000_000) -> dict:
+                 keylist=None, max_entries=2_000_000, normal_weight: float = 0.0) -> dict:
     """Autograd gradients of sum(rgba * dL_drgba) w.r.t. every parameter.
 
+    With ``normal_weight`` the objective adds normal_weight x L_n (the
+    normal-consistency loss of oracle/loss.py over the whole view).
     Returns numpy float64 arrays for means, quats, scales, opacity, texels,
     spec (list per level) and irr, plus the rendered rgba.
     """
@@ -36,6 +38,10 @@ def render_grads(scene: dict, cam: dict, env: dict, dL_drgba: np.ndarray, *, til
     out = R.render(scene, cam, env, params=params, envp=envp, tiles=tiles, margins=None,
                    max_entries=max_entries, keylist=keylist)
     S = (out["rgba"] * g).sum()
+    if normal_weight:
+        from .loss import depth_normal_loss
+        Ln, _, _ = depth_normal_loss(out["Z"], out["A"], out["X"], cam)
+        S = S + normal_weight * Ln
     S.backward()
     res = {k: params[k].grad.numpy().copy() for k in PARAM_NAMES}
     res["spec"] = [m.grad.numpy().copy() for m in envp["spec"]]

@@ -17,9 +17,19 @@ evaluates it (reading R17):
 Everything is float64 numpy/torch; the convolution is torch's conv2d (a
 library primitive), the gradient is autograd of the same expression.
 
+Normal consistency (Sec. 3.6, L_n = 1 - N~^T N, reading R18): the rendered
+depth is the expected depth D = Z / A of the blended camera depth Z and the
+coverage A; each pixel is back-projected to P = D (x'/fx, y'/fy, 1) in camera
+space; the depth normal is N~ = normalize((P[y+1] - P[y-1]) x (P[x+1] - P[x-1]))
+(central differences, facing the camera), turned to world space by R^T; N is
+the normalised blended normal channel.  A pixel counts when it is interior and
+it and its four neighbours have coverage >= 0.5 (a surface is there) and its
+normal and cross product are non-zero; L_n = sum over counted pixels of
+(1 - N~ . N) / ((W - 2)(H - 2)).
+
 Parity: pinned by tests/test_oracle_loss.py against a direct per-pixel
-window sum on tiny images, the closed form on constant images, SSIM(x, x) = 1
-and central differences.
+window sum on tiny images, the closed form on constant images, SSIM(x, x) = 1,
+central differences, and for L_n by planes in closed form (tests/test_oracle_render.py).
 """
 from __future__ import annotations
 
@@ -71,6 +81,42 @@ def image_loss(rgba: np.ndarray, target: np.ndarray, lam: float = LAMBDA_DSSIM):
     return float(loss.detach()), grad, float(l1.detach()), float(ssim.detach())
 
 
+NORMAL_COVER_MIN = 0.5
+
+
+def depth_normal_loss(Z: torch.Tensor, A: torch.Tensor, X: torch.Tensor, cam: dict):
+    """L_n of [H, W] blended depth Z and coverage A and the [H, W, 8] G-buffer
+    X (normal channels 5-7), float64 torch (differentiable).  Returns
+    (L_n, counted mask [H, W] bool, depth normal in world space [H, W, 3])."""
+    H, W = Z.shape
+    R = torch.tensor(np.asarray(cam["R"], dtype=np.float64))
+    fx, fy, cx, cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
+    xs = (torch.arange(W, dtype=F64) + 0.5 - cx) / fx
+    ys = (torch.arange(H, dtype=F64) + 0.5 - cy) / fy
+    ok_a = A >= NORMAL_COVER_MIN
+    D = torch.where(ok_a, Z / torch.where(ok_a, A, torch.ones_like(A)), torch.zeros_like(Z))
+    P = torch.stack([D * xs[None, :], D * ys[:, None], D], -1)  # [H, W, 3] camera space
+    dx = P[1:-1, 2:] - P[1:-1, :-2]
+    dy = P[2:, 1:-1] - P[:-2, 1:-1]
+    c = torch.cross(dy, dx, dim=-1)
+    cn = torch.linalg.vector_norm(c, dim=-1)
+    N = X[1:-1, 1:-1, 5:8]
+    nn = torch.linalg.vector_norm(N, dim=-1)
+    valid = ok_a[1:-1, 1:-1] & ok_a[1:-1, 2:] & ok_a[1:-1, :-2] & ok_a[2:, 1:-1] & ok_a[:-2, 1:-1]
+    valid = valid & (nn >= 1e-12) & (cn > 0)
+    one = torch.ones_like(cn)
+    Nt_c = c / torch.where(valid, cn, one)[..., None]
+    Nt_w = Nt_c @ R  # R^T n, row-vector form
+    Nh = N / torch.where(valid, nn, one)[..., None]
+    term = torch.where(valid, 1.0 - (Nt_w * Nh).sum(-1), torch.zeros_like(cn))
+    L = term.sum() / float((W - 2) * (H - 2))
+    mask = torch.zeros(H, W, dtype=torch.bool)
+    mask[1:-1, 1:-1] = valid
+    full = torch.zeros(H, W, 3, dtype=F64)
+    full[1:-1, 1:-1] = Nt_w.detach()
+    return L, mask, full
+
+
 def ssim_direct(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     """SSIM map of [H, W] single-channel images by explicit window sums at
     every pixel (window taps outside the image count as zero).  Slow; for
@@ -106,4 +152,4 @@ def ssim_constant_interior(a: float, b: float) -> float:
 
 
 __all__ = ["gaussian_window", "ssim_map", "image_loss", "ssim_direct", "ssim_constant_interior",
-           "WIN", "SIGMA", "C1", "C2", "LAMBDA_DSSIM"]
+           "depth_normal_loss", "WIN", "SIGMA", "C1", "C2", "LAMBDA_DSSIM", "NORMAL_COVER_MIN"]

@@ -159,10 +159,14 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
     w = torch.where(blended, a * T_before, torch.zeros_like(a))
     X = torch.cumsum(w[..., None] * x, dim=1)[:, -1, :] if L > 0 else torch.zeros(P, 8, dtype=F64)
     A = torch.cumsum(w, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
+    # depth channel: the blended camera depth of the hits, sum_i w_i tau_i (the
+    # ray has camera-space z component 1, so tau is the camera depth)
+    tau_s = torch.where(blended, tau, torch.zeros_like(tau))
+    Z = torch.cumsum(w * tau_s, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
     ab = torch.where(blended, a, torch.zeros_like(a))
     T_final = torch.cumprod(1.0 - ab, dim=1)[:, -1] if L > 0 else torch.ones(P, dtype=F64)
 
-    out = dict(X=X, A=A, T=T_final, ray_d=d, blended=blended, valid=valid, T_before=T_before)
+    out = dict(X=X, A=A, Z=Z, T=T_final, ray_d=d, blended=blended, valid=valid, T_before=T_before)
     with torch.no_grad():
         evaluated = (T_before >= T_MIN) & ~pad
         out["n_eval"] = evaluated.sum(1)
@@ -237,7 +241,8 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
            tiles=None, margins=DEFAULT_MARGINS, max_entries=4_000_000, keylist=None) -> dict:
     """Render the view (or the listed ``tiles``) in float64.
 
-    Returns rgba [H,W,4], the G-buffer X [H,W,8], A, T_final, the ambiguity
+    Returns rgba [H,W,4], the G-buffer X [H,W,8], A, the blended depth Z
+    (sum of alpha T times the hit's camera depth), T_final, the ambiguity
     mask, fragment counts (evaluated / contributing), the last contributor
     index and the key list.  With ``params``/``envp`` (torch leaves) the
     images are differentiable.
@@ -255,6 +260,7 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
     rgba = torch.zeros(H, W, 4, dtype=F64)
     Xb = torch.zeros(H, W, 8, dtype=F64)
     Ab = torch.zeros(H, W, dtype=F64)
+    Zb = torch.zeros(H, W, dtype=F64)
     Tb = torch.ones(H, W, dtype=F64)
     amb = torch.zeros(H, W, dtype=torch.bool)
     gamb = torch.zeros(H, W, dtype=torch.bool)
@@ -289,6 +295,7 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         rgba.index_put_((pyt, pxt), col)
         Xb.index_put_((pyt, pxt), fr["X"])
         Ab.index_put_((pyt, pxt), fr["A"])
+        Zb.index_put_((pyt, pxt), fr["Z"])
         Tb.index_put_((pyt, pxt), fr["T"])
         n_eval[pyt, pxt] = fr["n_eval"]
         n_con[pyt, pxt] = fr["n_contrib"]
@@ -310,8 +317,8 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         size += ent
     if chunk:
         run_chunk(chunk)
-    return dict(rgba=rgba, X=Xb, A=Ab, T=Tb, ambiguous=amb, grad_ambiguous=gamb, n_eval=n_eval, n_contrib=n_con,
-                last=last, covered=covered, keys=kl)
+    return dict(rgba=rgba, X=Xb, A=Ab, Z=Zb, T=Tb, ambiguous=amb, grad_ambiguous=gamb, n_eval=n_eval,
+                n_contrib=n_con, last=last, covered=covered, keys=kl)
 
 
 def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, params=None,
@@ -333,7 +340,8 @@ def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, pa
     col = shade(fr["X"], fr["A"], fr["ray_d"], envp)
     amb = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
     gamb = amb | fr["kink"] | shading_kinks(fr["X"].detach(), fr["A"].detach(), fr["ray_d"], envp)
-    return dict(rgba=col, X=fr["X"], A=fr["A"], T=fr["T"], ambiguous=amb, grad_ambiguous=gamb, n_eval=fr["n_eval"],
+    return dict(rgba=col, X=fr["X"], A=fr["A"], Z=fr["Z"], T=fr["T"], ambiguous=amb, grad_ambiguous=gamb,
+                n_eval=fr["n_eval"],
                 n_contrib=fr["n_contrib"], last=fr["last"])
 
 

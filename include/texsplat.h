@@ -213,6 +213,28 @@ ts_status ts_scene_texels(ts_scene* scene, void** texels, int* T, int* dtype);
 ts_status ts_image_loss(const float* rgba, const float* target, int width, int height, float lambda_dssim,
                         float* loss, float* grad, void* stream);
 
+/* Copies view v's blended camera depth zsum [H][W] (sum over blended
+ * fragments of alpha T z, z the camera depth of the ray-splat hit) and
+ * coverage acc [H][W] (sum of alpha T) of a saved render.  The expected
+ * depth is zsum / acc.  NULL skips. */
+ts_status ts_saved_copy_depth(const ts_saved* saved, int view, float* zsum, float* acc, void* stream);
+
+/* Normal-consistency loss of Sec. 3.6 on view `view` of a saved render:
+ *   *loss = weight * L_n,  L_n = sum over counted pixels of (1 - N~ . N^)
+ *                               / ((W - 2)(H - 2)),
+ * N^ the normalised blended normal channel, N~ the normal of the depth map:
+ * the expected depth zsum / acc back-projected through the camera, central
+ * differences of the 4 neighbours, cross product facing the camera, in
+ * world space.  A pixel counts when it is interior, it and its neighbours
+ * have coverage >= 0.5 and its normal and cross product are non-zero.
+ * Stores the loss's gradient w.r.t. the view's normal channels, coverage
+ * and blended depth in the saved state (overwriting an earlier call); the
+ * next ts_render_backward of `saved` adds them to the image gradient, so
+ * the backward differentiates L_img + weight L_n.  Writes the device float
+ * `loss`; stream-ordered (first call on a view allocates its buffers).
+ * Errors: TS_ERR_ARG (NULL, bad view, negative weight), TS_ERR_CUDA. */
+ts_status ts_normal_loss(ts_saved* saved, int view, float weight, float* loss, void* stream);
+
 /* ---- hardware-texture atlas (test-time sampling) ------------------------- */
 
 /* Texture samplers of the forward render (ts_scene_set_sampler). */

@@ -25,7 +25,7 @@ EXPORTED = [
     "ts_render_noalloc", "ts_scene_info", "ts_server_create", "ts_server_destroy", "ts_server_submit",
     "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
     "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
-    "ts_image_loss",
+    "ts_image_loss", "ts_saved_copy_depth", "ts_normal_loss",
 ]
 
 
@@ -104,6 +104,8 @@ def lib() -> C.CDLL:
         "ts_scene_build_atlas2d": [vp, i32, i32, vp],
         "ts_scene_set_sampler": [vp, i32],
         "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
+        "ts_saved_copy_depth": [vp, i32, vp, vp, vp],
+        "ts_normal_loss": [vp, i32, C.c_float, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

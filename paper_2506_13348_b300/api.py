@@ -166,6 +166,19 @@ class Saved:
               "ts_saved_copy_pixels")
         return g, tr, last
 
+    def depth(self, view: int = 0, stream=None):
+        """(blended camera depth zsum [H, W], coverage [H, W]) of a view."""
+        W, H = self.views[view]
+        z = torch.empty(H, W, dtype=torch.float32, device="cuda")
+        a = torch.empty(H, W, dtype=torch.float32, device="cuda")
+        check(lib().ts_saved_copy_depth(self.handle, view, _ptr(z), _ptr(a), _stream(stream)), "ts_saved_copy_depth")
+        return z, a
+
+    def normal_loss(self, loss: torch.Tensor, weight: float = 1.0, view: int = 0, stream=None):
+        """weight x L_n (Sec. 3.6) of a view into the device scalar ``loss``;
+        its gradient joins the next render_backward of this saved state."""
+        check(lib().ts_normal_loss(self.handle, view, float(weight), _ptr(loss), _stream(stream)), "ts_normal_loss")
+
     def frag_stats(self, stream=None) -> dict:
         st = TsFragStats()
         check(lib().ts_saved_frag_stats(self.handle, C.byref(st), _stream(stream)), "ts_saved_frag_stats")

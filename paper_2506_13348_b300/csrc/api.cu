@@ -510,6 +510,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
       TS_CUDA_K(salloc((void**)&V.gbuf, np * 2 * sizeof(float4)));
       TS_CUDA_K(salloc((void**)&V.trans, np * sizeof(float)));
       TS_CUDA_K(salloc((void**)&V.acc, np * sizeof(float)));
+      TS_CUDA_K(salloc((void**)&V.zsum, np * sizeof(float)));
       TS_CUDA_K(salloc((void**)&V.last, np * sizeof(int)));
     }
   }
@@ -634,6 +635,49 @@ ts_status ts_saved_copy_pixels(const ts_saved* sv, int view, float* gbuf, float*
   if (gbuf) TS_CUDA(cudaMemcpyAsync(gbuf, V.gbuf, np * 32, cudaMemcpyDeviceToDevice, st));
   if (trans) TS_CUDA(cudaMemcpyAsync(trans, V.trans, np * 4, cudaMemcpyDeviceToDevice, st));
   if (last) TS_CUDA(cudaMemcpyAsync(last, V.last, np * 4, cudaMemcpyDeviceToDevice, st));
+  return TS_OK;
+}
+
+ts_status ts_saved_copy_depth(const ts_saved* sv, int view, float* zsum, float* acc, void* stream) {
+  if (!sv) return fail(TS_ERR_ARG, "ts_saved_copy_depth: NULL saved");
+  if (view < 0 || view >= sv->vt.n_views) return fail(TS_ERR_ARG, "ts_saved_copy_depth: bad view");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(sv->device));
+  const ViewDesc& V = sv->vt.v[view];
+  const size_t np = (size_t)V.W * V.H;
+  if (zsum) TS_CUDA(cudaMemcpyAsync(zsum, V.zsum, np * 4, cudaMemcpyDeviceToDevice, st));
+  if (acc) TS_CUDA(cudaMemcpyAsync(acc, V.acc, np * 4, cudaMemcpyDeviceToDevice, st));
+  return TS_OK;
+}
+
+ts_status ts_normal_loss(ts_saved* sv, int view, float weight, float* loss, void* stream) {
+  if (!sv || !loss) return fail(TS_ERR_ARG, "ts_normal_loss: NULL argument");
+  if (view < 0 || view >= sv->vt.n_views) return fail(TS_ERR_ARG, "ts_normal_loss: bad view");
+  if (!(weight >= 0.f)) return fail(TS_ERR_ARG, "ts_normal_loss: weight must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(sv->device));
+  ViewDesc& V = sv->vt.v[view];
+  const size_t np = (size_t)V.W * V.H;
+  if (!V.gnorm) {  // per-view gradient buffers, owned by the saved state
+    void* a = nullptr;
+    void* b = nullptr;
+    TS_CUDA(cudaMallocAsync(&a, np * sizeof(float4), sv->stream));
+    TS_CUDA(cudaMallocAsync(&b, np * sizeof(float), sv->stream));
+    sv->bufs.push_back(a);
+    sv->bufs.push_back(b);
+    V.gnorm = reinterpret_cast<const float4*>(a);
+    V.gzsum = reinterpret_cast<const float*>(b);
+    if (st != sv->stream) TS_CUDA(cudaStreamSynchronize(sv->stream));
+  }
+  void* temp = nullptr;
+  TS_CUDA(cudaMallocAsync(&temp, normal_loss_temp_bytes(V.W, V.H), st));
+  {
+    ProfScope p(st, "normal_loss");
+    launch_normal_loss(V, weight, loss, const_cast<float4*>(V.gnorm), const_cast<float*>(V.gzsum), temp, st);
+  }
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(temp, st);
+  if (e != cudaSuccess) return fail(TS_ERR_CUDA, std::string("ts_normal_loss: ") + cudaGetErrorString(e));
   return TS_OK;
 }
 

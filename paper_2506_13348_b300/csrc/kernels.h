@@ -76,4 +76,9 @@ size_t image_loss_temp_bytes(int W, int H);
 void launch_image_loss(const float4* img, const float4* tgt, int W, int H, float lam, float* loss, float4* grad,
                        void* temp, cudaStream_t st);
 
+// normal_loss.cu: normal consistency against the depth-derived normal
+size_t normal_loss_temp_bytes(int W, int H);
+void launch_normal_loss(const ViewDesc& V, float weight, float* loss, float4* gnorm, float* gzsum, void* temp,
+                        cudaStream_t st);
+
 }  // namespace ts

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) k_preprocess(ViewTable vt, Record* __rest
   r.r1 = make_float4(hu[2], hv[2], hw[0], hw[1]);
   r.r2 = make_float4(hw[2], o, tu[0], tu[1]);
   r.r3 = make_float4(tu[2], tv[0], tv[1], tv[2]);
-  r.r4 = make_float4(sg * n[0], sg * n[1], sg * n[2], __int_as_float(k));
+  r.r4 = make_float4(sg * n[0], sg * n[1], sg * n[2], D);  // D: hit depth = D / den
   rec[item] = r;
 }
 
@@ -164,7 +164,8 @@ void launch_preprocess(const ViewTable& vt, Record* rec, uint32_t* counts, uint6
 // ---------------------------------------------------------------------------
 // Adjoint.  g_items[item][14]: 0-2 d/dh_u, 3-5 d/dh_v, 6-8 d/dh_w (centred
 // pixel rows), 9 d/do, 10-12 the torque tau of the normal-mapping frame
-// (world): a rotation by a small angle vector w changes the loss by tau . w.
+// (world): a rotation by a small angle vector w changes the loss by tau . w,
+// 13 d/dD (D = p_c . n_c, the plane offset of the depth channel).
 // The per-splat sums arrive in float64 (accumulated across warps without
 // FP32 cancellation); the chain itself runs in float32 (a float64 chain was
 // measured: no accuracy change, 10x the time on this part).
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(ViewTable vt, const doub
   R_t gpc[3] = {0, 0, 0}, gtuc[3] = {0, 0, 0}, gtvc[3] = {0, 0, 0};
   R_t gnc[3] = {ghw[0], ghw[1], ghw[2]};
   // h_u = (D t_u - P_u n)/s_u, h_v likewise, h_w = n
-  R_t gD = 0, gPu = 0, gPv = 0, gsu = 0, gsv = 0;
+  R_t gD = gi[13], gPu = 0, gPv = 0, gsu = 0, gsv = 0;  // gi[13]: D through the depth channel
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const R_t hu = (D * tuc[i] - Pu * nc[i]) * isu;

@@ -10,8 +10,8 @@
 // stored); the transmittance in front of it is recovered by division
 // (alpha <= 0.99) and the colour behind it by the usual recurrence.
 // Reductions (all lanes of a warp work on the same splat at a time):
-//   * the 13 record gradients of the fragment are transposed through shared
-//     memory and lane L < 13 sums value L over the warp (independent loads,
+//   * the 14 record gradients of the fragment are transposed through shared
+//     memory and lane L < 14 sums value L over the warp (independent loads,
 //     tree add), adding it once per warp;
 //   * texel gradients are summed per bilinear cell over the warp (a
 //     reduce-scatter through shuffles) before one reduction per cell; lanes
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
   const float Ts6 = (float)T * (1.0f / 6.0f);
   const int lane = threadIdx.x & 31;
 
-  float gX[8], gA = 0.f, Tcur = 1.f;
+  float gX[8], gA = 0.f, gZ = 0.f, Tcur = 1.f;
   int last = -1;
 #pragma unroll
   for (int c = 0; c < 8; ++c) gX[c] = 0.f;
@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
     const float4 a = gxa[3 * gp], b = gxa[3 * gp + 1];
     gX[0] = a.x; gX[1] = a.y; gX[2] = a.z; gX[3] = a.w;
     gX[4] = b.x; gX[5] = b.y; gX[6] = b.z; gX[7] = b.w;
-    gA = gxa[3 * gp + 2].x;
+    const float4 c = gxa[3 * gp + 2];
+    gA = c.x;
+    gZ = c.y;  // dL/d(blended depth), zero unless a depth loss is in use
     Tcur = V.trans[pix];
     last = V.last[pix];
   }
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
     if (__any_sync(FULL, ok)) {
       r.r3 = __ldg(rp + 3);
       r.r4 = __ldg(rp + 4);
-      const long long splat = (long long)__float_as_int(r.r4.w);
+      const long long splat = (long long)item - V.item_off;
       float t8[8], w4[4] = {0.f, 0.f, 0.f, 0.f};
       TexSample ts_;
       ts_.ia = ts_.ib = ts_.ja = ts_.jb = 0;
@@ -153,7 +155,8 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         float dxs = dxy.x, dys = dxy.y;
         // dL/dalpha = T_before (Q - P): Q = gX.x + gA of this fragment, P the
         // same projection of everything blended behind it (P <- a Q + (1-a) P)
-        const float Q = gxx + gA;
+        const float z = r.r4.w * f.rd;  // camera depth of the hit
+        const float Q = fmaf(gZ, z, gxx + gA);
         const float ga = (Q - P) * Tb;
         P = fmaf(f.alpha, Q, om * P);
         Tcur = Tb;
@@ -176,7 +179,9 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         const float gv = fmaf(dys, Ts6, -gG * f.G * f.v);
         // u = un / den, v = vn / den
         const float gun = gu * f.rd, gvn = gv * f.rd;
-        const float gden = -(gu * f.u + gv * f.v) * f.rd;
+        // z = D / den enters through den and D (dL/dz = wgt gZ)
+        const float gzw = wgt * gZ;
+        const float gden = -fmaf(gzw, z, gu * f.u + gv * f.v) * f.rd;
         {
           const float2 XY = f2(xp, yp);
           const float2 a0 = mul2(f2(gun, gun), XY), a1 = mul2(f2(gvn, gvn), XY), a2 = mul2(f2(gden, gden), XY);
@@ -196,10 +201,11 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         gi[10] = fmaf(nw1, gn2, -nw2 * gn1);
         gi[11] = fmaf(nw2, gn0, -nw0 * gn2);
         gi[12] = fmaf(nw0, gn1, -nw1 * gn0);
+        gi[13] = gzw * f.rd;  // dL/dD
       }
-      // per-splat record gradients (13 values): transpose through shared
+      // per-splat record gradients (14 values): transpose through shared
       // memory (value-major, rows padded to 36 floats so the 16-byte reads
-      // below are conflict-free), then lane L < 13 adds up value L of all
+      // below are conflict-free), then lane L < 14 adds up value L of all
       // 32 lanes with a tree and issues one reduction per warp
       if (!ok) {
 #pragma unroll

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Recor
 
   float Tr = 1.f;
   float Acc = 0.f;  // coverage as the blended sum (Eq. 3 with a = 1): exact where 1 - T cancels
+  float Zs = 0.f;   // blended camera depth of the hits (saved renders)
   float X[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) X[c] = 0.f;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Recor
           r.r3 = __ldg(rp + 3);
           r.r4 = __ldg(rp + 4);
           if (ok) {
-            const long long splat = (long long)__float_as_int(r.r4.w);
+            const long long splat = (long long)s_it[warp][t] - V.item_off;
             float x[8];
             if (SMP == SMP_SOFTWARE) {
               const TexSample ts_ = tex_setup(f.u, f.v, T);
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Recor
               X[2 * q + 1] = o.y;
             }
             Acc += w;
+            if (SAVE) Zs = fmaf(w, r.r4.w * f.rd, Zs);  // depth channel: z = D / den
             Tr = Tr * (1.f - f.alpha);
             last = (int)(c0 + t);
             if (STATS) ++n_blend;
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_fwd(ViewTable vt, const Recor
       V.gbuf[2 * pix + 1] = make_float4(X[4], X[5], X[6], X[7]);
       V.trans[pix] = Tr;
       V.acc[pix] = Acc;
+      V.zsum[pix] = Zs;
       V.last[pix] = last;
     }
   }

@@ -1,7 +1,9 @@
 // Shading adjoint (Eq. 10-12) as its own pass over all pixels of a batch.
 //
 // Each pixel turns dL/drgba into dL/dX (8 G-buffer channels) and dL/dA,
-// written for the backward rasteriser (3 x float4 per pixel), and scatters
+// adds the depth-normal loss's dL/dN, dL/dA and dL/d(blended depth) when
+// the view has them, writes them for the backward rasteriser (3 x float4 per
+// pixel: X 0-3, X 4-7, (A, depth)), and scatters
 // its gradient into the environment maps with bilinear / trilinear weights.
 // Environment maps are small and every pixel of a view hits them, so
 // atomics on them contend heavily: lanes that hit the same bilinear cell
@@ -170,9 +172,18 @@ __global__ void __launch_bounds__(SB_THREADS) k_shade_bwd(ViewTable vt, long lon
       const float4 dl = V.dl[pix];
       float gX[8], gA;
       shade_pixel_bwd(V.env, X, A, d, dl, gX, gA, eg);
+      float gZ = 0.f;
+      if (V.gnorm) {  // the depth-normal loss of this view (ts_normal_loss)
+        const float4 gn = V.gnorm[pix];
+        gX[5] += gn.x;
+        gX[6] += gn.y;
+        gX[7] += gn.z;
+        gA += gn.w;
+        gZ = V.gzsum[pix];
+      }
       gxa[3 * p] = make_float4(gX[0], gX[1], gX[2], gX[3]);
       gxa[3 * p + 1] = make_float4(gX[4], gX[5], gX[6], gX[7]);
-      gxa[3 * p + 2] = make_float4(gA, 0.f, 0.f, 0.f);
+      gxa[3 * p + 2] = make_float4(gA, gZ, 0.f, 0.f);
     }
     if (want_env) {
       const EnvDesc& E = vt.v[0].env;

@@ -31,8 +31,9 @@ __host__ __device__ constexpr float kNdotVMin() { return 1e-4f; }
 
 // Per-item record gradients summed by the backward rasteriser (float64):
 // 0-8 d/d(h_u, h_v, h_w), 9 d/do, 10-12 the torque of the normal-mapping
-// frame; stride 14 keeps rows 16-byte aligned.
-constexpr int kRecGrads = 13;
+// frame, 13 d/dD (through the depth channel); stride 14 keeps rows 16-byte
+// aligned.
+constexpr int kRecGrads = 14;
 constexpr int kRecGradStride = 14;
 
 enum Dtype : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
@@ -84,6 +85,9 @@ struct ViewDesc {
   float4* gbuf;   // [H][W][2] (X of Eq. 9, 8 channels)
   float* trans;   // [H][W]
   float* acc;     // [H][W] blended coverage A = sum alpha_i T_i (not 1 - T: no cancellation)
+  float* zsum;    // [H][W] blended camera depth of the hits, sum alpha_i T_i z_i (saved renders)
+  const float4* gnorm;  // [H][W] extra dL/dN (xyz), dL/dA (w) from the depth-normal loss, or NULL
+  const float* gzsum;   // [H][W] dL/d zsum from the depth-normal loss, or NULL
   int* last;      // [H][W]
   const float4* dl;  // backward input dL/drgba [H][W]
 };
@@ -102,13 +106,15 @@ struct ViewTable {
 // intersection, Sec. 3.1).  tu, tv, nf: world-space tangent frame with the
 // normal turned towards the camera (for normal mapping, Eq. 7).  The h_u and
 // h_v coefficients are interleaved so that (u, v) numerators evaluate as
-// channel pairs from adjacent registers.
+// channel pairs from adjacent registers.  D = p_c . n_c (camera space) makes
+// the camera depth of the hit z = D / (h_w . x) (Eq. 1: the ray meets the
+// splat plane).  The splat of an item is item - item_off of its view.
 struct Record {
   float4 r0;  // hu0 hv0 hu1 hv1
   float4 r1;  // hu2 hv2 hw0 hw1
   float4 r2;  // hw2 opacity tu0 tu1
   float4 r3;  // tu2 tv0 tv1 tv2
-  float4 r4;  // nf0 nf1 nf2 (splat id bits)
+  float4 r4;  // nf0 nf1 nf2 D
 };
 static_assert(sizeof(Record) == 80, "record is 5 x 16 B");
 

@@ -358,13 +358,17 @@ def scene_texels(scene: Scene):
 
 class Trainer:
     """Multi-view training step on one scene, all in library kernels: a
-    batched forward of V views (saved state), the L1 loss of each view, one
+    batched forward of V views (saved state), the loss of each view (L1, or
+    L1 + D-SSIM, plus the normal-consistency term when asked), one
     backward over the batch, then Adam on float32 masters of geometry and
     texels with the texel master written back into the scene's stored atlas
     (bf16 / f16 / f32) and the geometry updated in place."""
 
     def __init__(self, scene: Scene, data: dict, store: str = "bf16", lr_geom: float = 1e-4,
-                 lr_tex: float = 1e-2):
+                 lr_tex: float = 1e-2, lambda_dssim: float = 0.0, normal_weight: float = 0.0):
+        """lambda_dssim > 0 trains on (1 - lambda) L1 + lambda D-SSIM and
+        normal_weight > 0 adds normal_weight x L_n (the paper's objective,
+        Sec. 3.6: lambda 0.2); the defaults keep the plain L1 loss."""
         dev = torch.device("cuda", scene.device)
         f = lambda a: _dev_f32(a, dev).clone()  # noqa: E731
         self.scene, self.store = scene, store
@@ -376,6 +380,7 @@ class Trainer:
         self.lr = dict(means=lr_geom, quats=lr_geom, scales=lr_geom, opacity=lr_geom, texels=lr_tex)
         self.step_count = 0
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.lambda_dssim, self.normal_weight = float(lambda_dssim), float(normal_weight)
 
     def step(self, cams, targets, outs=None, dls=None):
         """One step over the views ``cams`` with target images ``targets``
@@ -386,7 +391,15 @@ class Trainer:
             dls = [torch.empty_like(o) for o in outs]
         losses = torch.zeros(n, dtype=torch.float32, device=outs[0].device)
         for i in range(n):
-            l1_loss(outs[i], targets[i], losses[i:i + 1], dls[i])
+            if self.lambda_dssim > 0.0:
+                image_loss(outs[i], targets[i], losses[i:i + 1], dls[i], self.lambda_dssim)
+            else:
+                l1_loss(outs[i], targets[i], losses[i:i + 1], dls[i])
+        if self.normal_weight > 0.0:
+            ln = torch.zeros(1, dtype=torch.float32, device=outs[0].device)
+            for i in range(n):
+                saved.normal_loss(ln, self.normal_weight, view=i)
+                losses[i:i + 1] += ln
         render_backward(saved, dls, self.grads)
         saved.release()
         self.step_count += 1

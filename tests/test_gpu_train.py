@@ -53,3 +53,18 @@ def test_training_steps_reduce_loss(P):
     losses = [tr.step(cams, targets).sum().item() for _ in range(30)]
     assert np.isfinite(losses).all()
     assert losses[-1] < 0.8 * losses[0], losses
+
+
+def test_training_with_the_paper_objective(P):
+    """0.8 L1 + 0.2 D-SSIM + 0.05 L_n (Sec. 3.6): finite and decreasing."""
+    scene = sg.make_scene(1, n=4000, T=8, seed=41)
+    env = sg.make_env(4, cube_res=16, irr_res=8, lut_res=32)
+    sc = P.Scene.from_arrays(scene, env, store="bf16")
+    cams = [sg.look_at_camera(e, 96, 96) for e in [(3.0, 0.5, 0.5), (0.5, 3.0, 0.2), (-2.0, -2.0, 1.0)]]
+    tgt_scene = dict(scene, texels=np.clip(scene["texels"] * 0.5 + 0.25, 0, 1).astype(np.float32))
+    tsc = P.Scene.from_arrays(tgt_scene, env)
+    targets = [P.render(tsc, c)[0].clone() for c in cams]
+    tr = P.Trainer(sc, scene, store="bf16", lr_tex=2e-2, lambda_dssim=0.2, normal_weight=0.05)
+    losses = [tr.step(cams, targets).sum().item() for _ in range(30)]
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.9 * losses[0], losses

@@ -27,7 +27,7 @@
 namespace ts {
 
 template <int DT, bool SAVE, bool STATS, int SMP>
-__global__ void __launch_bounds__(256, SAVE ? 3 : 4) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
+__global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
                                                      const uint32_t* __restrict__ pair_items,
                                                      const uint2* __restrict__ ranges,
                                                      unsigned long long* __restrict__ stats) {

@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-sampling", action="store_true", help="skip the texture-sampler comparison (Table 3 shape)")
     ap.add_argument("--sampling-only", action="store_true")
     ap.add_argument("--sampling-views", type=int, default=40)
+    ap.add_argument("--no-image-loss", action="store_true", help="skip the L1 + D-SSIM timing after the step")
+    ap.add_argument("--no-fp32-probe", action="store_true", help="skip the FP32 rate probe after the step")
     return ap.parse_args()
 
 
@@ -279,7 +281,7 @@ def run_ours(args):
     traffic = read_traffic(dom)
     # measured FP32 FMA rate of this GPU (after the timed region): context for
     # the derived peak above
-    meas_scalar, meas_paired = _lib.measure_fp32_peak(local)
+    meas_scalar, meas_paired = (float("nan"), float("nan")) if args.no_fp32_probe else _lib.measure_fp32_peak(local)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -294,14 +296,15 @@ def run_ours(args):
                          "peak_note": f"FP32 FMA peak {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                       f"(clock from {peak_kind} peaks)",
                          "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
-                         "peak_measured": {"scalar_fma_tflops": round(meas_scalar, 2),
-                                           "paired_fma_tflops": round(meas_paired, 2),
-                                           "frac_of_measured_scalar": achieved / meas_scalar}},
+                         "peak_measured": None if args.no_fp32_probe else {
+                             "scalar_fma_tflops": round(meas_scalar, 2), "paired_fma_tflops": round(meas_paired, 2),
+                             "frac_of_measured_scalar": achieved / meas_scalar}},
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "fragments_per_view": {k: int(v) for k, v in fr.items()},
             "gpu_launches": int(launches),
             "clocks": clocks}
-    line["image_loss"] = time_image_loss(P, out, targets[0], dev)
+    if not args.no_image_loss:
+        line["image_loss"] = time_image_loss(P, out, targets[0], dev)
     if not args.no_e2e:
         line["e2e"] = run_e2e(P, sc, my_cams, n_needed, args, dev, pg, world)
     if rank == 0 and not args.no_serve:

@@ -37,7 +37,9 @@ __device__ __forceinline__ bool eval_frag(const Record& r, float xp, float yp, F
 // whenever the homography's denominator keeps its sign over the block; the
 // splat is rejected only when all four corners lie beyond the same side of
 // the support square |u|, |v| <= 3 by a 0.1 % margin, far above the FP32
-// error of any pixel's (u, v).  Blocks the plane crosses edge-on are kept.
+// error of any pixel's (u, v), or when the bounding box of the corner images
+// lies outside the disc where the opacity cut alpha >= 1/255 can pass.
+// Blocks the plane crosses edge-on are kept.
 __device__ __forceinline__ bool block_may_hit(const Record& r, float x0, float x1, float y0, float y1) {
   float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
   float dmin = 3.0e38f, dmax = -3.0e38f;
@@ -55,7 +57,14 @@ __device__ __forceinline__ bool block_may_hit(const Record& r, float x0, float x
   }
   if (!(dmin > 0.f || dmax < 0.f)) return true;
   const float lim = 3.003f;
-  return !(umin > lim || umax < -lim || vmin > lim || vmax < -lim);
+  if (umin > lim || umax < -lim || vmin > lim || vmax < -lim) return false;
+  // alpha >= 1/255 needs o exp(-(u^2 + v^2)/2) >= 1/255, i.e. u^2 + v^2 <=
+  // 2 ln(255 o): reject when the box of the corner images misses that disc
+  // (0.2 % + 1e-3 margin, far above the FP32 error of (u, v) and of the
+  // exponential in eval_frag)
+  const float du = fmaxf(fmaxf(umin, -umax), 0.f), dv = fmaxf(fmaxf(vmin, -vmax), 0.f);
+  const float r2 = 2.f * __logf(255.f * r.r2.y);
+  return fmaf(du, du, dv * dv) <= fmaf(r2, 1.002f, 1e-3f);
 }
 
 struct TexSample {

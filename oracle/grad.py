@@ -24,7 +24,7 @@ PARAM_NAMES = ("means", "quats", "scales", "opacity", "texels")
 
 
 def render_grads(scene: dict, cam: dict, env: dict, dL_drgba: np.ndarray, *, tiles=None,
-                 keylist=None, max_entries=2_000_000, normal_weight: float = 0.0) -> dict:
+                 keylist=None, max_entries=2_000_000, normal_weight: float = 0.0, vis=None) -> dict:
     """Autograd gradients of sum(rgba * dL_drgba) w.r.t. every parameter.
 
     With ``normal_weight`` the objective adds normal_weight x L_n (the
@@ -36,7 +36,7 @@ def render_grads(scene: dict, cam: dict, env: dict, dL_drgba: np.ndarray, *, til
     envp = R.env_params(env, requires_grad=True)
     g = torch.from_numpy(np.asarray(dL_drgba, dtype=np.float64))
     out = R.render(scene, cam, env, params=params, envp=envp, tiles=tiles, margins=None,
-                   max_entries=max_entries, keylist=keylist)
+                   max_entries=max_entries, keylist=keylist, vis=vis)
     S = (out["rgba"] * g).sum()
     if normal_weight:
         from .loss import depth_normal_loss
@@ -44,23 +44,25 @@ def render_grads(scene: dict, cam: dict, env: dict, dL_drgba: np.ndarray, *, til
         S = S + normal_weight * Ln
     S.backward()
     res = {k: params[k].grad.numpy().copy() for k in PARAM_NAMES}
+    if "sh" in params:
+        res["sh"] = params["sh"].grad.numpy().copy()
     res["spec"] = [m.grad.numpy().copy() for m in envp["spec"]]
     res["irr"] = envp["irr"].grad.numpy().copy()
     res["rgba"] = out["rgba"].detach().numpy()
     return res
 
 
-def scalar_objective(scene: dict, cam: dict, env: dict, dL_drgba: np.ndarray, keylist=None) -> float:
+def scalar_objective(scene: dict, cam: dict, env: dict, dL_drgba: np.ndarray, keylist=None, vis=None) -> float:
     """S = sum(rgba * dL_drgba) of the FP64 forward (for finite differences).
 
     The key list (tile binning, culling, order) is held fixed by passing the
     unperturbed one, so a difference quotient sees only the smooth part."""
-    out = R.render(scene, cam, env, margins=None, keylist=keylist)
+    out = R.render(scene, cam, env, margins=None, keylist=keylist, vis=vis)
     return float((out["rgba"] * torch.from_numpy(np.asarray(dL_drgba, dtype=np.float64))).sum())
 
 
 def central_difference(scene: dict, cam: dict, env: dict, dL_drgba, name: str, index, h: float,
-                       keylist=None) -> float:
+                       keylist=None, vis=None) -> float:
     """(S(x + h e) - S(x - h e)) / 2h for one parameter entry.  ``name`` is a
     scene key, or ('spec', level) / 'irr' for the environment maps.  Values
     are perturbed in float64 copies (no float32 rounding of the step)."""
@@ -75,6 +77,6 @@ def central_difference(scene: dict, cam: dict, env: dict, dL_drgba, name: str, i
             ev["irr"][index] += sign * h
         else:
             sc[name][index] += sign * h
-        return scalar_objective(sc, cam, ev, dL_drgba, keylist=keylist)
+        return scalar_objective(sc, cam, ev, dL_drgba, keylist=keylist, vis=vis)
 
     return (perturbed(+1.0) - perturbed(-1.0)) / (2.0 * h)

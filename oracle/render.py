@@ -21,6 +21,10 @@ splat):
   blending   X = sum_i x_i alpha_i prod_{j<i}(1 - alpha_j)  (Eq. 3, Eq. 8-9)
              A = sum_i alpha_i prod_{j<i}(1 - alpha_j); stop after the first
              fragment that brings the transmittance below 1e-4
+  depth      Z = sum_i w_i tau_i (blended camera depth of the hits)
+  indirect   with per-splat SH coefficients c_k (degree <= 2, reading R19):
+             l_i = c_k . Y(w_r,i), w_r,i the reflection of w_o = -d/|d| about
+             the fragment's normalised normal; Xind = sum_i w_i l_i (Eq. 9)
   shading    see shading.py                               (Eq. 10-12)
 
 Products along a pixel's list are cumulative products and sums cumulative sums
@@ -51,9 +55,10 @@ NEAR = float(K.NEAR)
 
 
 def to_params(scene: dict, requires_grad: bool = False) -> dict:
-    """Float64 torch leaves of the splat parameters."""
+    """Float64 torch leaves of the splat parameters (and of the per-splat
+    indirect-light SH coefficients 'sh' [n, K, 3] when the scene has them)."""
     out = {}
-    for k in ("means", "quats", "scales", "opacity", "texels"):
+    for k in ("means", "quats", "scales", "opacity", "texels") + (("sh",) if "sh" in scene else ()):
         t = torch.from_numpy(np.asarray(scene[k], dtype=np.float64).copy())
         t.requires_grad_(requires_grad)
         out[k] = t
@@ -163,10 +168,26 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
     # ray has camera-space z component 1, so tau is the camera depth)
     tau_s = torch.where(blended, tau, torch.zeros_like(tau))
     Z = torch.cumsum(w * tau_s, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
+    Xind = None
+    if "sh" in params:
+        # indirect light (Sec. 3.5, Eq. 9 and 12): each fragment evaluates its
+        # splat's SH coefficients in the reflection direction of its own
+        # (normal-mapped, normalised) normal; the results are blended
+        from .shading import sh_basis
+        wo = -(d / torch.linalg.vector_norm(d, dim=-1, keepdim=True))[:, None, :]
+        nl = torch.linalg.vector_norm(n_w, dim=-1, keepdim=True)
+        nz = nl >= 1e-12
+        nh = torch.where(nz, n_w / torch.where(nz, nl, torch.ones_like(nl)), wo.expand_as(n_w))
+        ndw = (nh * wo).sum(-1, keepdim=True)
+        wr = 2.0 * ndw * nh - wo
+        sh = params["sh"][ci]                                   # [P,L,K,3]
+        Y = sh_basis(wr, sh.shape[-2])                          # [P,L,K]
+        lind = (Y[..., None] * sh).sum(-2)                      # [P,L,3]
+        Xind = torch.cumsum(w[..., None] * lind, dim=1)[:, -1, :] if L > 0 else torch.zeros(P, 3, dtype=F64)
     ab = torch.where(blended, a, torch.zeros_like(a))
     T_final = torch.cumprod(1.0 - ab, dim=1)[:, -1] if L > 0 else torch.ones(P, dtype=F64)
 
-    out = dict(X=X, A=A, Z=Z, T=T_final, ray_d=d, blended=blended, valid=valid, T_before=T_before)
+    out = dict(X=X, A=A, Z=Z, Xind=Xind, T=T_final, ray_d=d, blended=blended, valid=valid, T_before=T_before)
     with torch.no_grad():
         evaluated = (T_before >= T_MIN) & ~pad
         out["n_eval"] = evaluated.sum(1)
@@ -238,9 +259,12 @@ DEFAULT_MARGINS = (3e-5, 1e-5, 2e-4, 1e-7)
 
 
 def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=False,
-           tiles=None, margins=DEFAULT_MARGINS, max_entries=4_000_000, keylist=None) -> dict:
+           tiles=None, margins=DEFAULT_MARGINS, max_entries=4_000_000, keylist=None, vis=None) -> dict:
     """Render the view (or the listed ``tiles``) in float64.
 
+    With per-splat SH in the scene ('sh' [n, K, 3]) the fragments also blend
+    their indirect light (Xind [H,W,3]) and ``vis`` [H,W] (visibility V,
+    default 1) mixes it into the specular term.
     Returns rgba [H,W,4], the G-buffer X [H,W,8], A, the blended depth Z
     (sum of alpha T times the hit's camera depth), T_final, the ambiguity
     mask, fragment counts (evaluated / contributing), the last contributor
@@ -261,6 +285,8 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
     Xb = torch.zeros(H, W, 8, dtype=F64)
     Ab = torch.zeros(H, W, dtype=F64)
     Zb = torch.zeros(H, W, dtype=F64)
+    Ib = torch.zeros(H, W, 3, dtype=F64)
+    vis_t = None if vis is None else torch.from_numpy(np.asarray(vis, dtype=np.float64))
     Tb = torch.ones(H, W, dtype=F64)
     amb = torch.zeros(H, W, dtype=torch.bool)
     gamb = torch.zeros(H, W, dtype=torch.bool)
@@ -290,12 +316,15 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         px = np.concatenate(pxs)
         py = np.concatenate(pys)
         fr = fragments(params, cam, px, py, torch.from_numpy(cm), margins)
-        col = shade(fr["X"], fr["A"], fr["ray_d"], envp)
         pyt, pxt = torch.from_numpy(py), torch.from_numpy(px)
+        col = shade(fr["X"], fr["A"], fr["ray_d"], envp, Xind=fr["Xind"],
+                    vis=None if vis_t is None else vis_t[pyt, pxt])
         rgba.index_put_((pyt, pxt), col)
         Xb.index_put_((pyt, pxt), fr["X"])
         Ab.index_put_((pyt, pxt), fr["A"])
         Zb.index_put_((pyt, pxt), fr["Z"])
+        if fr["Xind"] is not None:
+            Ib.index_put_((pyt, pxt), fr["Xind"])
         Tb.index_put_((pyt, pxt), fr["T"])
         n_eval[pyt, pxt] = fr["n_eval"]
         n_con[pyt, pxt] = fr["n_contrib"]
@@ -317,12 +346,12 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         size += ent
     if chunk:
         run_chunk(chunk)
-    return dict(rgba=rgba, X=Xb, A=Ab, Z=Zb, T=Tb, ambiguous=amb, grad_ambiguous=gamb, n_eval=n_eval,
+    return dict(rgba=rgba, X=Xb, A=Ab, Z=Zb, Xind=Ib, T=Tb, ambiguous=amb, grad_ambiguous=gamb, n_eval=n_eval,
                 n_contrib=n_con, last=last, covered=covered, keys=kl)
 
 
 def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, params=None,
-                  envp=None, margins=DEFAULT_MARGINS) -> dict:
+                  envp=None, margins=DEFAULT_MARGINS, vis=None) -> dict:
     """Render individual pixels (px, py) from their tiles' lists: the sampled
     check used at sizes where a whole image would take too long."""
     kl = keylist if keylist is not None else K.build_keys(scene, cam)
@@ -337,7 +366,8 @@ def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, pa
     for i, c in enumerate(cands):
         cm[i, :c.size] = c
     fr = fragments(params, cam, px, py, torch.from_numpy(cm), margins)
-    col = shade(fr["X"], fr["A"], fr["ray_d"], envp)
+    vis_p = None if vis is None else torch.from_numpy(np.asarray(vis, dtype=np.float64)[np.asarray(py), np.asarray(px)])
+    col = shade(fr["X"], fr["A"], fr["ray_d"], envp, Xind=fr["Xind"], vis=vis_p)
     amb = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
     gamb = amb | fr["kink"] | shading_kinks(fr["X"].detach(), fr["A"].detach(), fr["ray_d"], envp)
     return dict(rgba=col, X=fr["X"], A=fr["A"], Z=fr["Z"], T=fr["T"], ambiguous=amb, grad_ambiguous=gamb,

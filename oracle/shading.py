@@ -117,12 +117,37 @@ def lut_sample(lut: torch.Tensor, ndotv: torch.Tensor, rough: torch.Tensor):
     return bilinear_2d(lut, ndotv * R_n - 0.5, rough * R_r - 0.5)
 
 
-def shade(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, env: dict):
+# Real spherical harmonics up to degree 2 (the convention of the 3DGS line):
+# Y_0 = 1/(2 sqrt(pi)); degree 1: -c1 y, c1 z, -c1 x with c1 = sqrt(3/(4 pi));
+# degree 2: c2 xy, -c2 yz, c3 (2 z^2 - x^2 - y^2), -c2 xz, c4 (x^2 - y^2) with
+# c2 = sqrt(15/(4 pi)), c3 = sqrt(5/(16 pi)), c4 = sqrt(15/(16 pi)).
+SH_C0 = 0.5 / math.sqrt(math.pi)
+SH_C1 = math.sqrt(3.0 / (4.0 * math.pi))
+SH_C2 = math.sqrt(15.0 / (4.0 * math.pi))
+SH_C3 = math.sqrt(5.0 / (16.0 * math.pi))
+SH_C4 = math.sqrt(15.0 / (16.0 * math.pi))
+
+
+def sh_basis(w: torch.Tensor, K: int) -> torch.Tensor:
+    """[..., 3] unit directions -> [..., K] basis values, K in {1, 4, 9}."""
+    x, y, z = w[..., 0], w[..., 1], w[..., 2]
+    cols = [torch.full_like(x, SH_C0)]
+    if K > 1:
+        cols += [-SH_C1 * y, SH_C1 * z, -SH_C1 * x]
+    if K > 4:
+        cols += [SH_C2 * x * y, -SH_C2 * y * z, SH_C3 * (2.0 * z * z - x * x - y * y), -SH_C2 * x * z,
+                 SH_C4 * (x * x - y * y)]
+    return torch.stack(cols, -1)
+
+
+def shade(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, env: dict, Xind=None, vis=None):
     """Deferred shading of G-buffer pixels.
 
     X [P,8] blended (albedo RGB, metallic, roughness, normal xyz); A [P] the
     blended coverage; ray_d [P,3] world-space pixel ray directions; env holds
-    torch tensors 'spec' (list of mips), 'irr', 'lut'.  Returns RGBA [P,4].
+    torch tensors 'spec' (list of mips), 'irr', 'lut'.  With Xind [P,3] (the
+    blended indirect light) and vis [P] (visibility V in [0, 1]) the specular
+    light is V C_spec + (1 - V) Xind / A (Eq. 12 with L_ind).  Returns RGBA [P,4].
     """
     P = X.shape[0]
     ok = A >= A_MIN
@@ -144,6 +169,9 @@ def shade(X: torch.Tensor, A: torch.Tensor, ray_d: torch.Tensor, env: dict):
     L = len(env["spec"])
     spec = cube_sample_lod(env["spec"], wr, rc * float(L - 1))
     irr = cube_sample(env["irr"], Nh)
+    if Xind is not None:
+        v = (torch.ones_like(A) if vis is None else vis)[:, None]
+        spec = v * spec + (1.0 - v) * Xind / A_s[:, None]
     Ls = (f0 * lt[:, 0:1] + lt[:, 1:2]) * spec
     Ld = lam / math.pi * (1.0 - met[:, None]) * irr
     col = A_s[:, None] * (Ld + Ls)

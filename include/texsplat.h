@@ -47,12 +47,17 @@ typedef enum ts_dtype { TS_F32 = 0, TS_BF16 = 1, TS_F16 = 2 } ts_dtype;
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  R is the
  * world->camera rotation (row-major), t the world->camera translation, so a
  * world point X maps to R X + t.  Pixel centres are at (i + 0.5, j + 0.5).
- * width, height >= 1. */
+ * width, height >= 1.  visibility: NULL, or a caller-owned device array
+ * [height][width] of the view's visibility V in [0, 1] (Eq. 12: the specular
+ * light is V C_spec + (1 - V) L_ind); read by the render and, for a saved
+ * render, by its backward, so it must stay valid until both ran.  Without
+ * per-splat SH (ts_upload_indirect) L_ind is 0. */
 typedef struct ts_camera {
   float R[9];
   float t[3];
   float fx, fy, cx, cy;
   int32_t width, height;
+  const float* visibility;
 } ts_camera;
 
 typedef struct ts_scene ts_scene;  /* library-owned splats, texels, environment */
@@ -63,7 +68,8 @@ typedef struct ts_saved ts_saved;  /* library-owned forward state for the backwa
  * the uploads: means [n][3], quats [n][4] (w,x,y,z; gradient w.r.t. the
  * uploaded, unnormalised quaternion), scales [n][2] (linear), opacity [n]
  * (linear), texels [n][T][T][8] (float32 whatever the stored dtype), spec
- * (all mip levels concatenated, [6][R_l][R_l][3] each), irr [6][R][R][3]. */
+ * (all mip levels concatenated, [6][R_l][R_l][3] each), irr [6][R][R][3],
+ * sh [n][K][3] (the indirect-light SH coefficients, K = (degree + 1)^2). */
 typedef struct ts_grads {
   float* means;
   float* quats;
@@ -72,6 +78,7 @@ typedef struct ts_grads {
   float* texels;
   float* spec;
   float* irr;
+  float* sh;
 } ts_grads;
 
 /* Fragment statistics of one forward (for roofline accounting). */
@@ -234,6 +241,21 @@ ts_status ts_saved_copy_depth(const ts_saved* saved, int view, float* zsum, floa
  * `loss`; stream-ordered (first call on a view allocates its buffers).
  * Errors: TS_ERR_ARG (NULL, bad view, negative weight), TS_ERR_CUDA. */
 ts_status ts_normal_loss(ts_saved* saved, int view, float weight, float* loss, void* stream);
+
+/* ---- indirect light (Eq. 9, Eq. 12) ---------------------------------------- */
+
+/* Per-splat indirect light: real SH coefficients of degree 0, 1 or 2 (the
+ * convention of 3DGS: K = 1, 4 or 9 basis functions), [n][K][3] float32 (RGB
+ * per basis function), copied to library memory (src_on_device selects the
+ * source side).  Each blended fragment evaluates its splat's SH in the
+ * reflection direction of its own normalised normal and the results are
+ * blended as a G-buffer channel L_ind; the pixel's visibility (ts_camera)
+ * mixes it into the specular light.  degree = -1 (coeffs ignored) removes
+ * the SH.  Renders of a scene with SH need the software sampler.  The
+ * upload synchronises `stream`.  Errors: TS_ERR_ARG (NULL scene, degree
+ * outside [-1, 2], NULL coeffs), TS_ERR_STATE (no geometry), TS_ERR_OOM,
+ * TS_ERR_CUDA. */
+ts_status ts_upload_indirect(ts_scene* scene, int degree, const float* coeffs, int src_on_device, void* stream);
 
 /* ---- hardware-texture atlas (test-time sampling) ------------------------- */
 

@@ -25,17 +25,18 @@ EXPORTED = [
     "ts_render_noalloc", "ts_scene_info", "ts_server_create", "ts_server_destroy", "ts_server_submit",
     "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
     "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
-    "ts_image_loss", "ts_saved_copy_depth", "ts_normal_loss",
+    "ts_image_loss", "ts_saved_copy_depth", "ts_normal_loss", "ts_upload_indirect",
 ]
 
 
 class TsCamera(C.Structure):
     _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
-                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("visibility", C.c_void_p)]
 
 
 class TsGrads(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("means", "quats", "scales", "opacity", "texels", "spec", "irr")]
+    _fields_ = [(n, C.c_void_p) for n in ("means", "quats", "scales", "opacity", "texels", "spec", "irr", "sh")]
 
 
 class TsFragStats(C.Structure):
@@ -106,6 +107,7 @@ def lib() -> C.CDLL:
         "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
         "ts_saved_copy_depth": [vp, i32, vp, vp, vp],
         "ts_normal_loss": [vp, i32, C.c_float, vp, vp],
+        "ts_upload_indirect": [vp, i32, vp, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -38,6 +38,10 @@ def make_camera(cam: dict) -> TsCamera:
         c.t[i] = float(t[i])
     c.fx, c.fy, c.cx, c.cy = (float(np.float32(cam[k])) for k in ("fx", "fy", "cx", "cy"))
     c.width, c.height = int(cam["W"]), int(cam["H"])
+    vis = cam.get("vis")  # optional [H, W] float32 CUDA tensor: visibility V (Eq. 12)
+    if vis is not None:
+        assert vis.is_cuda and vis.dtype == torch.float32 and vis.is_contiguous() and tuple(vis.shape) == (c.height, c.width)
+        c.visibility = vis.data_ptr()
     return c
 
 
@@ -88,6 +92,19 @@ class Scene:
               "ts_upload_atlas")
         self.T = T
 
+    def upload_indirect(self, coeffs, stream=None):
+        """Per-splat SH coefficients of the indirect light, [n, K, 3] with K in
+        {1, 4, 9} (degree 0-2); None removes them."""
+        if coeffs is None:
+            check(lib().ts_upload_indirect(self.handle, -1, None, 1, _stream(stream)), "ts_upload_indirect")
+            self.sh_K = 0
+            return
+        t = _dev_f32(coeffs, torch.device("cuda", self.device))
+        K = t.shape[1]
+        deg = {1: 0, 4: 1, 9: 2}[K]
+        check(lib().ts_upload_indirect(self.handle, deg, _ptr(t), 1, _stream(stream)), "ts_upload_indirect")
+        self.sh_K = K
+
     def build_atlas2d(self, store="f32", packing="splat_id", stream=None):
         """Packs the charts into the 2-D hardware-texture atlases (supplementary
         Sec. 1), in splat id order or the Morton order of the splat centres."""
@@ -120,6 +137,8 @@ class Scene:
         s.upload_gaussians(scene["means"], scene["quats"], scene["scales"], scene["opacity"])
         s.upload_atlas(scene["texels"], store)
         s.upload_envmap(env, env_store)
+        if "sh" in scene:
+            s.upload_indirect(scene["sh"])
         return s
 
 
@@ -216,8 +235,11 @@ def render_views(scenes: Sequence[Scene], cams: Sequence[dict], outs=None, save:
 def zero_grads(scene: Scene, device=None) -> dict:
     dev = device or torch.device("cuda", scene.device)
     z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=dev)  # noqa: E731
-    return dict(means=z(scene.n, 3), quats=z(scene.n, 4), scales=z(scene.n, 2), opacity=z(scene.n),
-                texels=z(scene.n, scene.T, scene.T, 8), spec=z(sum(scene.spec_sizes)), irr=z(scene.irr_size))
+    out = dict(means=z(scene.n, 3), quats=z(scene.n, 4), scales=z(scene.n, 2), opacity=z(scene.n),
+               texels=z(scene.n, scene.T, scene.T, 8), spec=z(sum(scene.spec_sizes)), irr=z(scene.irr_size))
+    if getattr(scene, "sh_K", 0):
+        out["sh"] = z(scene.n, scene.sh_K, 3)
+    return out
 
 
 def render_backward(saved: Saved, dL_drgba, grads: dict, stream=None):
@@ -227,7 +249,7 @@ def render_backward(saved: Saved, dL_drgba, grads: dict, stream=None):
     dls = [d.contiguous() for d in dls]
     arr = (C.c_void_p * len(dls))(*[d.data_ptr() for d in dls])
     g = TsGrads(*[grads.get(k).data_ptr() if grads.get(k) is not None else None
-                  for k in ("means", "quats", "scales", "opacity", "texels", "spec", "irr")])
+                  for k in ("means", "quats", "scales", "opacity", "texels", "spec", "irr", "sh")])
     check(lib().ts_render_backward(saved.handle, arr, C.byref(g), _stream(stream)), "ts_render_backward")
 
 

@@ -107,10 +107,15 @@ struct ts_scene {
   int64_t a2d_version = -1;  // tex_version the 2-D atlases were built from
   int64_t a2d_n = -1;
   int sampler = SMP_SOFTWARE;
+  // indirect light: SH coefficients [n][sh_stride] (K x 3 floats, padded to 4)
+  float* sh = nullptr;
+  int sh_deg = -1, sh_stride = 0;
+  int64_t sh_n = -1;
 };
 
 struct ts_saved {
   int device = 0;
+  bool indirect = false;  // the batch blended per-splat SH light
   cudaStream_t stream = nullptr;
   ViewTable vt;
   std::vector<ts_scene*> scenes;
@@ -139,7 +144,7 @@ static void free_atlas2d(ts_scene* s) {
 }
 
 static void free_scene_buffers(ts_scene* s) {
-  void* ptrs[] = {s->means, s->quats, s->scales, s->opacity, s->texels, s->spec, s->irr, s->lut};
+  void* ptrs[] = {s->means, s->quats, s->scales, s->opacity, s->texels, s->spec, s->irr, s->lut, s->sh};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_atlas2d(s);
@@ -354,6 +359,14 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
       return fail(TS_ERR_STATE, "ts_render_views: hardware sampler selected but the 2-D atlas is missing or stale");
   }
   const int sampler = scenes[0]->sampler;
+  bool indirect = false;
+  for (int i = 0; i < n_views; ++i) {
+    if (scenes[i]->sh && scenes[i]->sh_n != scenes[i]->n)
+      return fail(TS_ERR_STATE, "ts_render_views: SH coefficients stale (re-upload after geometry)");
+    indirect = indirect || (scenes[i]->sh != nullptr);
+  }
+  if (indirect && sampler != SMP_SOFTWARE)
+    return fail(TS_ERR_STATE, "ts_render_views: indirect light (SH) needs the software sampler");
   if (sampler != SMP_SOFTWARE && saved_out)
     return fail(TS_ERR_STATE, "ts_render_views: the hardware-atlas and flat samplers are inference-only (no saved state)");
   cudaStream_t st = (cudaStream_t)stream;
@@ -382,6 +395,10 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     V.atlas2d[0] = s->a2d_tex[0];
     V.atlas2d[1] = s->a2d_tex[1];
     V.chart = s->chart;
+    V.sh = s->sh;
+    V.sh_deg = s->sh ? s->sh_deg : 0;
+    V.sh_stride = s->sh_stride;
+    V.vis = c.visibility;
     fill_env(s, V.env);
     V.rgba = reinterpret_cast<float4*>(out_rgba[i]);
     tiles += (long long)V.tiles_x * V.tiles_y;
@@ -511,12 +528,14 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
       TS_CUDA_K(salloc((void**)&V.trans, np * sizeof(float)));
       TS_CUDA_K(salloc((void**)&V.acc, np * sizeof(float)));
       TS_CUDA_K(salloc((void**)&V.zsum, np * sizeof(float)));
+      if (indirect) TS_CUDA_K(salloc((void**)&V.gind, np * sizeof(float4)));
       TS_CUDA_K(salloc((void**)&V.last, np * sizeof(int)));
     }
   }
   {
     ProfScope p(st, "raster_fwd");
-    launch_raster_fwd(vt, rec, pitems, ranges, scenes[0]->tex_dtype, saved_out != nullptr, nullptr, sampler, st);
+    launch_raster_fwd(vt, rec, pitems, ranges, scenes[0]->tex_dtype, saved_out != nullptr, nullptr, sampler, indirect,
+                      st);
   }
   TS_CHECK_LAUNCH();
 
@@ -529,6 +548,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     sv->device = device;
     sv->stream = st;
     sv->vt = vt;
+    sv->indirect = indirect;
     sv->scenes.assign(scenes, scenes + n_views);
     sv->rec = rec;
     sv->pair_items = pitems;
@@ -577,6 +597,7 @@ ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, c
   g.opacity = grads->opacity;
   g.texels = grads->texels;
   g.irr = grads->irr;
+  g.sh = grads->sh;
   if (grads->spec) {
     for (int l = 0; l < s->levels; ++l) g.spec[l] = grads->spec + s->spec_off[l];
   }
@@ -588,13 +609,17 @@ ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, c
   TS_CUDA(tmp.alloc((void**)&g_items, (size_t)std::max(vt.n_items, 1) * kRecGradStride * sizeof(double)));
   TS_CUDA(tmp.alloc((void**)&gxa, (size_t)std::max(n_pix, 1ll) * 3 * sizeof(float4)));
   TS_CUDA(cudaMemsetAsync(g_items, 0, (size_t)std::max(vt.n_items, 1) * kRecGradStride * sizeof(double), st));
+  if (sv->indirect) {  // per-pixel dL/dX_ind between the shading and raster adjoints
+    for (int i = 0; i < vt.n_views; ++i)
+      TS_CUDA(tmp.alloc((void**)&vt.v[i].gxind, (size_t)vt.v[i].W * vt.v[i].H * sizeof(float4)));
+  }
   {
     ProfScope p(st, "shade_bwd");
     launch_shade_bwd(vt, gxa, g, st);
   }
   {
     ProfScope p(st, "raster_bwd");
-    launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, gxa, g_items, g, st);
+    launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, gxa, g_items, g, sv->indirect, st);
   }
   {
     ProfScope p(st, "preprocess_bwd");
@@ -694,7 +719,8 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   unsigned long long* d = nullptr;
   TS_CUDA(tmp.alloc((void**)&d, 2 * sizeof(unsigned long long)));
   TS_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st));
-  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, SMP_SOFTWARE, st);
+  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, SMP_SOFTWARE, false,
+                    st);
   TS_CHECK_LAUNCH();
   unsigned long long h[2] = {0, 0};
   TS_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -710,6 +736,35 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   int64_t vis = 0;
   for (uint32_t b : hb) vis += (b != 0xffffffffu);
   out->n_visible = vis;
+  return TS_OK;
+}
+
+ts_status ts_upload_indirect(ts_scene* s, int degree, const float* coeffs, int src_on_device, void* stream) {
+  if (!s) return fail(TS_ERR_ARG, "ts_upload_indirect: scene is NULL");
+  if (degree < -1 || degree > 2) return fail(TS_ERR_ARG, "ts_upload_indirect: degree must be -1, 0, 1 or 2");
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaSetDevice(s->device));
+  TS_CUDA(cudaStreamSynchronize(st));
+  if (s->sh) cudaFree(s->sh);
+  s->sh = nullptr;
+  s->sh_deg = -1;
+  s->sh_stride = 0;
+  s->sh_n = -1;
+  if (degree < 0) return TS_OK;
+  if (!s->means) return fail(TS_ERR_STATE, "ts_upload_indirect: geometry not uploaded");
+  if (s->n > 0 && !coeffs) return fail(TS_ERR_ARG, "ts_upload_indirect: coeffs is NULL");
+  const int K = (degree + 1) * (degree + 1);
+  const int stride = (3 * K + 3) & ~3;
+  const size_t n = (size_t)std::max<int64_t>(s->n, 1);
+  TS_CUDA(cudaMalloc(&s->sh, n * stride * sizeof(float)));
+  TS_CUDA(cudaMemsetAsync(s->sh, 0, n * stride * sizeof(float), st));
+  if (s->n > 0)
+    TS_CUDA(cudaMemcpy2DAsync(s->sh, stride * sizeof(float), coeffs, 3 * K * sizeof(float), 3 * K * sizeof(float),
+                              (size_t)s->n, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  s->sh_deg = degree;
+  s->sh_stride = stride;
+  s->sh_n = s->n;
   return TS_OK;
 }
 

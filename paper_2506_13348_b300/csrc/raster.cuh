@@ -142,6 +142,65 @@ __device__ __forceinline__ void normal_map(const Record& r, float x[8]) {
   x[7] = fmaf(a, r.r3.x, fmaf(b, r.r3.w, c * r.r4.z));
 }
 
+// ---- indirect light (Eq. 9, Eq. 12): per-splat SH in the reflection direction
+// Real SH normalisation constants up to degree 2.
+constexpr float kSH0 = 0.28209479177387814f;   // 1 / (2 sqrt(pi))
+constexpr float kSH1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+constexpr float kSH2 = 1.09254843059207907f;   // sqrt(15 / (4 pi))
+constexpr float kSH3 = 0.31539156525252005f;   // sqrt(5 / (16 pi))
+constexpr float kSH4 = 0.54627421529603959f;   // sqrt(15 / (16 pi))
+
+__device__ __forceinline__ void sh_basis(float3 w, int K, float Y[9]) {
+  Y[0] = kSH0;
+  if (K > 1) {
+    Y[1] = -kSH1 * w.y;
+    Y[2] = kSH1 * w.z;
+    Y[3] = -kSH1 * w.x;
+  }
+  if (K > 4) {
+    Y[4] = kSH2 * w.x * w.y;
+    Y[5] = -kSH2 * w.y * w.z;
+    Y[6] = kSH3 * (2.f * w.z * w.z - w.x * w.x - w.y * w.y);
+    Y[7] = -kSH2 * w.x * w.z;
+    Y[8] = kSH4 * (w.x * w.x - w.y * w.y);
+  }
+}
+
+// Reflection of w_o about the fragment's normalised normal n_w (w_o when n_w
+// vanishes): returns w_r and the pieces the adjoint needs.
+struct Refl {
+  float3 nh, wr;
+  float ndw, inl;
+};
+__device__ __forceinline__ Refl reflect_dir(float3 nw, float3 wo) {
+  Refl r;
+  const float n2 = nw.x * nw.x + nw.y * nw.y + nw.z * nw.z;
+  if (n2 >= 1e-24f) {
+    r.inl = rsqrtf(n2);
+    r.nh = make_float3(nw.x * r.inl, nw.y * r.inl, nw.z * r.inl);
+  } else {
+    r.inl = 0.f;
+    r.nh = wo;
+  }
+  r.ndw = r.nh.x * wo.x + r.nh.y * wo.y + r.nh.z * wo.z;
+  r.wr = make_float3(2.f * r.ndw * r.nh.x - wo.x, 2.f * r.ndw * r.nh.y - wo.y, 2.f * r.ndw * r.nh.z - wo.z);
+  return r;
+}
+
+// l = sum_j c_j Y_j(w_r) for the three channels; c rows are [K][3] floats.
+__device__ __forceinline__ float3 sh_eval(const float* __restrict__ c, int K, const float Y[9]) {
+  float3 l = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    if (j < K) {
+      l.x = fmaf(__ldg(c + 3 * j), Y[j], l.x);
+      l.y = fmaf(__ldg(c + 3 * j + 1), Y[j], l.y);
+      l.z = fmaf(__ldg(c + 3 * j + 2), Y[j], l.z);
+    }
+  }
+  return l;
+}
+
 __device__ __forceinline__ void pixel_of(int tile_local, int tiles_x, int& px, int& py) {
   int tx = tile_local % tiles_x, ty = tile_local / tiles_x;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

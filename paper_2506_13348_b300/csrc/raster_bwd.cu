@@ -23,14 +23,16 @@
 
 namespace ts {
 
-template <int DT>
-__global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
-                                                        const uint32_t* __restrict__ pair_items,
-                                                        const uint2* __restrict__ ranges,
-                                                        const float4* __restrict__ gxa, double* __restrict__ g_items,
-                                                        GradTable g) {
+template <int DT, bool IND>
+__global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
+                                                                  const uint32_t* __restrict__ pair_items,
+                                                                  const uint2* __restrict__ ranges,
+                                                                  const float4* __restrict__ gxa,
+                                                                  double* __restrict__ g_items, GradTable g) {
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ __align__(16) float s_gi[8][kRecGrads][36];  // record gradients, value-major, per warp
+  // indirect light: per lane dL/dl (3) and the SH basis (9), value-major
+  __shared__ __align__(16) float s_sh[IND ? 8 : 1][12][36];
   __shared__ float4 s_rec[8][32][5];               // the records of a chunk
   __shared__ uint32_t s_item[8][32];
   const int warp = threadIdx.x >> 5;
@@ -48,6 +50,9 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
   const int lane = threadIdx.x & 31;
 
   float gX[8], gA = 0.f, gZ = 0.f, Tcur = 1.f;
+  float gXi[3] = {0.f, 0.f, 0.f};  // dL/dX_ind (indirect light channel)
+  float3 wo = make_float3(0.f, 0.f, 1.f);
+  const int shK = (V.sh_deg + 1) * (V.sh_deg + 1);
   int last = -1;
 #pragma unroll
   for (int c = 0; c < 8; ++c) gX[c] = 0.f;
@@ -62,6 +67,15 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
     gZ = c.y;  // dL/d(blended depth), zero unless a depth loss is in use
     Tcur = V.trans[pix];
     last = V.last[pix];
+    if (IND) {
+      const float4 q = V.gxind[pix];
+      gXi[0] = q.x;
+      gXi[1] = q.y;
+      gXi[2] = q.z;
+      const float3 d = world_ray(V, xp, yp);
+      const float id = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+      wo = make_float3(-d.x * id, -d.y * id, -d.z * id);
+    }
   }
   const int hi = __reduce_max_sync(FULL, last);
 
@@ -113,6 +127,9 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
       TexSample ts_;
       ts_.ia = ts_.ib = ts_.ja = ts_.jb = 0;
       float gi[kRecGrads];
+      float shv[12];  // indirect light: dL/dl (3), basis Y (9)
+#pragma unroll
+      for (int q = 0; q < 12; ++q) shv[q] = 0.f;
       if (ok) {
         ts_ = tex_setup(f.u, f.v, T);
         const float om = 1.f - f.alpha;
@@ -135,6 +152,8 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         w4[0] = hx * hy; w4[1] = ts_.fx * hy; w4[2] = hx * ts_.fy; w4[3] = ts_.fx * ts_.fy;
         float2 nt01 = f2(0.f, 0.f), dxy = f2(0.f, 0.f);
         float nt2 = 0.f, gxx = 0.f;
+        // indirect light: d(tangent normal)/d(texel-space u, v)
+        float dnu[3] = {0.f, 0.f, 0.f}, dnv[3] = {0.f, 0.f, 0.f};
         const float2 g01 = f2(g8[0], g8[1]), g23 = f2(g8[2], g8[3]), g45 = f2(g8[4], g8[5]), g67 = f2(g8[6], g8[7]);
         const long long base = splat * (long long)T * T;
 #pragma unroll
@@ -154,13 +173,36 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
           const float wyk = (k & 2) ? ts_.fy : hy;
           const float wxk = (k & 1) ? ts_.fx : hx;
           dxy = fma2(f2((k & 1) ? wyk : -wyk, (k & 2) ? wxk : -wxk), f2(tdot, tdot), dxy);
+          if (IND) {
+            const float au = (k & 1) ? wyk : -wyk, av = (k & 2) ? wxk : -wxk;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              dnu[c] = fmaf(au, cv[5 + c], dnu[c]);
+              dnv[c] = fmaf(av, cv[5 + c], dnv[c]);
+            }
+          }
         }
         const float nt0 = nt01.x, nt1 = nt01.y;
         float dxs = dxy.x, dys = dxy.y;
+        // indirect light of the fragment: l = c . Y(w_r), w_r the reflection
+        // of w_o about normalize(n_w), n_w = [t_u t_v n_f] n^t (Eq. 7)
+        float lx = 0.f, ly = 0.f, lz = 0.f;
+        Refl rf;
+        if (IND && V.sh) {
+          const float3 nw = make_float3(fmaf(nt0, r.r2.z, fmaf(nt1, r.r3.y, nt2 * r.r4.x)),
+                                        fmaf(nt0, r.r2.w, fmaf(nt1, r.r3.z, nt2 * r.r4.y)),
+                                        fmaf(nt0, r.r3.x, fmaf(nt1, r.r3.w, nt2 * r.r4.z)));
+          rf = reflect_dir(nw, wo);
+          sh_basis(rf.wr, shK, shv + 3);
+          const float3 l = sh_eval(V.sh + splat * V.sh_stride, shK, shv + 3);
+          lx = l.x;
+          ly = l.y;
+          lz = l.z;
+        }
         // dL/dalpha = T_before (Q - P): Q = gX.x + gA of this fragment, P the
         // same projection of everything blended behind it (P <- a Q + (1-a) P)
         const float z = r.r4.w * f.rd;  // camera depth of the hit
-        const float Q = fmaf(gZ, z, gxx + gA);
+        const float Q = fmaf(gXi[0], lx, fmaf(gXi[1], ly, fmaf(gXi[2], lz, fmaf(gZ, z, gxx + gA))));
         const float ga = (Q - P) * Tb;
         P = fmaf(f.alpha, Q, om * P);
         Tcur = Tb;
@@ -172,7 +214,49 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         }
         dxs *= wgt;
         dys *= wgt;
-        const float gn0 = wgt * gX[5], gn1 = wgt * gX[6], gn2 = wgt * gX[7];
+        float gn0 = wgt * gX[5], gn1 = wgt * gX[6], gn2 = wgt * gX[7];
+        if (IND && V.sh) {
+          // dL/dl = wgt dL/dX_ind; through w_r into the fragment's normal
+          const float d0 = wgt * gXi[0], d1 = wgt * gXi[1], d2 = wgt * gXi[2];
+          shv[0] = d0;
+          shv[1] = d1;
+          shv[2] = d2;
+          const float* c = V.sh + splat * V.sh_stride;
+          float sj[9];
+#pragma unroll
+          for (int j = 0; j < 9; ++j)
+            sj[j] = j < shK ? fmaf(d0, __ldg(c + 3 * j), fmaf(d1, __ldg(c + 3 * j + 1), d2 * __ldg(c + 3 * j + 2))) : 0.f;
+          const float wx = rf.wr.x, wy = rf.wr.y, wz = rf.wr.z;
+          // sum_j s_j grad Y_j(w_r)
+          float gx = -kSH1 * sj[3], gy = -kSH1 * sj[1], gz = kSH1 * sj[2];
+          if (shK > 4) {
+            gx += kSH2 * (wy * sj[4] - wz * sj[7]) - 2.f * kSH3 * wx * sj[6] + 2.f * kSH4 * wx * sj[8];
+            gy += kSH2 * (wx * sj[4] - wz * sj[5]) - 2.f * kSH3 * wy * sj[6] - 2.f * kSH4 * wy * sj[8];
+            gz += -kSH2 * (wy * sj[5] + wx * sj[7]) + 4.f * kSH3 * wz * sj[6];
+          }
+          // w_r = 2 (n.w_o) n - w_o  ->  dL/dn = 2 ((n.w_o) g + (g.n) w_o)
+          const float gdn = gx * rf.nh.x + gy * rf.nh.y + gz * rf.nh.z;
+          float en0 = 2.f * (rf.ndw * gx + gdn * wo.x), en1 = 2.f * (rf.ndw * gy + gdn * wo.y);
+          float en2 = 2.f * (rf.ndw * gz + gdn * wo.z);
+          // n = n_w / |n_w|
+          const float pr = en0 * rf.nh.x + en1 * rf.nh.y + en2 * rf.nh.z;
+          en0 = (en0 - rf.nh.x * pr) * rf.inl;
+          en1 = (en1 - rf.nh.y * pr) * rf.inl;
+          en2 = (en2 - rf.nh.z * pr) * rf.inl;
+          // into the tangent normal (R'^T e): its texels, the texture
+          // coordinates it is interpolated at, and the frame's torque
+          const float et0 = r.r2.z * en0 + r.r2.w * en1 + r.r3.x * en2;
+          const float et1 = r.r3.y * en0 + r.r3.z * en1 + r.r3.w * en2;
+          const float et2 = r.r4.x * en0 + r.r4.y * en1 + r.r4.z * en2;
+          t8[5] += et0;
+          t8[6] += et1;
+          t8[7] += et2;
+          dxs = fmaf(et0, dnu[0], fmaf(et1, dnu[1], fmaf(et2, dnu[2], dxs)));
+          dys = fmaf(et0, dnv[0], fmaf(et1, dnv[1], fmaf(et2, dnv[2], dys)));
+          gn0 += en0;
+          gn1 += en1;
+          gn2 += en2;
+        }
         // alpha = min(0.99, o G), G = exp(-(u^2+v^2)/2)
         float go = 0.f, gG = 0.f;
         if (f.oG <= kAlphaMax()) {
@@ -236,6 +320,27 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
         if (s != 0.f) atomicAdd(g_items + (size_t)item * kRecGradStride + lane, (double)s);
       }
       __syncwarp();
+      // SH coefficient gradients of the splat: dL/dc_jc = sum over lanes of
+      // (dL/dl_c) Y_j -- lane v < 3K gathers its (c, j) products through
+      // shared memory and adds them once per warp
+      if (IND && V.sh) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) s_sh[IND ? warp : 0][q][lane] = shv[q];
+        __syncwarp();
+        if (lane < 3 * shK && g.sh) {
+          const int j = lane / 3, c = lane - 3 * j;
+          const float4* dc = reinterpret_cast<const float4*>(s_sh[IND ? warp : 0][c]);
+          const float4* yj = reinterpret_cast<const float4*>(s_sh[IND ? warp : 0][3 + j]);
+          float acc = 0.f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 a = dc[q], b = yj[q];
+            acc = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+          }
+          if (acc != 0.f) red_add(g.sh + splat * 3 * shK + lane, acc);
+        }
+        __syncwarp();
+      }
       // texel gradients: lanes are grouped by bilinear cell (the four texels
       // they interpolate).  A lane whose cell at most kDirect live lanes share
       // adds its own four corners (16-byte vector reductions); each larger
@@ -316,14 +421,21 @@ __global__ void __launch_bounds__(256, 3) k_raster_bwd(ViewTable vt, const Recor
 
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
-                       const GradTable& g, cudaStream_t st) {
+                       const GradTable& g, bool indirect, cudaStream_t st) {
   dim3 grid(vt.n_tiles), block(256);
-  if (tex_dtype == DT_F32)
-    k_raster_bwd<DT_F32><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
-  else if (tex_dtype == DT_BF16)
-    k_raster_bwd<DT_BF16><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
-  else
-    k_raster_bwd<DT_F16><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
+#define TS_LAUNCH_B(DTV)                                                                              \
+  if (indirect)                                                                                       \
+    k_raster_bwd<DTV, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);   \
+  else                                                                                                \
+    k_raster_bwd<DTV, false><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
+  if (tex_dtype == DT_F32) {
+    TS_LAUNCH_B(DT_F32)
+  } else if (tex_dtype == DT_BF16) {
+    TS_LAUNCH_B(DT_BF16)
+  } else {
+    TS_LAUNCH_B(DT_F16)
+  }
+#undef TS_LAUNCH_B
   note_launches(1);
 }
 

@@ -26,7 +26,7 @@
 
 namespace ts {
 
-template <int DT, bool SAVE, bool STATS, int SMP>
+template <int DT, bool SAVE, bool STATS, int SMP, bool IND = false>
 __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
                                                      const uint32_t* __restrict__ pair_items,
                                                      const uint2* __restrict__ ranges,
@@ -57,6 +57,15 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
   int stop = -1;  // list index at which the pixel terminated (statistics)
   bool done = !inside;
   unsigned n_blend = 0;
+  // indirect light: w_o of the pixel and the blended SH light of the fragments
+  float3 wo = make_float3(0.f, 0.f, 1.f);
+  float Xi[3] = {0.f, 0.f, 0.f};
+  const int shK = (V.sh_deg + 1) * (V.sh_deg + 1);
+  if (IND) {
+    const float3 d = world_ray(V, xp, yp);
+    const float id = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    wo = make_float3(-d.x * id, -d.y * id, -d.z * id);
+  }
 
   // per-warp walk: no CTA barrier; lane t stages entry c0 + t's first 48
   // bytes in shared memory for the block test and the lockstep loop
@@ -108,6 +117,17 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
             }
             normal_map(r, x);
             const float w = f.alpha * Tr;
+            if (IND && V.sh) {
+              // the splat's SH light in the reflection direction of this
+              // fragment's normal (Eq. 9: blended like the other channels)
+              const Refl rf = reflect_dir(make_float3(x[5], x[6], x[7]), wo);
+              float Y[9];
+              sh_basis(rf.wr, shK, Y);
+              const float3 l = sh_eval(V.sh + splat * V.sh_stride, shK, Y);
+              Xi[0] = fmaf(w, l.x, Xi[0]);
+              Xi[1] = fmaf(w, l.y, Xi[1]);
+              Xi[2] = fmaf(w, l.z, Xi[2]);
+            }
             const float2 W2 = f2(w, w);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -135,7 +155,9 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
     const int pix = py * V.W + px;
     const float A = Acc;
     float3 d = world_ray(V, xp, yp);
-    V.rgba[pix] = shade_pixel(V.env, X, A, d, nullptr);
+    V.rgba[pix] = IND ? shade_pixel(V.env, X, A, d, nullptr, Xi, V.vis ? V.vis[pix] : 1.f)
+                      : shade_pixel(V.env, X, A, d, nullptr);
+    if (SAVE && IND) V.gind[pix] = make_float4(Xi[0], Xi[1], Xi[2], 0.f);
     if (SAVE) {
       V.gbuf[2 * pix] = make_float4(X[0], X[1], X[2], X[3]);
       V.gbuf[2 * pix + 1] = make_float4(X[4], X[5], X[6], X[7]);
@@ -164,7 +186,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
 
 void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
-                       cudaStream_t st) {
+                       bool indirect, cudaStream_t st) {
   dim3 grid(vt.n_tiles), block(256);
   if (sampler == SMP_HW_ATLAS) {  // inference only; the atlas dtype is the texture's
     k_raster_fwd<DT_F32, false, false, SMP_HW_ATLAS><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
@@ -176,8 +198,12 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
     k_raster_fwd<DTV, false, false, SMP_FLAT><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
   else if (stats)                                                                                         \
     k_raster_fwd<DTV, false, true, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
+  else if (save && indirect)                                                                              \
+    k_raster_fwd<DTV, true, false, SMP_SOFTWARE, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
   else if (save)                                                                                          \
     k_raster_fwd<DTV, true, false, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
+  else if (indirect)                                                                                      \
+    k_raster_fwd<DTV, false, false, SMP_SOFTWARE, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
   else                                                                                                    \
     k_raster_fwd<DTV, false, false, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
   if (tex_dtype == DT_F32) {

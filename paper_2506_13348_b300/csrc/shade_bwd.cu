@@ -128,8 +128,11 @@ __device__ __forceinline__ void warp_cell_scatter(const EnvTarget& tg, bool live
   }
 }
 
-__global__ void __launch_bounds__(SB_THREADS) k_shade_bwd(ViewTable vt, long long n_pix, float4* __restrict__ gxa,
-                                                          GradTable g, EnvGradLayout lay, int use_smem) {
+// IND: the views blended per-splat indirect light (mixed by the visibility);
+// a separate instance so the plain path keeps its register budget.
+template <bool IND>
+__global__ void __launch_bounds__(SB_THREADS, 2) k_shade_bwd(ViewTable vt, long long n_pix, float4* __restrict__ gxa,
+                                                             GradTable g, EnvGradLayout lay, int use_smem) {
   extern __shared__ float s_env[];
   const bool want_env = (g.irr != nullptr) || (g.spec[0] != nullptr);
   const bool shared = use_smem && want_env;
@@ -171,7 +174,15 @@ __global__ void __launch_bounds__(SB_THREADS) k_shade_bwd(ViewTable vt, long lon
       const float3 d = world_ray(V, xp, yp);
       const float4 dl = V.dl[pix];
       float gX[8], gA;
-      shade_pixel_bwd(V.env, X, A, d, dl, gX, gA, eg);
+      if (IND) {
+        const float4 xi = V.gind[pix];
+        const float ind[3] = {xi.x, xi.y, xi.z};
+        float gind[3];
+        shade_pixel_bwd(V.env, X, A, d, dl, gX, gA, eg, ind, V.vis ? V.vis[pix] : 1.f, gind);
+        V.gxind[pix] = make_float4(gind[0], gind[1], gind[2], 0.f);
+      } else {
+        shade_pixel_bwd(V.env, X, A, d, dl, gX, gA, eg);
+      }
       float gZ = 0.f;
       if (V.gnorm) {  // the depth-normal loss of this view (ts_normal_loss)
         const float4 gn = V.gnorm[pix];
@@ -232,7 +243,8 @@ void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cuda
   const size_t smem = use_smem ? (size_t)tot * sizeof(float) : 0;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_shade_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_MAX_SMEM_FLOATS * 4);
+    cudaFuncSetAttribute(k_shade_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_MAX_SMEM_FLOATS * 4);
+    cudaFuncSetAttribute(k_shade_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_MAX_SMEM_FLOATS * 4);
     attr_set = true;
   }
   int dev = 0, sms = 148;
@@ -241,7 +253,11 @@ void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cuda
   const long long want = (n_pix + SB_THREADS - 1) / SB_THREADS;
   const int per_sm = use_smem ? 2 : 8;
   const int grid = (int)((want < (long long)sms * per_sm) ? want : (long long)sms * per_sm);
-  k_shade_bwd<<<grid, SB_THREADS, smem, st>>>(vt, n_pix, gxa, g, lay, use_smem);
+  // a batch's views are all rendered with or all without indirect light
+  if (vt.v[0].gind && vt.v[0].gxind)
+    k_shade_bwd<true><<<grid, SB_THREADS, smem, st>>>(vt, n_pix, gxa, g, lay, use_smem);
+  else
+    k_shade_bwd<false><<<grid, SB_THREADS, smem, st>>>(vt, n_pix, gxa, g, lay, use_smem);
   note_launches(1);
 }
 

@@ -139,9 +139,12 @@ __device__ __forceinline__ float3 world_ray(const ViewDesc& V, float xp, float y
                      V.R[2] * a + V.R[5] * b + V.R[8]);
 }
 
+// ind (optional): the blended indirect light X_ind (3 channels, not yet
+// divided by A) and vis the pixel's visibility V: the specular light becomes
+// V C_spec + (1 - V) X_ind / A (Eq. 12 with L_ind).
 template <bool GRAD = false>
 __device__ __forceinline__ float4 shade_pixel(const EnvDesc& E, const float X[8], float A, float3 d,
-                                              ShadeState* st) {
+                                              ShadeState* st, const float* ind = nullptr, float vis = 1.f) {
   ShadeState s;
   s.ok = A >= kAMin();
   if (!s.ok) {
@@ -194,6 +197,10 @@ __device__ __forceinline__ float4 shade_pixel(const EnvDesc& E, const float X[8]
   s.irr = cube_bilinear(E.irr, E.cube_dtype, E.irr_res, s.cn, s.bi, GRAD ? &s.idx : nullptr, GRAD ? &s.idy : nullptr);
   const float inv_pi = 0.318309886183790672f;
   float spec3[3] = {s.spec.x, s.spec.y, s.spec.z};
+  if (ind) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) spec3[c] = fmaf(vis, spec3[c], (1.f - vis) * ind[c] * iA);
+  }
   float irr3[3] = {s.irr.x, s.irr.y, s.irr.z};
   float col[3];
 #pragma unroll
@@ -219,18 +226,27 @@ struct EnvGrad {
 
 // Adjoint of shade_pixel: given dL/drgba returns dL/dX (8) and dL/dA, and
 // the environment-map gradient of the pixel in `eg` (scattered by the caller).
+// With ind / vis as in shade_pixel, gind (3) receives dL/dX_ind.
 __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[8], float A, float3 d,
-                                                float4 g, float gX[8], float& gA, EnvGrad& eg) {
+                                                float4 g, float gX[8], float& gA, EnvGrad& eg,
+                                                const float* ind = nullptr, float vis = 1.f,
+                                                float* gind = nullptr) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) gX[c] = 0.f;
   ShadeState s;
   shade_pixel<true>(E, X, A, d, &s);
   gA = g.w;
   eg.ok = s.ok;
+  if (gind) gind[0] = gind[1] = gind[2] = 0.f;
   if (!s.ok) return;
   const float inv_pi = 0.318309886183790672f;
   float gc[3] = {g.x, g.y, g.z};
-  float spec3[3] = {s.spec.x, s.spec.y, s.spec.z};
+  const float iAs = 1.f / A;
+  float spec3[3] = {s.spec.x, s.spec.y, s.spec.z};  // the mixed specular light M
+  if (ind) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) spec3[c] = fmaf(vis, spec3[c], (1.f - vis) * ind[c] * iAs);
+  }
   float irr3[3] = {s.irr.x, s.irr.y, s.irr.z};
   float gLo[3], glam[3] = {0.f, 0.f, 0.f}, gmet = 0.f, gF0[3];
   float gspec3[3], girr3[3];
@@ -249,7 +265,13 @@ __device__ __forceinline__ void shade_pixel_bwd(const EnvDesc& E, const float X[
     gF0[c] = s.lt.x * spec3[c] * gLo[c];
     gLA += s.F0[c] * spec3[c] * gLo[c];
     gLB += spec3[c] * gLo[c];
-    gspec3[c] = (s.F0[c] * s.lt.x + s.lt.y) * gLo[c];
+    gspec3[c] = (s.F0[c] * s.lt.x + s.lt.y) * gLo[c];  // dL/dM
+    if (ind) {
+      const float gi = (1.f - vis) * gspec3[c] * iAs;  // M = V C + (1 - V) X_ind / A
+      gind[c] = gi;
+      gA -= gi * ind[c] * iAs;
+      gspec3[c] *= vis;  // -> dL/dC_spec
+    }
     // F0
     glam[c] += s.met * gF0[c];
     gmet += (s.lam[c] - 0.04f) * gF0[c];

@@ -79,6 +79,12 @@ struct ViewDesc {
   // chart origin (texels) -- the indirection buffer of supplementary Sec. 1
   cudaTextureObject_t atlas2d[2];
   const uint2* chart;
+  // indirect light: per-splat SH coefficients (degree sh_deg <= 2, K = (deg+1)^2
+  // basis functions x RGB, rows of sh_stride floats), NULL when the scene has
+  // none; the view's visibility V [H][W] (NULL: V = 1)
+  const float* sh;
+  int sh_deg, sh_stride;
+  const float* vis;
   EnvDesc env;
   // outputs / saved state
   float4* rgba;   // [H][W]
@@ -86,6 +92,8 @@ struct ViewDesc {
   float* trans;   // [H][W]
   float* acc;     // [H][W] blended coverage A = sum alpha_i T_i (not 1 - T: no cancellation)
   float* zsum;    // [H][W] blended camera depth of the hits, sum alpha_i T_i z_i (saved renders)
+  float4* gind;   // [H][W] blended indirect light X_ind (xyz), saved when the batch has SH
+  float4* gxind;  // [H][W] backward scratch: dL/dX_ind (xyz)
   const float4* gnorm;  // [H][W] extra dL/dN (xyz), dL/dA (w) from the depth-normal loss, or NULL
   const float* gzsum;   // [H][W] dL/d zsum from the depth-normal loss, or NULL
   int* last;      // [H][W]

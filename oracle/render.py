@@ -18,6 +18,10 @@ splat):
              texel centres at (i+0.5)/T, clamp-to-edge inside the splat's texture
   normals    n = R_k n^t with R_k = [t_u, t_v, n_k'] and n_k' the splat normal
              turned to face the camera                    (Eq. 7)
+             with the two-component encoding (scene["normal_encoding"] ==
+             "xy", Sec. 3.5.1, reading R20) only channels 5-6 are read and
+             n^t = (n_x, n_y, sqrt(max(0, 1 - n_x^2 - n_y^2))) from the
+             interpolated (n_x, n_y)
   blending   X = sum_i x_i alpha_i prod_{j<i}(1 - alpha_j)  (Eq. 3, Eq. 8-9)
              A = sum_i alpha_i prod_{j<i}(1 - alpha_j); stop after the first
              fragment that brings the transmittance below 1e-4
@@ -62,6 +66,7 @@ def to_params(scene: dict, requires_grad: bool = False) -> dict:
         t = torch.from_numpy(np.asarray(scene[k], dtype=np.float64).copy())
         t.requires_grad_(requires_grad)
         out[k] = t
+    out["normal_xy"] = scene.get("normal_encoding", "xyz") == "xy"
     return out
 
 
@@ -153,6 +158,14 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
     flip = num > 0.0
     n_face = torch.where(flip[..., None], -n, n)
     nt = tex[..., 5:8]
+    nz_r = None
+    if params.get("normal_xy", False):
+        # two stored components (Sec. 3.5.1): n_z from the interpolated
+        # (n_x, n_y); zero (and a zero derivative) outside the unit disc
+        nz_r = 1.0 - tex[..., 5] * tex[..., 5] - tex[..., 6] * tex[..., 6]
+        pos = nz_r > 0.0
+        nz = torch.where(pos, torch.sqrt(torch.where(pos, nz_r, torch.ones_like(nz_r))), torch.zeros_like(nz_r))
+        nt = torch.cat([tex[..., 5:7], nz[..., None]], -1)
     n_w = nt[..., 0:1] * tu + nt[..., 1:2] * tv + nt[..., 2:3] * n_face
     x = torch.cat([tex[..., 0:5], n_w], -1)  # [P,L,8]
 
@@ -222,6 +235,8 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
             # d(u,v)/d(params) grows like 1/cos^2 and an FP32 evaluation
             # keeps only a few correct digits of those gradients
             kink |= den.abs() <= EDGE_ON_COS * dnorm
+            if nz_r is not None:  # the n_z reconstruction's clamp at the unit circle
+                kink |= nz_r.abs() <= 1e-6
             out["kink"] = (kink & blended).any(1)
     return out
 

@@ -302,6 +302,21 @@ ts_status ts_scene_build_atlas2d(ts_scene* scene, ts_dtype store, int packing, v
  * different samplers (TS_ERR_ARG).  Returns TS_ERR_ARG for an unknown value. */
 ts_status ts_scene_set_sampler(ts_scene* scene, int sampler);
 
+/* Tangent-normal encodings of the texture channels 5-7 (Sec. 3.5.1). */
+enum { TS_NORMAL_XYZ = 0, TS_NORMAL_XY = 1 };
+
+/* Selects how the scene's textures hold the tangent normal n^t:
+ *   TS_NORMAL_XYZ (default): channels 5-7 store the three signed components;
+ *   TS_NORMAL_XY: channels 5-6 store (n_x, n_y) and the renderer rebuilds
+ *     n_z = sqrt(max(0, 1 - n_x^2 - n_y^2)) from the bilinearly interpolated
+ *     pair (Sec. 3.5.1); channel 7 is never read and its gradient is zero.
+ * The texel keeps its 8-channel stride either way (16-byte aligned vector
+ * loads), so the encoding changes what is rendered, not the atlas size.
+ * Applies to every sampler and to the backward.  All scenes of one batch
+ * must share the encoding (TS_ERR_ARG).  Returns TS_ERR_ARG for NULL or an
+ * unknown value. */
+ts_status ts_scene_set_normal_encoding(ts_scene* scene, int encoding);
+
 /* Overwrites the scene's geometry (same n as uploaded) from device arrays,
  * stream-ordered without synchronisation (for updates between training
  * steps).  Layouts as in ts_upload_gaussians. */

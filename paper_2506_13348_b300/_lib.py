@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libtexsplat.so")
 TS_F32, TS_BF16, TS_F16 = 0, 1, 2
 SAMPLERS = {"software": 0, "hw_atlas": 1, "flat": 2}
 PACKINGS = {"splat_id": 0, "morton": 1}
+NORMAL_ENCODINGS = {"xyz": 0, "xy": 1}
 STATUS = {0: "TS_OK", 1: "TS_ERR_ARG", 2: "TS_ERR_OOM", 3: "TS_ERR_CAPACITY", 4: "TS_ERR_CUDA",
           5: "TS_ERR_TIMEOUT", 6: "TS_ERR_STATE"}
 
@@ -26,6 +27,7 @@ EXPORTED = [
     "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
     "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
     "ts_image_loss", "ts_saved_copy_depth", "ts_normal_loss", "ts_upload_indirect",
+    "ts_scene_set_normal_encoding",
 ]
 
 
@@ -104,6 +106,7 @@ def lib() -> C.CDLL:
         "ts_measure_fp32_peak": [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "ts_scene_build_atlas2d": [vp, i32, i32, vp],
         "ts_scene_set_sampler": [vp, i32],
+        "ts_scene_set_normal_encoding": [vp, i32],
         "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
         "ts_saved_copy_depth": [vp, i32, vp, vp, vp],
         "ts_normal_loss": [vp, i32, C.c_float, vp, vp],

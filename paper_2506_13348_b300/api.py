@@ -64,6 +64,7 @@ class Scene:
         self.levels = 0
         self.spec_sizes = []
         self.irr_size = 0
+        self.normal_encoding = "xyz"
 
     def close(self):
         if self.handle:
@@ -118,6 +119,15 @@ class Scene:
         from ._lib import SAMPLERS
         check(lib().ts_scene_set_sampler(self.handle, SAMPLERS[sampler]), "ts_scene_set_sampler")
 
+    def set_normal_encoding(self, encoding: str):
+        """'xyz' (default: three stored tangent-normal components) or 'xy'
+        (channels 5-6 hold n_x, n_y; n_z is rebuilt from the interpolated
+        pair, Sec. 3.5.1)."""
+        from ._lib import NORMAL_ENCODINGS
+        check(lib().ts_scene_set_normal_encoding(self.handle, NORMAL_ENCODINGS[encoding]),
+              "ts_scene_set_normal_encoding")
+        self.normal_encoding = encoding
+
     def upload_envmap(self, env: dict, store="f32", stream=None):
         dev = torch.device("cuda", self.device)
         spec = [_dev_f32(m, dev) for m in env["spec"]]
@@ -139,6 +149,8 @@ class Scene:
         s.upload_envmap(env, env_store)
         if "sh" in scene:
             s.upload_indirect(scene["sh"])
+        if scene.get("normal_encoding", "xyz") != "xyz":
+            s.set_normal_encoding(scene["normal_encoding"])
         return s
 
 

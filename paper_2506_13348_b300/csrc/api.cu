@@ -111,11 +111,13 @@ struct ts_scene {
   float* sh = nullptr;
   int sh_deg = -1, sh_stride = 0;
   int64_t sh_n = -1;
+  bool normal_xy = false;  // two-component tangent normals (Sec. 3.5.1)
 };
 
 struct ts_saved {
   int device = 0;
   bool indirect = false;  // the batch blended per-splat SH light
+  int feat = 0;           // FEAT_* bits the batch was rendered with
   cudaStream_t stream = nullptr;
   ViewTable vt;
   std::vector<ts_scene*> scenes;
@@ -367,6 +369,10 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   }
   if (indirect && sampler != SMP_SOFTWARE)
     return fail(TS_ERR_STATE, "ts_render_views: indirect light (SH) needs the software sampler");
+  for (int i = 1; i < n_views; ++i)
+    if (scenes[i]->normal_xy != scenes[0]->normal_xy)
+      return fail(TS_ERR_ARG, "ts_render_views: views of one batch must share the tangent-normal encoding");
+  const int feat = (indirect ? FEAT_IND : 0) | (scenes[0]->normal_xy ? FEAT_N2 : 0);
   if (sampler != SMP_SOFTWARE && saved_out)
     return fail(TS_ERR_STATE, "ts_render_views: the hardware-atlas and flat samplers are inference-only (no saved state)");
   cudaStream_t st = (cudaStream_t)stream;
@@ -534,8 +540,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   }
   {
     ProfScope p(st, "raster_fwd");
-    launch_raster_fwd(vt, rec, pitems, ranges, scenes[0]->tex_dtype, saved_out != nullptr, nullptr, sampler, indirect,
-                      st);
+    launch_raster_fwd(vt, rec, pitems, ranges, scenes[0]->tex_dtype, saved_out != nullptr, nullptr, sampler, feat, st);
   }
   TS_CHECK_LAUNCH();
 
@@ -549,6 +554,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     sv->stream = st;
     sv->vt = vt;
     sv->indirect = indirect;
+    sv->feat = feat;
     sv->scenes.assign(scenes, scenes + n_views);
     sv->rec = rec;
     sv->pair_items = pitems;
@@ -619,7 +625,7 @@ ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, c
   }
   {
     ProfScope p(st, "raster_bwd");
-    launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, gxa, g_items, g, sv->indirect, st);
+    launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, gxa, g_items, g, sv->feat, st);
   }
   {
     ProfScope p(st, "preprocess_bwd");
@@ -719,8 +725,7 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   unsigned long long* d = nullptr;
   TS_CUDA(tmp.alloc((void**)&d, 2 * sizeof(unsigned long long)));
   TS_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st));
-  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, SMP_SOFTWARE, false,
-                    st);
+  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, SMP_SOFTWARE, 0, st);
   TS_CHECK_LAUNCH();
   unsigned long long h[2] = {0, 0};
   TS_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -875,6 +880,14 @@ ts_status ts_scene_set_sampler(ts_scene* s, int sampler) {
   if (sampler != SMP_SOFTWARE && sampler != SMP_HW_ATLAS && sampler != SMP_FLAT)
     return fail(TS_ERR_ARG, "ts_scene_set_sampler: unknown sampler");
   s->sampler = sampler;
+  return TS_OK;
+}
+
+ts_status ts_scene_set_normal_encoding(ts_scene* s, int encoding) {
+  if (!s) return fail(TS_ERR_ARG, "ts_scene_set_normal_encoding: scene is NULL");
+  if (encoding != TS_NORMAL_XYZ && encoding != TS_NORMAL_XY)
+    return fail(TS_ERR_ARG, "ts_scene_set_normal_encoding: unknown encoding");
+  s->normal_xy = encoding == TS_NORMAL_XY;
   return TS_OK;
 }
 

@@ -47,7 +47,7 @@ void launch_depth_bits(const uint64_t* depth_keys_unsorted, uint32_t* out, int n
 // raster_fwd.cu / raster_bwd.cu
 void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
-                       bool indirect, cudaStream_t st);
+                       int feat, cudaStream_t st);
 void launch_pack_atlas2d(const void* texels, int dtype, long long n, int T, int charts_x, cudaSurfaceObject_t s0,
                          cudaSurfaceObject_t s1, uint2* chart, const uint32_t* chart_of, int half_store,
                          cudaStream_t st);
@@ -56,7 +56,7 @@ void launch_morton_order(const float4* means, long long n, uint32_t* bbox, uint3
 void launch_chart_of(const uint32_t* ids_sorted, long long n, uint32_t* chart_of, cudaStream_t st);
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
-                       const GradTable& g, bool indirect, cudaStream_t st);
+                       const GradTable& g, int feat, cudaStream_t st);
 // shade_bwd.cu: per-pixel shading adjoint -> gxa [pixels][3] (dL/dX 0-3, 4-7, dL/dA)
 void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cudaStream_t st);
 

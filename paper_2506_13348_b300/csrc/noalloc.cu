@@ -184,7 +184,7 @@ extern "C" ts_status ts_render_noalloc(int64_t n, const float* means, const floa
   e = cudaMemsetAsync(ranges, 0, (size_t)vt.n_tiles * sizeof(uint2), st);
   if (e != cudaSuccess) return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: ") + cudaGetErrorString(e));
   launch_tile_ranges(tkeys, (int)K, ranges, st);
-  launch_raster_fwd(vt, rec, pitems, ranges, DT_F32, false, nullptr, SMP_SOFTWARE, false, st);
+  launch_raster_fwd(vt, rec, pitems, ranges, DT_F32, false, nullptr, SMP_SOFTWARE, 0, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: launch: ") + cudaGetErrorString(e));
   return TS_OK;

@@ -133,6 +133,13 @@ __device__ __forceinline__ void tex_fetch_hw(const ViewDesc& V, long long splat,
   out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
 }
 
+// Two-component tangent normal (Sec. 3.5.1): n_z from the interpolated
+// (n_x, n_y), zero outside the unit disc.
+__device__ __forceinline__ float rebuild_nz(float nx, float ny) {
+  const float r = fmaf(-nx, nx, fmaf(-ny, ny, 1.f));
+  return r > 0.f ? sqrtf(r) : 0.f;
+}
+
 // Normal mapping (Eq. 7): n = [t_u, t_v, n_f] n^t, in place on x[5..7].
 __device__ __forceinline__ void normal_map(const Record& r, float x[8]) {
   float a = x[5], b = x[6], c = x[7];

@@ -23,13 +23,14 @@
 
 namespace ts {
 
-template <int DT, bool IND>
-__global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
+template <int DT, int FEAT>
+__global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pair_items,
                                                                   const uint2* __restrict__ ranges,
                                                                   const float4* __restrict__ gxa,
                                                                   double* __restrict__ g_items, GradTable g) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr bool IND = (FEAT & FEAT_IND) != 0, N2 = (FEAT & FEAT_N2) != 0;
   __shared__ __align__(16) float s_gi[8][kRecGrads][36];  // record gradients, value-major, per warp
   // indirect light: per lane dL/dl (3) and the SH basis (9), value-major
   __shared__ __align__(16) float s_sh[IND ? 8 : 1][12][36];
@@ -143,16 +144,23 @@ __global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, c
         float g8[8];
 #pragma unroll
         for (int c = 0; c < 5; ++c) g8[c] = gX[c];
-        g8[5] = r.r2.z * gX[5] + r.r2.w * gX[6] + r.r3.x * gX[7];
-        g8[6] = r.r3.y * gX[5] + r.r3.z * gX[6] + r.r3.w * gX[7];
-        g8[7] = r.r4.x * gX[5] + r.r4.y * gX[6] + r.r4.z * gX[7];
+        // e = dL/dn^t (tangent normal); with two stored components n^t is
+        // not linear in the texels: the corner loop takes channels 0-4 only
+        // and the normal's share is added once n^t is known
+        const float e0 = r.r2.z * gX[5] + r.r2.w * gX[6] + r.r3.x * gX[7];
+        const float e1 = r.r3.y * gX[5] + r.r3.z * gX[6] + r.r3.w * gX[7];
+        const float e2 = r.r4.x * gX[5] + r.r4.y * gX[6] + r.r4.z * gX[7];
+        g8[5] = N2 ? 0.f : e0;
+        g8[6] = N2 ? 0.f : e1;
+        g8[7] = N2 ? 0.f : e2;
         // stream the four bilinear corners: only the projections g8 . texel
         // and the tangent normal are needed
         const float hx = 1.f - ts_.fx, hy = 1.f - ts_.fy;
         w4[0] = hx * hy; w4[1] = ts_.fx * hy; w4[2] = hx * ts_.fy; w4[3] = ts_.fx * ts_.fy;
         float2 nt01 = f2(0.f, 0.f), dxy = f2(0.f, 0.f);
         float nt2 = 0.f, gxx = 0.f;
-        // indirect light: d(tangent normal)/d(texel-space u, v)
+        // indirect light, two-component normals: d(interpolated normal
+        // channels)/d(texel-space u, v)
         float dnu[3] = {0.f, 0.f, 0.f}, dnv[3] = {0.f, 0.f, 0.f};
         const float2 g01 = f2(g8[0], g8[1]), g23 = f2(g8[2], g8[3]), g45 = f2(g8[4], g8[5]), g67 = f2(g8[6], g8[7]);
         const long long base = splat * (long long)T * T;
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, c
           const float wyk = (k & 2) ? ts_.fy : hy;
           const float wxk = (k & 1) ? ts_.fx : hx;
           dxy = fma2(f2((k & 1) ? wyk : -wyk, (k & 2) ? wxk : -wxk), f2(tdot, tdot), dxy);
-          if (IND) {
+          if (IND || N2) {
             const float au = (k & 1) ? wyk : -wyk, av = (k & 2) ? wxk : -wxk;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -184,6 +192,19 @@ __global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, c
         }
         const float nt0 = nt01.x, nt1 = nt01.y;
         float dxs = dxy.x, dys = dxy.y;
+        // two-component normal: n^t = (n_x, n_y, n_z(n_x, n_y)); dL/d(n_x, n_y)
+        // = (e0, e1) + e2 dn_z/d(n_x, n_y), dn_z/dn_x = -n_x / n_z
+        float inz = 0.f;
+        if (N2) {
+          nt2 = rebuild_nz(nt0, nt1);
+          inz = nt2 > 0.f ? 1.f / nt2 : 0.f;
+          gxx = fmaf(e0, nt0, fmaf(e1, nt1, fmaf(e2, nt2, gxx)));  // dL/dX . x: the normal's share
+          const float k = -e2 * inz;
+          g8[5] = fmaf(k, nt0, e0);
+          g8[6] = fmaf(k, nt1, e1);
+          dxs = fmaf(g8[5], dnu[0], fmaf(g8[6], dnu[1], dxs));
+          dys = fmaf(g8[5], dnv[0], fmaf(g8[6], dnv[1], dys));
+        }
         // indirect light of the fragment: l = c . Y(w_r), w_r the reflection
         // of w_o about normalize(n_w), n_w = [t_u t_v n_f] n^t (Eq. 7)
         float lx = 0.f, ly = 0.f, lz = 0.f;
@@ -211,6 +232,10 @@ __global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, c
           float2 p0 = mul2(W, g01), p1 = mul2(W, g23), p2 = mul2(W, g45), p3 = mul2(W, g67);
           t8[0] = p0.x; t8[1] = p0.y; t8[2] = p1.x; t8[3] = p1.y;
           t8[4] = p2.x; t8[5] = p2.y; t8[6] = p3.x; t8[7] = p3.y;
+          if (N2) {
+            t8[5] = wgt * g8[5];
+            t8[6] = wgt * g8[6];
+          }
         }
         dxs *= wgt;
         dys *= wgt;
@@ -245,9 +270,15 @@ __global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, c
           en2 = (en2 - rf.nh.z * pr) * rf.inl;
           // into the tangent normal (R'^T e): its texels, the texture
           // coordinates it is interpolated at, and the frame's torque
-          const float et0 = r.r2.z * en0 + r.r2.w * en1 + r.r3.x * en2;
-          const float et1 = r.r3.y * en0 + r.r3.z * en1 + r.r3.w * en2;
-          const float et2 = r.r4.x * en0 + r.r4.y * en1 + r.r4.z * en2;
+          float et0 = r.r2.z * en0 + r.r2.w * en1 + r.r3.x * en2;
+          float et1 = r.r3.y * en0 + r.r3.z * en1 + r.r3.w * en2;
+          float et2 = r.r4.x * en0 + r.r4.y * en1 + r.r4.z * en2;
+          if (N2) {  // through the rebuilt n_z into the stored (n_x, n_y)
+            const float k = -et2 * inz;
+            et0 = fmaf(k, nt0, et0);
+            et1 = fmaf(k, nt1, et1);
+            et2 = 0.f;
+          }
           t8[5] += et0;
           t8[6] += et1;
           t8[7] += et2;
@@ -421,13 +452,21 @@ __global__ void __launch_bounds__(256, IND ? 2 : 3) k_raster_bwd(ViewTable vt, c
 
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
-                       const GradTable& g, bool indirect, cudaStream_t st) {
+                       const GradTable& g, int feat, cudaStream_t st) {
   dim3 grid(vt.n_tiles), block(256);
-#define TS_LAUNCH_B(DTV)                                                                              \
-  if (indirect)                                                                                       \
-    k_raster_bwd<DTV, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);   \
-  else                                                                                                \
-    k_raster_bwd<DTV, false><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);
+#define TS_LAUNCH_B(DTV)                                                                                      \
+  switch (feat & (FEAT_IND | FEAT_N2)) {                                                                      \
+    case 0: k_raster_bwd<DTV, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g); break; \
+    case FEAT_N2:                                                                                             \
+      k_raster_bwd<DTV, FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);       \
+      break;                                                                                                  \
+    case FEAT_IND:                                                                                            \
+      k_raster_bwd<DTV, FEAT_IND><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g);      \
+      break;                                                                                                  \
+    default:                                                                                                  \
+      k_raster_bwd<DTV, FEAT_IND | FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, \
+                                                                    g);                                       \
+  }
   if (tex_dtype == DT_F32) {
     TS_LAUNCH_B(DT_F32)
   } else if (tex_dtype == DT_BF16) {

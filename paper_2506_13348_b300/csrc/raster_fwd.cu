@@ -26,12 +26,13 @@
 
 namespace ts {
 
-template <int DT, bool SAVE, bool STATS, int SMP, bool IND = false>
+template <int DT, bool SAVE, bool STATS, int SMP, int FEAT = 0>
 __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
                                                      const uint32_t* __restrict__ pair_items,
                                                      const uint2* __restrict__ ranges,
                                                      unsigned long long* __restrict__ stats) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr bool IND = (FEAT & FEAT_IND) != 0, N2 = (FEAT & FEAT_N2) != 0;
   const int tile = blockIdx.x;
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
             } else {
               load_texel(V.texels, DT, splat * (long long)T * T, x);
             }
+            if (N2) x[7] = rebuild_nz(x[5], x[6]);
             normal_map(r, x);
             const float w = f.alpha * Tr;
             if (IND && V.sh) {
@@ -184,36 +186,63 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
   }
 }
 
+namespace {
+
+template <int DT, bool SAVE, bool STATS, int SMP>
+void launch_feat(int feat, dim3 grid, dim3 block, cudaStream_t st, const ViewTable& vt, const Record* rec,
+                 const uint32_t* pair_items, const uint2* ranges, unsigned long long* stats) {
+  switch (feat & (FEAT_IND | FEAT_N2)) {
+    case 0: k_raster_fwd<DT, SAVE, STATS, SMP, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); break;
+    case FEAT_N2:
+      k_raster_fwd<DT, SAVE, STATS, SMP, FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+      break;
+    case FEAT_IND:
+      k_raster_fwd<DT, SAVE, STATS, SMP, FEAT_IND><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+      break;
+    default:
+      k_raster_fwd<DT, SAVE, STATS, SMP, FEAT_IND | FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges,
+                                                                                       stats);
+  }
+}
+
+// samplers without indirect light (the host rejects that combination)
+template <int DT, int SMP>
+void launch_feat_n2(int feat, dim3 grid, dim3 block, cudaStream_t st, const ViewTable& vt, const Record* rec,
+                    const uint32_t* pair_items, const uint2* ranges) {
+  if (feat & FEAT_N2)
+    k_raster_fwd<DT, false, false, SMP, FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, nullptr);
+  else
+    k_raster_fwd<DT, false, false, SMP, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, nullptr);
+}
+
+template <int DT>
+void launch_dt(const ViewTable& vt, const Record* rec, const uint32_t* pair_items, const uint2* ranges, bool save,
+               unsigned long long* stats, int sampler, int feat, cudaStream_t st) {
+  dim3 grid(vt.n_tiles), block(256);
+  if (sampler == SMP_FLAT)
+    launch_feat_n2<DT, SMP_FLAT>(feat, grid, block, st, vt, rec, pair_items, ranges);
+  else if (stats)  // fragment statistics: the features change no fragment
+    k_raster_fwd<DT, false, true, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+  else if (save)
+    launch_feat<DT, true, false, SMP_SOFTWARE>(feat, grid, block, st, vt, rec, pair_items, ranges, nullptr);
+  else
+    launch_feat<DT, false, false, SMP_SOFTWARE>(feat, grid, block, st, vt, rec, pair_items, ranges, nullptr);
+}
+
+}  // namespace
+
 void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
-                       bool indirect, cudaStream_t st) {
-  dim3 grid(vt.n_tiles), block(256);
+                       int feat, cudaStream_t st) {
   if (sampler == SMP_HW_ATLAS) {  // inference only; the atlas dtype is the texture's
-    k_raster_fwd<DT_F32, false, false, SMP_HW_ATLAS><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
-    note_launches(1);
-    return;
-  }
-#define TS_LAUNCH(DTV)                                                                                    \
-  if (sampler == SMP_FLAT)                                                                                \
-    k_raster_fwd<DTV, false, false, SMP_FLAT><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
-  else if (stats)                                                                                         \
-    k_raster_fwd<DTV, false, true, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
-  else if (save && indirect)                                                                              \
-    k_raster_fwd<DTV, true, false, SMP_SOFTWARE, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
-  else if (save)                                                                                          \
-    k_raster_fwd<DTV, true, false, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
-  else if (indirect)                                                                                      \
-    k_raster_fwd<DTV, false, false, SMP_SOFTWARE, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); \
-  else                                                                                                    \
-    k_raster_fwd<DTV, false, false, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
-  if (tex_dtype == DT_F32) {
-    TS_LAUNCH(DT_F32)
+    launch_feat_n2<DT_F32, SMP_HW_ATLAS>(feat, dim3(vt.n_tiles), dim3(256), st, vt, rec, pair_items, ranges);
+  } else if (tex_dtype == DT_F32) {
+    launch_dt<DT_F32>(vt, rec, pair_items, ranges, save, stats, sampler, feat, st);
   } else if (tex_dtype == DT_BF16) {
-    TS_LAUNCH(DT_BF16)
+    launch_dt<DT_BF16>(vt, rec, pair_items, ranges, save, stats, sampler, feat, st);
   } else {
-    TS_LAUNCH(DT_F16)
+    launch_dt<DT_F16>(vt, rec, pair_items, ranges, save, stats, sampler, feat, st);
   }
-#undef TS_LAUNCH
   note_launches(1);
 }
 

@@ -45,6 +45,14 @@ enum Dtype : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
 //                 texture lookup -- the untextured baseline of the paper's Table 3.
 enum Sampler : int { SMP_SOFTWARE = 0, SMP_HW_ATLAS = 1, SMP_FLAT = 2 };
 
+// Optional features of a render, as template bits of the rasterisers:
+//   FEAT_IND: per-splat SH indirect light blended into its own channel and
+//             mixed with the environment by the visibility (Eq. 9, Eq. 12);
+//   FEAT_N2:  two-component tangent normals (Sec. 3.5.1): channels 5-6 hold
+//             (n_x, n_y), n_z = sqrt(max(0, 1 - n_x^2 - n_y^2)) is rebuilt
+//             from the interpolated pair and channel 7 is not read.
+enum Feature : int { FEAT_IND = 1, FEAT_N2 = 2 };
+
 // Environment light (Eq. 11-12): specular mip chain, irradiance cube, BRDF LUT.
 struct EnvDesc {
   const void* spec[MAX_LEVELS];  // [6][R_l][R_l][3]

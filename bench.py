@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--sampling-views", type=int, default=40)
     ap.add_argument("--no-image-loss", action="store_true", help="skip the L1 + D-SSIM timing after the step")
     ap.add_argument("--no-fp32-probe", action="store_true", help="skip the FP32 rate probe after the step")
+    ap.add_argument("--no-features", action="store_true",
+                    help="skip the indirect-light / two-component-normal step timings")
+    ap.add_argument("--features-only", action="store_true")
+    ap.add_argument("--feature-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -318,6 +322,8 @@ def run_ours(args):
         line["precision"] = run_precision(args, local)
     if rank == 0 and not args.no_sampling:
         line["texture_sampling"] = run_sampling(args, local)
+    if rank == 0 and not args.no_features:
+        line["features"] = run_features(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, thr, px = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -645,6 +651,76 @@ def read_traffic(kernel: str):
     return ent.get("dram_bytes_per_launch")
 
 
+def run_features(args, device):
+    """The optional features of the render on the cfg1 step (200k splats,
+    8x8 texels, 800x800, forward + L1 + backward): indirect light (per-splat
+    SH of degree 2, a random per-pixel visibility in [0, 1]), two-component
+    tangent normals, and both, each against the plain step on the same
+    scene, cameras and targets."""
+    import numpy as np
+    import torch
+
+    import paper_2506_13348_b300 as P
+    from paper_2506_13348_b300 import _lib
+    import scenegen as sg
+
+    dev = torch.device("cuda", device)
+    scene, env, cams = build_workload()
+    sc = P.Scene.from_arrays(scene, env, device=device)
+    n = len(scene["opacity"])
+    rng = np.random.default_rng(31)
+    sh = torch.from_numpy((rng.normal(size=(n, 9, 3)) * 0.3).astype(np.float32)).to(dev)
+    nv = args.feature_steps + 3
+    targets = [torch.from_numpy(sg.make_target(i % N_CAMS, RES, RES)).to(dev) for i in range(nv)]
+    vis = [torch.from_numpy(rng.uniform(0, 1, size=(RES, RES)).astype(np.float32)).to(dev) for _ in range(nv)]
+    out = torch.empty(RES, RES, 4, dtype=torch.float32, device=dev)
+    dl = torch.empty_like(out)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def run(indirect, xy):
+        sc.upload_indirect(sh if indirect else None)
+        sc.set_normal_encoding("xy" if xy else "xyz")
+        grads = P.zero_grads(sc)
+
+        def step(i):
+            cam = dict(cams[i % N_CAMS], vis=vis[i]) if indirect else cams[i % N_CAMS]
+            _, saved = P.render(sc, cam, out=out, save=True)
+            P.l1_loss(out, targets[i], loss, dl)
+            P.render_backward(saved, dl, grads)
+            saved.release()
+
+        for i in range(3):
+            step(i)
+        torch.cuda.synchronize()
+        _lib.profile_enable(True)
+        _lib.profile_report()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.feature_steps):
+            step(3 + i)
+        e1.record()
+        torch.cuda.synchronize()
+        stages = _lib.profile_report()
+        _lib.profile_enable(False)
+        ms = e0.elapsed_time(e1) / args.feature_steps
+        del grads
+        return {"ms_per_step": ms, "mpix_per_s": RES * RES / 1e6 / (ms / 1e3),
+                "stages_ms": {k: round(v[1] / max(1, v[0]), 4) for k, v in stages.items()
+                              if k in ("raster_fwd", "raster_bwd", "shade_bwd")}}
+
+    res = {"workload": "cfg1 step (200k splats, 8x8 texels, 800x800, fwd + L1 + bwd), "
+                       f"{args.feature_steps} timed steps per variant",
+           "indirect_input": "per-splat SH degree 2 (9 x 3 coefficients, N(0, 0.3)), visibility U[0,1] per pixel"}
+    for name, ind, xy in (("plain", False, False), ("indirect", True, False), ("normal_xy", False, True),
+                          ("indirect_normal_xy", True, True)):
+        res[name] = run(ind, xy)
+    for name in ("indirect", "normal_xy", "indirect_normal_xy"):
+        res[name]["vs_plain"] = res[name]["ms_per_step"] / res["plain"]["ms_per_step"]
+    sc.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_sampling(args, device):
     """The shape of the paper's Table 3: forward-render throughput of textured
     splats relative to the same splats without textures, for T = 2, 4, 8, 16,
@@ -718,7 +794,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.serve_only or args.large_only or args.precision_only or args.sampling_only:
+    if args.serve_only or args.large_only or args.precision_only or args.sampling_only or args.features_only:
         import torch
         torch.cuda.set_device(dist_env()[2])
         res = {}
@@ -730,6 +806,8 @@ def main():
             res["precision"] = run_precision(args, dist_env()[2])
         if args.sampling_only:
             res["texture_sampling"] = run_sampling(args, dist_env()[2])
+        if args.features_only:
+            res["features"] = run_features(args, dist_env()[2])
         print(json.dumps(res))
         return 0
     return run_ours(args)

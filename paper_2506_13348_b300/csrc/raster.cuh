@@ -194,18 +194,55 @@ __device__ __forceinline__ Refl reflect_dir(float3 nw, float3 wo) {
   return r;
 }
 
-// l = sum_j c_j Y_j(w_r) for the three channels; c rows are [K][3] floats.
-__device__ __forceinline__ float3 sh_eval(const float* __restrict__ c, int K, const float Y[9]) {
+// l = sum_j c_j Y_j(w_r) for the three channels, and with PROJ also
+// s_j = gl . c_j; c rows are [K][3] floats padded to a multiple of 4, read
+// as 16-byte vectors (the same address on every lane of the warp).
+template <bool PROJ>
+__device__ __forceinline__ float3 sh_eval(const float* __restrict__ c, int K, const float Y[9], float3 gl = {},
+                                          float s[9] = nullptr) {
   float3 l = make_float3(0.f, 0.f, 0.f);
+  if (PROJ) {
 #pragma unroll
-  for (int j = 0; j < 9; ++j) {
-    if (j < K) {
-      l.x = fmaf(__ldg(c + 3 * j), Y[j], l.x);
-      l.y = fmaf(__ldg(c + 3 * j + 1), Y[j], l.y);
-      l.z = fmaf(__ldg(c + 3 * j + 2), Y[j], l.z);
+    for (int j = 0; j < 9; ++j) s[j] = 0.f;
+  }
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  const int n4 = (3 * K + 3) >> 2;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    if (q < n4) {
+      const float4 a = __ldg(c4 + q);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int e = 4 * q + i, j = e / 3, ch = e - 3 * (e / 3);
+        if (e < 27 && j < K) {
+          const float x = av[i];
+          if (ch == 0) l.x = fmaf(x, Y[j], l.x);
+          if (ch == 1) l.y = fmaf(x, Y[j], l.y);
+          if (ch == 2) l.z = fmaf(x, Y[j], l.z);
+          if (PROJ) s[j] = fmaf(ch == 0 ? gl.x : (ch == 1 ? gl.y : gl.z), x, s[j]);
+        }
+      }
     }
   }
   return l;
+}
+
+// sum_j s_j grad Y_j(w) (the gradient of the basis as written in sh_basis,
+// taken on the full space; the reflection adjoint projects it)
+__device__ __forceinline__ float3 sh_grad_dir(float3 w, int K, const float s[9]) {
+  float3 g = make_float3(0.f, 0.f, 0.f);
+  if (K > 1) {
+    g.x = -kSH1 * s[3];
+    g.y = -kSH1 * s[1];
+    g.z = kSH1 * s[2];
+  }
+  if (K > 4) {
+    g.x += kSH2 * (w.y * s[4] - w.z * s[7]) - 2.f * kSH3 * w.x * s[6] + 2.f * kSH4 * w.x * s[8];
+    g.y += kSH2 * (w.x * s[4] - w.z * s[5]) - 2.f * kSH3 * w.y * s[6] - 2.f * kSH4 * w.y * s[8];
+    g.z += -kSH2 * (w.y * s[5] + w.x * s[7]) + 4.f * kSH3 * w.z * s[6];
+  }
+  return g;
 }
 
 __device__ __forceinline__ void pixel_of(int tile_local, int tiles_x, int& px, int& py) {

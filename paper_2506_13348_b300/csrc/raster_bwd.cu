@@ -207,15 +207,22 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
         }
         // indirect light of the fragment: l = c . Y(w_r), w_r the reflection
         // of w_o about normalize(n_w), n_w = [t_u t_v n_f] n^t (Eq. 7)
+        // (one pass over the coefficients also gives s_j = dL/dX_ind . c_j
+        // and with it the direction gradient gd = sum_j s_j grad Y_j(w_r),
+        // both still to be scaled by the fragment's weight)
         float lx = 0.f, ly = 0.f, lz = 0.f;
         Refl rf;
+        float3 gd = make_float3(0.f, 0.f, 0.f);
         if (IND && V.sh) {
           const float3 nw = make_float3(fmaf(nt0, r.r2.z, fmaf(nt1, r.r3.y, nt2 * r.r4.x)),
                                         fmaf(nt0, r.r2.w, fmaf(nt1, r.r3.z, nt2 * r.r4.y)),
                                         fmaf(nt0, r.r3.x, fmaf(nt1, r.r3.w, nt2 * r.r4.z)));
           rf = reflect_dir(nw, wo);
           sh_basis(rf.wr, shK, shv + 3);
-          const float3 l = sh_eval(V.sh + splat * V.sh_stride, shK, shv + 3);
+          float sj[9];
+          const float3 l = sh_eval<true>(V.sh + splat * V.sh_stride, shK, shv + 3,
+                                         make_float3(gXi[0], gXi[1], gXi[2]), sj);
+          gd = sh_grad_dir(rf.wr, shK, sj);
           lx = l.x;
           ly = l.y;
           lz = l.z;
@@ -246,19 +253,7 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
           shv[0] = d0;
           shv[1] = d1;
           shv[2] = d2;
-          const float* c = V.sh + splat * V.sh_stride;
-          float sj[9];
-#pragma unroll
-          for (int j = 0; j < 9; ++j)
-            sj[j] = j < shK ? fmaf(d0, __ldg(c + 3 * j), fmaf(d1, __ldg(c + 3 * j + 1), d2 * __ldg(c + 3 * j + 2))) : 0.f;
-          const float wx = rf.wr.x, wy = rf.wr.y, wz = rf.wr.z;
-          // sum_j s_j grad Y_j(w_r)
-          float gx = -kSH1 * sj[3], gy = -kSH1 * sj[1], gz = kSH1 * sj[2];
-          if (shK > 4) {
-            gx += kSH2 * (wy * sj[4] - wz * sj[7]) - 2.f * kSH3 * wx * sj[6] + 2.f * kSH4 * wx * sj[8];
-            gy += kSH2 * (wx * sj[4] - wz * sj[5]) - 2.f * kSH3 * wy * sj[6] - 2.f * kSH4 * wy * sj[8];
-            gz += -kSH2 * (wy * sj[5] + wx * sj[7]) + 4.f * kSH3 * wz * sj[6];
-          }
+          const float gx = wgt * gd.x, gy = wgt * gd.y, gz = wgt * gd.z;
           // w_r = 2 (n.w_o) n - w_o  ->  dL/dn = 2 ((n.w_o) g + (g.n) w_o)
           const float gdn = gx * rf.nh.x + gy * rf.nh.y + gz * rf.nh.z;
           float en0 = 2.f * (rf.ndw * gx + gdn * wo.x), en1 = 2.f * (rf.ndw * gy + gdn * wo.y);

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
               const Refl rf = reflect_dir(make_float3(x[5], x[6], x[7]), wo);
               float Y[9];
               sh_basis(rf.wr, shK, Y);
-              const float3 l = sh_eval(V.sh + splat * V.sh_stride, shK, Y);
+              const float3 l = sh_eval<false>(V.sh + splat * V.sh_stride, shK, Y);
               Xi[0] = fmaf(w, l.x, Xi[0]);
               Xi[1] = fmaf(w, l.y, Xi[1]);
               Xi[2] = fmaf(w, l.z, Xi[2]);

@@ -368,32 +368,34 @@ def run_serving(args, device):
     which = rng.integers(0, 3, size=nreq)
 
     def run(server, scenes, gaps):
-        tickets = [None] * nreq
-        done = threading.Event()
+        # warm-up requests first (all collected), then the statistics are
+        # reset and the measured requests follow on the same schedule
+        def phase(lo, hi):
+            tickets = [None] * nreq
 
-        def consumer():
-            for i in range(nreq):
-                while tickets[i] is None:
-                    time.sleep(0.0002)
-                server.wait(tickets[i], None, timeout_s=120.0)
-                if i == args.serve_warmup - 1:
-                    server.reset_stats()
-            done.set()
+            def consumer():
+                for i in range(lo, hi):
+                    while tickets[i] is None:
+                        time.sleep(0.0002)
+                    server.wait(tickets[i], None, timeout_s=120.0)
 
-        th = threading.Thread(target=consumer)
-        th.start()
-        t0 = time.perf_counter()
-        t_next = t0
-        for i in range(nreq):
-            if gaps is not None:
-                t_next += gaps[i]
-                while True:
-                    d = t_next - time.perf_counter()
-                    if d <= 0:
-                        break
-                    time.sleep(min(d, 0.001) if d > 0.0015 else 0)
-            tickets[i] = server.submit(scenes[which[i]], cams[i])
-        th.join()
+            th = threading.Thread(target=consumer)
+            th.start()
+            t_next = time.perf_counter()
+            for i in range(lo, hi):
+                if gaps is not None:
+                    t_next += gaps[i]
+                    while True:
+                        d = t_next - time.perf_counter()
+                        if d <= 0:
+                            break
+                        time.sleep(min(d, 0.001) if d > 0.0015 else 0)
+                tickets[i] = server.submit(scenes[which[i]], cams[i])
+            th.join()
+
+        phase(0, args.serve_warmup)
+        server.reset_stats()
+        phase(args.serve_warmup, nreq)
         return server.stats()
 
     arena = 24 << 30

@@ -273,7 +273,8 @@ def run_ours(args):
             fr[k] += s[k] / nstat
     npix = RES * RES
     flops_fwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_FWD * fr["n_blended"] + FLOP_SHADE_FWD * npix
-    flops_bwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_BWD * fr["n_blended"] + FLOP_SHADE_BWD * npix
+    # the shading adjoint (FLOP_SHADE_BWD per pixel) runs in k_shade_bwd, not in the rasteriser
+    flops_bwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_BWD * fr["n_blended"]
     peaks, peak_kind = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s

@@ -207,6 +207,14 @@ ts_status ts_adam_update(float* param, float* grad, float* m, float* v, int64_t 
  * ([n][T][T][8] in that dtype); valid until the atlas is re-uploaded. */
 ts_status ts_scene_texels(ts_scene* scene, void** texels, int* T, int* dtype);
 
+/* Device pointers and dtype (TS_F32 or TS_F16) of a scene's stored
+ * environment: the specular cube levels back to back in the layout of
+ * ts_upload_envmap (level l at offset sum_{k<l} 6 r_k^2 3 elements) and the
+ * irradiance cube -- the same element order as the gradients of ts_grads
+ * (spec, irr), so ts_adam_update can write its shadow copy there.  Valid
+ * until the environment is re-uploaded.  TS_ERR_STATE if none is. */
+ts_status ts_scene_envmap(ts_scene* scene, void** spec, void** irr, int* dtype);
+
 /* Image term of the training loss (Sec. 3.6) over the RGB channels of
  * [height][width][4] float32 device images (alpha ignored):
  *   *loss = (1 - lambda) L1 + lambda (1 - SSIM),
@@ -251,8 +259,11 @@ ts_status ts_normal_loss(ts_saved* saved, int view, float weight, float* loss, v
  * reflection direction of its own normalised normal and the results are
  * blended as a G-buffer channel L_ind; the pixel's visibility (ts_camera)
  * mixes it into the specular light.  degree = -1 (coeffs ignored) removes
- * the SH.  Renders of a scene with SH need the software sampler.  The
- * upload synchronises `stream`.  Errors: TS_ERR_ARG (NULL scene, degree
+ * the SH.  Renders of a scene with SH need the software sampler.  A first
+ * upload (or one that changes the degree or the splat count) allocates and
+ * synchronises `stream`; a re-upload of the same degree and count from
+ * device memory overwrites the coefficients in place, stream-ordered
+ * without synchronisation (training updates).  Errors: TS_ERR_ARG (NULL scene, degree
  * outside [-1, 2], NULL coeffs), TS_ERR_STATE (no geometry), TS_ERR_OOM,
  * TS_ERR_CUDA. */
 ts_status ts_upload_indirect(ts_scene* scene, int degree, const float* coeffs, int src_on_device, void* stream);

@@ -390,28 +390,56 @@ def scene_texels(scene: Scene):
     return p.value, T.value, dt.value
 
 
+def scene_envmap(scene: Scene):
+    """(spec pointer, irr pointer, dtype code) of the scene's stored environment."""
+    sp, ir, dt = C.c_void_p(), C.c_void_p(), C.c_int()
+    check(lib().ts_scene_envmap(scene.handle, C.byref(sp), C.byref(ir), C.byref(dt)), "ts_scene_envmap")
+    return sp.value, ir.value, dt.value
+
+
 class Trainer:
     """Multi-view training step on one scene, all in library kernels: a
     batched forward of V views (saved state), the loss of each view (L1, or
     L1 + D-SSIM, plus the normal-consistency term when asked), one
     backward over the batch, then Adam on float32 masters of geometry and
     texels with the texel master written back into the scene's stored atlas
-    (bf16 / f16 / f32) and the geometry updated in place."""
+    (bf16 / f16 / f32) and the geometry updated in place.  Optionally the
+    environment (every specular level and the irradiance cube, written back
+    into the scene's stored cubes) and the per-splat SH of the indirect light
+    are optimised too, as in Sec. 3.6."""
 
     def __init__(self, scene: Scene, data: dict, store: str = "bf16", lr_geom: float = 1e-4,
-                 lr_tex: float = 1e-2, lambda_dssim: float = 0.0, normal_weight: float = 0.0):
+                 lr_tex: float = 1e-2, lambda_dssim: float = 0.0, normal_weight: float = 0.0,
+                 env: dict | None = None, lr_env: float = 0.0, lr_sh: float = 0.0):
         """lambda_dssim > 0 trains on (1 - lambda) L1 + lambda D-SSIM and
         normal_weight > 0 adds normal_weight x L_n (the paper's objective,
-        Sec. 3.6: lambda 0.2); the defaults keep the plain L1 loss."""
+        Sec. 3.6: lambda 0.2); the defaults keep the plain L1 loss.
+        lr_env > 0 optimises the environment maps, starting from ``env`` (the
+        dict the scene's environment was uploaded from); lr_sh > 0 optimises
+        data["sh"] (the scene must carry SH of that shape)."""
         dev = torch.device("cuda", scene.device)
         f = lambda a: _dev_f32(a, dev).clone()  # noqa: E731
         self.scene, self.store = scene, store
         self.master = dict(means=f(data["means"]), quats=f(data["quats"]), scales=f(data["scales"]),
                            opacity=f(data["opacity"]), texels=f(data["texels"]))
+        self.lr = dict(means=lr_geom, quats=lr_geom, scales=lr_geom, opacity=lr_geom, texels=lr_tex)
+        if lr_env > 0.0:
+            if env is None:
+                raise ValueError("Trainer: lr_env needs the initial environment (env=...)")
+            self.master["spec"] = torch.cat([f(m).reshape(-1) for m in env["spec"]])
+            self.master["irr"] = f(env["irr"]).reshape(-1)
+            self.lr["spec"] = self.lr["irr"] = lr_env
+        if lr_sh > 0.0:
+            if not getattr(scene, "sh_K", 0) or "sh" not in data:
+                raise ValueError("Trainer: lr_sh needs a scene with SH and data['sh']")
+            self.master["sh"] = f(data["sh"])
+            self.lr["sh"] = lr_sh
         self.m = {k: torch.zeros_like(t) for k, t in self.master.items()}
         self.v = {k: torch.zeros_like(t) for k, t in self.master.items()}
         self.grads = zero_grads(scene)
-        self.lr = dict(means=lr_geom, quats=lr_geom, scales=lr_geom, opacity=lr_geom, texels=lr_tex)
+        for k in ("spec", "irr"):
+            if k in self.master and self.master[k].numel() != self.grads[k].numel():
+                raise ValueError(f"Trainer: env['{k}'] does not match the scene's environment")
         self.step_count = 0
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.lambda_dssim, self.normal_weight = float(lambda_dssim), float(normal_weight)
@@ -437,15 +465,24 @@ class Trainer:
         render_backward(saved, dls, self.grads)
         saved.release()
         self.step_count += 1
+        codes = {0: "f32", 1: "bf16", 2: "f16"}
         tex_ptr, _, dt = scene_texels(self.scene)
-        for k in ("means", "quats", "scales", "opacity", "texels"):
+        shadow = {"texels": (tex_ptr, codes[dt])}
+        if "spec" in self.master:
+            sp, ir, edt = scene_envmap(self.scene)
+            shadow["spec"], shadow["irr"] = (sp, codes[edt]), (ir, codes[edt])
+        for k in self.master:
+            ptr, sdt = shadow.get(k, (0, "f32"))
             adam_update(self.master[k], self.grads[k], self.m[k], self.v[k], self.step_count, self.lr[k],
-                        shadow_ptr=tex_ptr if k == "texels" else 0,
-                        shadow_dtype={0: "f32", 1: "bf16", 2: "f16"}[dt] if k == "texels" else "f32")
+                        shadow_ptr=ptr, shadow_dtype=sdt)
         ms = self.master
         check(lib().ts_scene_set_geometry(self.scene.handle, _ptr(ms["means"]), _ptr(ms["quats"]),
                                           _ptr(ms["scales"]), _ptr(ms["opacity"]), _stream(None)),
               "ts_scene_set_geometry")
-        self.grads["spec"].zero_()
-        self.grads["irr"].zero_()
+        if "sh" in ms:  # same degree and count: an in-place, stream-ordered copy
+            check(lib().ts_upload_indirect(self.scene.handle, {1: 0, 4: 1, 9: 2}[self.scene.sh_K], _ptr(ms["sh"]), 1,
+                                           _stream(None)), "ts_upload_indirect")
+        for k in ("spec", "irr", "sh"):  # not optimised: drop the accumulated gradient
+            if k not in ms and k in self.grads:
+                self.grads[k].zero_()
         return losses

@@ -749,6 +749,17 @@ ts_status ts_upload_indirect(ts_scene* s, int degree, const float* coeffs, int s
   if (degree < -1 || degree > 2) return fail(TS_ERR_ARG, "ts_upload_indirect: degree must be -1, 0, 1 or 2");
   cudaStream_t st = (cudaStream_t)stream;
   TS_CUDA(cudaSetDevice(s->device));
+  if (degree >= 0 && s->sh && s->sh_deg == degree && s->sh_n == s->n) {
+    // same degree and splat count: overwrite in place, stream-ordered (training updates)
+    if (s->n > 0 && !coeffs) return fail(TS_ERR_ARG, "ts_upload_indirect: coeffs is NULL");
+    const int K = (degree + 1) * (degree + 1);
+    if (s->n > 0)
+      TS_CUDA(cudaMemcpy2DAsync(s->sh, s->sh_stride * sizeof(float), coeffs, 3 * K * sizeof(float),
+                                3 * K * sizeof(float), (size_t)s->n,
+                                src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (!src_on_device) TS_CUDA(cudaStreamSynchronize(st));
+    return TS_OK;
+  }
   TS_CUDA(cudaStreamSynchronize(st));
   if (s->sh) cudaFree(s->sh);
   s->sh = nullptr;
@@ -920,6 +931,15 @@ ts_status ts_scene_texels(ts_scene* s, void** texels, int* T, int* dtype) {
   if (texels) *texels = s->texels;
   if (T) *T = s->T;
   if (dtype) *dtype = s->tex_dtype;
+  return TS_OK;
+}
+
+ts_status ts_scene_envmap(ts_scene* s, void** spec, void** irr, int* dtype) {
+  if (!s) return fail(TS_ERR_ARG, "ts_scene_envmap: scene is NULL");
+  if (!s->spec || !s->irr) return fail(TS_ERR_STATE, "ts_scene_envmap: environment not uploaded");
+  if (spec) *spec = s->spec;
+  if (irr) *irr = s->irr;
+  if (dtype) *dtype = s->cube_dtype;
   return TS_OK;
 }
 

@@ -68,3 +68,40 @@ def test_training_with_the_paper_objective(P):
     losses = [tr.step(cams, targets).sum().item() for _ in range(30)]
     assert np.isfinite(losses).all()
     assert losses[-1] < 0.9 * losses[0], losses
+
+
+def test_training_the_environment_and_indirect_light(P):
+    """lr_env / lr_sh: the stored cubes and SH follow the Adam masters (a
+    fresh scene built from the masters renders the same image) and learning
+    the environment alone pulls the render towards a target lit by a
+    brighter environment."""
+    scene = sg.make_scene(1, n=3000, T=4, seed=42)
+    rng = np.random.default_rng(3)
+    scene["sh"] = (rng.normal(size=(3000, 4, 3)) * 0.2).astype(np.float32)
+    env = sg.make_env(5, cube_res=16, levels=2, irr_res=8, lut_res=32)
+    bright = dict(env, spec=[np.clip(m * 1.6 + 0.05, 0, None).astype(np.float32) for m in env["spec"]],
+                  irr=(env["irr"] * 1.6 + 0.05).astype(np.float32))
+    cams = [sg.look_at_camera(e, 96, 96) for e in [(3.0, 0.5, 0.5), (0.5, 3.0, 0.2), (-2.0, -2.0, 1.0)]]
+    vis = torch.full((96, 96), 0.7, device="cuda")
+    cams = [dict(c, vis=vis) for c in cams]
+    tsc = P.Scene.from_arrays(scene, bright)
+    targets = [P.render(tsc, c)[0].clone() for c in cams]
+    sc = P.Scene.from_arrays(scene, env, store="f32")
+    tr = P.Trainer(sc, scene, store="f32", lr_geom=0.0, lr_tex=0.0, env=env, lr_env=1e-2, lr_sh=1e-2)
+    losses = [tr.step(cams, targets).sum().item() for _ in range(25)]
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.7 * losses[0], losses
+    # the SH and cubes moved, and the stored copies are the masters
+    assert not np.allclose(tr.master["sh"].cpu().numpy(), scene["sh"])
+    spec_sizes = [m.size for m in env["spec"]]
+    flat = tr.master["spec"].cpu().numpy()
+    parts = np.split(flat, np.cumsum(spec_sizes)[:-1])
+    env2 = dict(env, spec=[p.reshape(m.shape) for p, m in zip(parts, env["spec"])],
+                irr=tr.master["irr"].cpu().numpy().reshape(env["irr"].shape))
+    assert np.abs(env2["spec"][0] - env["spec"][0]).max() > 1e-3
+    geo = {k: tr.master[k].cpu().numpy() for k in ("means", "quats", "scales", "opacity", "texels")}
+    ref = P.Scene.from_arrays(dict(scene, **geo, sh=tr.master["sh"].cpu().numpy()), env2, store="f32")
+    a, _ = P.render(sc, cams[0])
+    b, _ = P.render(ref, cams[0])
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)

@@ -125,3 +125,41 @@ def test_xy_gradients_match_oracle(P, with_sh):
     gt = grads["texels"].cpu().numpy()
     assert np.abs(gt[..., 7]).max() == 0.0
     saved.release()
+
+
+@pytest.mark.parametrize("store,tdt", [("bf16", torch.bfloat16), ("f16", torch.float16)])
+def test_reduced_precision_atlas_with_both_features(P, store, tdt):
+    """BF16 / F16 atlases with two-component normals and indirect light:
+    image and gradients against the oracle fed the same rounded texels."""
+    scene = xy_scene(seed=8)
+    rounded = torch.from_numpy(scene["texels"]).to(tdt).to(torch.float32).numpy()
+    rng = np.random.default_rng(12)
+    scene["sh"] = (rng.normal(size=(600, 4, 3)) * 0.3).astype(np.float32)
+    env = sg.make_env(6, cube_res=16, levels=2, irr_res=8, lut_res=32)
+    cam = sg.look_at_camera((2.6, 1.2, 0.8), 96, 80)
+    H, W = 80, 96
+    vis = rng.uniform(0, 1, size=(H, W)).astype(np.float32)
+    ref_scene = dict(scene, texels=rounded)
+    kl = K.build_keys(ref_scene, cam)
+    ref = R.render(ref_scene, cam, env, keylist=kl, vis=vis)
+    sc = P.Scene.from_arrays(scene, env, store=store)
+    cg = dict(cam, vis=torch.from_numpy(vis).cuda())
+    out, saved = P.render(sc, cg, save=True)
+    torch.cuda.synchronize()
+    amb = ref["ambiguous"].numpy()
+    err = np.abs(out.cpu().numpy().astype(np.float64) - ref["rgba"].numpy()).max(-1)
+    assert err[~amb].max() <= 1e-4, err[~amb].max()
+    gamb = ref["grad_ambiguous"].numpy()
+    dL = np.random.default_rng(13).normal(size=(H, W, 4))
+    dL[gamb] = 0.0
+    rg = G.render_grads(ref_scene, cam, env, dL, keylist=kl, vis=vis)
+    grads = P.zero_grads(sc)
+    P.render_backward(saved, torch.from_numpy(dL.astype(np.float32)).cuda(), grads)
+    torch.cuda.synchronize()
+    for name in ("means", "quats", "scales", "opacity", "texels", "sh"):
+        r = rg[name]
+        g = grads[name].cpu().numpy().astype(np.float64).reshape(r.shape)
+        scale = np.abs(r).max()
+        bad = np.abs(g - r) > 1e-3 * scale + 1e-6
+        assert not bad.any(), (name, int(bad.sum()), float(np.abs(g - r).max()), float(scale))
+    saved.release()

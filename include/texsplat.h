@@ -405,6 +405,9 @@ ts_status ts_l1_loss(const float* rgba, const float* target, int64_t n_pixels, f
  *   (8-byte aligned), opacity [n], texels [n][T][T][8] float32 (16-byte
  *   aligned), the environment as in ts_upload_envmap in float32 (spec
  *   levels concatenated), camera by value, out_rgba [H][W][4].
+ *   It renders the default model: three stored tangent-normal components,
+ *   no indirect light (the camera's visibility is ignored), the software
+ *   sampler.
  *   The first call on a device looks up the array's device address (once
  *   per device, with that device current): make that first call before any
  *   stream capture.  Every call shares the array: the call clears what must

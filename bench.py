@@ -86,6 +86,34 @@ def dist_env():
     return rank, world, local
 
 
+def rank_views(rank: int, n_needed: int) -> list:
+    """Camera (and target) indices rank `rank` renders: each rank starts at
+    its own offset of the camera set, so replicas work on different views."""
+    return [(rank * 7 + i) % N_CAMS for i in range(n_needed)]
+
+
+def max_over_ranks(ms: float, pg, device) -> float:
+    """The slowest rank's time: the whole job's time for `value`."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job Mpix/s: every rank renders `steps` views of RES x RES."""
+    return world * steps * RES * RES / 1e6 / (ms_max / 1e3)
+
+
+def workload_config(world: int) -> dict:
+    return {"workload": "cfg1: 200k textured splats (160k sphere + 40k box), 8x8 texels x 8 ch, "
+                        "800x800, forward + L1 loss + backward per view",
+            "splats": N_SPLATS, "texels": f"{T_TEX}x{T_TEX}x8 f32", "resolution": f"{RES}x{RES}",
+            "views_per_step": 1, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (texel atlas 410 MB, records+pairs ~90 MB per view)"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -188,8 +216,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "cfg1: 200k textured splats (8x8x8 texels), 800x800, fwd+L1+bwd",
-                       "sample": f"{max(1, args.cpu_tiles // 3)} random non-empty 16x16 tiles per step"},
+            "config": dict(workload_config(world),
+                           sample=f"{max(1, args.cpu_tiles // 3)} random non-empty 16x16 tiles per step"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": f"{max(1, args.cpu_tiles // 3)} random non-empty tiles of each view, fwd+autograd bwd, FP64"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -218,9 +246,9 @@ def run_ours(args):
     scene, env, cams = build_workload()
     sc = P.Scene.from_arrays(scene, env, device=local)
     n_needed = min(N_CAMS, args.warmup + args.steps)
-    my_cams = [cams[(rank * 7 + i) % N_CAMS] for i in range(n_needed)]
-    targets = [torch.from_numpy(sg.make_target((rank * 7 + i) % N_CAMS, RES, RES)).to(dev)
-               for i in range(n_needed)]
+    views = rank_views(rank, n_needed)
+    my_cams = [cams[i] for i in views]
+    targets = [torch.from_numpy(sg.make_target(i, RES, RES)).to(dev) for i in views]
     out = torch.empty(RES, RES, 4, dtype=torch.float32, device=dev)
     dl = torch.empty_like(out)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
@@ -254,13 +282,10 @@ def run_ours(args):
     _lib.profile_enable(False)
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=dev)
     if pg:
         pg.barrier()
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    ms_max = float(t.item())
-    mpix = RES * RES / 1e6
-    value = world * args.steps * mpix / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, pg, dev)
+    value = aggregate_value(world, args.steps, ms_max)
 
     # fragment statistics of a few of the timed views (untimed pass)
     fr = {"n_pairs": 0, "n_evaluated": 0, "n_blended": 0, "n_visible": 0}
@@ -291,11 +316,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "cfg1: 200k textured splats (160k sphere + 40k box), 8x8 texels x 8 ch, "
-                                   "800x800, forward + L1 loss + backward per view",
-                       "splats": N_SPLATS, "texels": f"{T_TEX}x{T_TEX}x8 f32", "resolution": f"{RES}x{RES}",
-                       "views_per_step": 1, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (texel atlas 410 MB, records+pairs ~90 MB per view)"},
+            "config": workload_config(world),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                          "peak_note": f"FP32 FMA peak {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
@@ -613,11 +634,8 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
         step(args.warmup + i)
     e1.record(stream)
     torch.cuda.synchronize()
-    t = torch.tensor([e0.elapsed_time(e1)], device=dev)
-    if pg:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    ms = float(t.item())
-    return {"value": world * args.steps * RES * RES / 1e6 / (ms / 1e3), "unit": UNIT,
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    return {"value": aggregate_value(world, args.steps, ms), "unit": UNIT,
             "h2d_bytes_per_step": RES * RES * 4 * 4, "d2h_bytes_per_step": 4,
             "note": "target H2D on a side stream overlapping the render (double-buffered)"}
 

@@ -384,6 +384,23 @@ ts_status ts_server_reset_stats(ts_server* server);
 ts_status ts_l1_loss(const float* rgba, const float* target, int64_t n_pixels, float* loss_out,
                      float* dL_drgba, void* stream);
 
+/* Activations of the raw optimisation variables, so that the render ABI
+ * sees linear values: scales[i] = exp(log_scales[i]) for the n x 2 scale
+ * components, opacity[k] = 1 / (1 + exp(-logit_opacity[k])) for the n
+ * opacities (the parameterisation the optimisation of Sec. 3.6 runs on;
+ * quaternions need none: the renderer normalises them and its gradient is
+ * w.r.t. the raw quaternion).  Device arrays, stream-ordered.
+ * TS_ERR_ARG for n < 0 or a NULL array with n > 0. */
+ts_status ts_activate(int64_t n, const float* log_scales, const float* logit_opacity, float* scales, float* opacity,
+                      void* stream);
+
+/* Chain rule of ts_activate: g_log_scales = g_scales * scales,
+ * g_logit_opacity = g_opacity * opacity * (1 - opacity), from the activated
+ * values; written, or added when accumulate != 0. */
+ts_status ts_activate_backward(int64_t n, const float* scales, const float* opacity, const float* g_scales,
+                               const float* g_opacity, float* g_log_scales, float* g_logit_opacity, int accumulate,
+                               void* stream);
+
 /* ---- rendering without device allocation ------------------------------------ */
 
 /* The paper has no counterpart of this entry point; it serves callers that

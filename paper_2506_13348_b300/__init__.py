@@ -8,7 +8,8 @@ import importlib
 from ._lib import TexSplatError, lib  # noqa: F401
 
 _API = ("Scene", "Saved", "render", "render_views", "render_backward", "zero_grads", "l1_loss", "image_loss", "make_camera",
-        "split_spec", "TexSplatRender", "Server", "Trainer", "adam_update", "scene_texels")
+        "split_spec", "TexSplatRender", "Server", "Trainer", "adam_update", "scene_texels", "scene_envmap",
+        "activate", "activate_backward")
 
 
 def __getattr__(name):

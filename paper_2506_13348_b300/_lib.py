@@ -27,7 +27,7 @@ EXPORTED = [
     "ts_server_wait", "ts_server_stats", "ts_server_reset_stats", "ts_scene_texels", "ts_scene_set_geometry",
     "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
     "ts_image_loss", "ts_saved_copy_depth", "ts_normal_loss", "ts_upload_indirect",
-    "ts_scene_set_normal_encoding", "ts_scene_envmap",
+    "ts_scene_set_normal_encoding", "ts_scene_envmap", "ts_activate", "ts_activate_backward",
 ]
 
 
@@ -108,6 +108,8 @@ def lib() -> C.CDLL:
         "ts_scene_set_sampler": [vp, i32],
         "ts_scene_set_normal_encoding": [vp, i32],
         "ts_scene_envmap": [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i32)],
+        "ts_activate": [i64, vp, vp, vp, vp, vp],
+        "ts_activate_backward": [i64, vp, vp, vp, vp, vp, vp, i32, vp],
         "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
         "ts_saved_copy_depth": [vp, i32, vp, vp, vp],
         "ts_normal_loss": [vp, i32, C.c_float, vp, vp],

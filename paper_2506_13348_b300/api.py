@@ -288,15 +288,36 @@ def split_spec(scene: Scene, flat: torch.Tensor):
     return out
 
 
+def activate(log_scales: torch.Tensor, logit_opacity: torch.Tensor, stream=None):
+    """(scales, opacity) = (exp(log_scales), sigmoid(logit_opacity)) by the
+    library kernel (ts_activate); CUDA float32 in and out."""
+    ls, lo = log_scales.contiguous(), logit_opacity.contiguous()
+    s, o = torch.empty_like(ls), torch.empty_like(lo)
+    check(lib().ts_activate(lo.numel(), _ptr(ls), _ptr(lo), _ptr(s), _ptr(o), _stream(stream)), "ts_activate")
+    return s, o
+
+
+def activate_backward(scales, opacity, g_scales, g_opacity, stream=None):
+    """Chain rule of :func:`activate` (ts_activate_backward)."""
+    gls, glo = torch.empty_like(scales), torch.empty_like(opacity)
+    check(lib().ts_activate_backward(opacity.numel(), _ptr(scales), _ptr(opacity), _ptr(g_scales.contiguous()),
+                                     _ptr(g_opacity.contiguous()), _ptr(gls), _ptr(glo), 0, _stream(stream)),
+          "ts_activate_backward")
+    return gls, glo
+
+
 class TexSplatRender(torch.autograd.Function):
-    """Differentiable render of one view of a scene whose parameters are
-    held by the caller as torch tensors (means, quats, scales, opacity,
-    texels, spec (flat), irr).  Parameters are uploaded into ``scene`` on
-    each forward (device-to-device copies); the backward calls the
-    library's hand-written adjoint."""
+    """Differentiable render of one view from the raw optimisation variables
+    held by the caller as torch tensors: means, quats (any norm), log_scales,
+    logit_opacity, texels, spec (flat, all levels), irr.  The activations run
+    in the library (ts_activate), the parameters are copied into ``scene``
+    on each forward (device to device) and the backward is the library's
+    hand-written adjoint followed by the activations' chain rule."""
 
     @staticmethod
-    def forward(ctx, scene: Scene, cam: dict, env_lut, means, quats, scales, opacity, texels, spec_flat, irr):
+    def forward(ctx, scene: Scene, cam: dict, env_lut, means, quats, log_scales, logit_opacity, texels, spec_flat,
+                irr):
+        scales, opacity = activate(log_scales, logit_opacity)
         scene.upload_gaussians(means, quats, scales, opacity)
         scene.upload_atlas(texels, "f32")
         levels = scene.levels or 1
@@ -311,16 +332,20 @@ class TexSplatRender(torch.autograd.Function):
         out, saved = render(scene, cam, save=True)
         ctx.scene = scene
         ctx.saved = saved
+        ctx.irr_shape = irr.shape
+        ctx.save_for_backward(scales, opacity)
         return out
 
     @staticmethod
     def backward(ctx, g):
         scene = ctx.scene
+        scales, opacity = ctx.saved_tensors
         grads = zero_grads(scene)
         render_backward(ctx.saved, g.contiguous(), grads)
         ctx.saved.release()
-        return (None, None, None, grads["means"], grads["quats"], grads["scales"], grads["opacity"],
-                grads["texels"], grads["spec"], grads["irr"].reshape(6, *([int((scene.irr_size / 18) ** 0.5)] * 2), 3))
+        g_ls, g_lo = activate_backward(scales, opacity, grads["scales"], grads["opacity"])
+        return (None, None, None, grads["means"], grads["quats"], g_ls, g_lo, grads["texels"], grads["spec"],
+                grads["irr"].reshape(ctx.irr_shape))
 
 
 class Server:

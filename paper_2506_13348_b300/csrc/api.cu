@@ -984,6 +984,26 @@ ts_status ts_scene_info(const ts_scene* s, int64_t* n, int* T, int* dtype) {
   return TS_OK;
 }
 
+ts_status ts_activate(int64_t n, const float* log_scales, const float* logit_opacity, float* scales, float* opacity,
+                      void* stream) {
+  if (n < 0 || (n > 0 && (!log_scales || !logit_opacity || !scales || !opacity)))
+    return fail(TS_ERR_ARG, "ts_activate: bad argument");
+  launch_activate(log_scales, logit_opacity, n, scales, opacity, (cudaStream_t)stream);
+  TS_CHECK_LAUNCH();
+  return TS_OK;
+}
+
+ts_status ts_activate_backward(int64_t n, const float* scales, const float* opacity, const float* g_scales,
+                               const float* g_opacity, float* g_log_scales, float* g_logit_opacity, int accumulate,
+                               void* stream) {
+  if (n < 0 || (n > 0 && (!scales || !opacity || !g_scales || !g_opacity || !g_log_scales || !g_logit_opacity)))
+    return fail(TS_ERR_ARG, "ts_activate_backward: bad argument");
+  launch_activate_bwd(scales, opacity, g_scales, g_opacity, n, g_log_scales, g_logit_opacity, accumulate,
+                      (cudaStream_t)stream);
+  TS_CHECK_LAUNCH();
+  return TS_OK;
+}
+
 ts_status ts_l1_loss(const float* rgba, const float* target, int64_t n_pixels, float* loss_out, float* dL_drgba,
                      void* stream) {
   if (!rgba || !target || !loss_out || !dL_drgba || n_pixels < 0) return fail(TS_ERR_ARG, "ts_l1_loss: bad argument");

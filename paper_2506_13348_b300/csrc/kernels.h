@@ -66,6 +66,9 @@ void launch_adam(float* p, float* g, float* m, float* v, long long n, float lr, 
 
 // misc.cu
 void launch_pack_texels(const float* src, void* dst, long long n, int dtype, cudaStream_t st);
+void launch_activate(const float* log_s, const float* logit_o, long long n, float* s, float* o, cudaStream_t st);
+void launch_activate_bwd(const float* s, const float* o, const float* gs, const float* go, long long n,
+                         float* g_log_s, float* g_logit_o, int accumulate, cudaStream_t st);
 void launch_pack_f16(const float* src, __half* dst, long long n, cudaStream_t st);
 void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStream_t st);
 void launch_l1_loss(const float4* rgba, const float4* target, long long n, float* loss, float4* grad,

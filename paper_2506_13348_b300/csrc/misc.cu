@@ -44,6 +44,51 @@ void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStre
   }
 }
 
+// Activations of the raw optimisation variables: s = exp(log s) per scale
+// component, o = sigmoid(logit o) (the 3DGS / 2DGS parameterisation the
+// optimisation of Sec. 3.6 runs on).  Element i < 2n is a scale component,
+// 2n <= i < 3n an opacity.
+__global__ void k_activate(const float* __restrict__ log_s, const float* __restrict__ logit_o, long long n,
+                           float* __restrict__ s, float* __restrict__ o) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 2 * n) {
+    s[i] = expf(log_s[i]);
+  } else if (i < 3 * n) {
+    const long long k = i - 2 * n;
+    o[k] = 1.f / (1.f + expf(-logit_o[k]));
+  }
+}
+
+// Chain rule of k_activate: dL/dlog s = dL/ds s, dL/dlogit o = dL/do o (1 - o).
+__global__ void k_activate_bwd(const float* __restrict__ s, const float* __restrict__ o,
+                               const float* __restrict__ gs, const float* __restrict__ go, long long n,
+                               float* __restrict__ g_log_s, float* __restrict__ g_logit_o, int accumulate) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 2 * n) {
+    const float v = gs[i] * s[i];
+    g_log_s[i] = accumulate ? g_log_s[i] + v : v;
+  } else if (i < 3 * n) {
+    const long long k = i - 2 * n;
+    const float v = go[k] * o[k] * (1.f - o[k]);
+    g_logit_o[k] = accumulate ? g_logit_o[k] + v : v;
+  }
+}
+
+void launch_activate(const float* log_s, const float* logit_o, long long n, float* s, float* o, cudaStream_t st) {
+  if (n > 0) {
+    k_activate<<<(unsigned)((3 * n + 255) / 256), 256, 0, st>>>(log_s, logit_o, n, s, o);
+    note_launches(1);
+  }
+}
+
+void launch_activate_bwd(const float* s, const float* o, const float* gs, const float* go, long long n,
+                         float* g_log_s, float* g_logit_o, int accumulate, cudaStream_t st) {
+  if (n > 0) {
+    k_activate_bwd<<<(unsigned)((3 * n + 255) / 256), 256, 0, st>>>(s, o, gs, go, n, g_log_s, g_logit_o, accumulate);
+    note_launches(1);
+  }
+}
+
 // L1 over RGB: loss = mean |rgb - target|, dL/drgb = sign / (3 n), dL/dalpha = 0.
 // Grid-stride over pixels; one atomic per block (a single float receives
 // the loss, so per-warp atomics would serialise on it).

@@ -11,6 +11,8 @@
 // the irradiance cube fit (<= 96 KB of float32 gradients) each CTA
 // accumulates them in shared memory and adds its copy to the global gradient
 // once at the end (persistent grid, a few CTAs per SM).
+#include <atomic>
+
 #include "kernels.h"
 #include "prof.h"
 #include "shading.cuh"
@@ -241,14 +243,15 @@ void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cuda
   lay.total = tot;
   const int use_smem = tot <= SB_MAX_SMEM_FLOATS ? 1 : 0;
   const size_t smem = use_smem ? (size_t)tot * sizeof(float) : 0;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_shade_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_MAX_SMEM_FLOATS * 4);
-    cudaFuncSetAttribute(k_shade_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_MAX_SMEM_FLOATS * 4);
-    attr_set = true;
-  }
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
+  // the shared-memory opt-in is a per-device attribute of the function
+  static std::atomic<bool> attr_set[64];
+  if (dev < 0 || dev >= 64 || !attr_set[dev].load()) {
+    cudaFuncSetAttribute(k_shade_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_MAX_SMEM_FLOATS * 4);
+    cudaFuncSetAttribute(k_shade_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_MAX_SMEM_FLOATS * 4);
+    if (dev >= 0 && dev < 64) attr_set[dev].store(true);
+  }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long want = (n_pix + SB_THREADS - 1) / SB_THREADS;
   const int per_sm = use_smem ? 2 : 8;

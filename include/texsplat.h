@@ -50,8 +50,10 @@ typedef enum ts_dtype { TS_F32 = 0, TS_BF16 = 1, TS_F16 = 2 } ts_dtype;
  * width, height >= 1.  visibility: NULL, or a caller-owned device array
  * [height][width] of the view's visibility V in [0, 1] (Eq. 12: the specular
  * light is V C_spec + (1 - V) L_ind); read by the render and, for a saved
- * render, by its backward, so it must stay valid until both ran.  Without
- * per-splat SH (ts_upload_indirect) L_ind is 0. */
+ * render, by its backward, so it must stay valid until both ran.  V and
+ * L_ind form the indirect-light model together: it applies to scenes with
+ * per-splat SH (ts_upload_indirect); for a scene without SH the plain model
+ * renders (V = 1, L_ind = 0) and visibility is not read. */
 typedef struct ts_camera {
   float R[9];
   float t[3];

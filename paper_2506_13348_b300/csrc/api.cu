@@ -404,7 +404,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     V.sh = s->sh;
     V.sh_deg = s->sh ? s->sh_deg : 0;
     V.sh_stride = s->sh_stride;
-    V.vis = c.visibility;
+    V.vis = s->sh ? c.visibility : nullptr;  // the indirect-light model only
     fill_env(s, V.env);
     V.rgba = reinterpret_cast<float4*>(out_rgba[i]);
     tiles += (long long)V.tiles_x * V.tiles_y;

@@ -85,3 +85,18 @@ def test_indirect_gradients_match_oracle(P, K_sh):
         bad = err > 1e-3 * scale + 1e-6
         assert not bad.any(), (name, int(bad.sum()), float(err.max()), float(scale))
     saved.release()
+
+
+def test_mixed_batch_applies_visibility_to_scenes_with_sh_only(P):
+    scene, env, cam, vis = case(4, seed=4)
+    plain_scene = {k: v for k, v in scene.items() if k != "sh"}
+    a = P.Scene.from_arrays(scene, env)
+    b = P.Scene.from_arrays(plain_scene, env)
+    v = torch.from_numpy(vis).cuda()
+    cv = dict(cam, vis=v)
+    outs, _ = P.render_views([a, b], [cv, cv])
+    alone_a, _ = P.render(a, cv)
+    alone_b, _ = P.render(b, cam)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], alone_a)
+    assert torch.equal(outs[1], alone_b)

@@ -751,7 +751,9 @@ def run_sampling(args, device):
     renders one attribute vector per splat (flat sampler, T = 1).  The
     hardware path is timed with charts in splat id order (the paper's) and in
     the Morton order of the splat centres.  Each figure is views per second
-    over the same views."""
+    over the same views.  The training step (forward with saved state, L1,
+    backward) is timed per T too, against T = 1 (one texel per splat: the
+    per-splat attribute model through the same software path)."""
     import torch
 
     import paper_2506_13348_b300 as P
@@ -776,6 +778,31 @@ def run_sampling(args, device):
         torch.cuda.synchronize()
         return nv / (e0.elapsed_time(e1) / 1e3)
 
+    tgt = torch.from_numpy(sg.make_target(0, RES, RES)).to(dev)
+    dl = torch.empty_like(img)
+    loss = torch.zeros(1, device=dev)
+
+    def train_ms(sc):
+        grads = P.zero_grads(sc)
+
+        def step(i):
+            _, saved = P.render(sc, cams[i % N_CAMS], out=img, save=True)
+            P.l1_loss(img, tgt, loss, dl)
+            P.render_backward(saved, dl, grads)
+            saved.release()
+
+        for i in range(3):
+            step(i)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(nv // 2):
+            step(i)
+        e1.record()
+        torch.cuda.synchronize()
+        del grads
+        return e0.elapsed_time(e1) / (nv // 2)
+
     def scene_with(T):
         sc = P.Scene(device)
         sc.upload_gaussians(geo["means"], geo["quats"], geo["scales"], geo["opacity"])
@@ -784,16 +811,18 @@ def run_sampling(args, device):
         return sc
 
     sc = scene_with(1)
+    base_train = train_ms(sc)
     sc.set_sampler("flat")
     base = fps(sc)
     sc.close()
     out = {"workload": "200k splats (cfg1 geometry), 800x800, forward render, views/s over "
                        f"{nv} views; FP32 charts (software) vs FP32 2-D atlases (tex2D)",
-           "untextured_fps": base,
+           "untextured_fps": base, "train_ms_T1": base_train,
            "paper_table3_ratios": {"software": [0.90, 0.86, 0.85, 0.79], "hardware": [0.92, 0.93, 0.94, 0.91]}}
     for T in (2, 4, 8, 16):
         sc = scene_with(T)
         sw = fps(sc)
+        tr = train_ms(sc)
         P.render(sc, cams[0], out=img)
         ref = img.clone()
         sc.build_atlas2d("f32")
@@ -806,6 +835,7 @@ def run_sampling(args, device):
         sc.close()
         torch.cuda.empty_cache()
         out[f"T{T}"] = {"software_fps": sw, "hardware_fps": hw, "hardware_morton_fps": hw_m,
+                        "train_ms": tr, "train_ratio": base_train / tr,
                         "software_ratio": sw / base, "hardware_ratio": hw / base, "hardware_morton_ratio": hw_m / base,
                         "hw_vs_software_rgb": {"max_abs": float(d.max()), "mean_abs": float(d.mean())}}
     return out

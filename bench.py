@@ -477,10 +477,18 @@ def run_precision(args, device):
     out = {"workload": "cfg2: 500k splats, 16x16 texels x 8 ch, 1920x1080, 6-level 128 FP16 cube, 10 views",
            "error_samples": f"{args.precision_samples} random pixels of views 0 and 5 vs the FP64 oracle with FP32 texels"}
     img = torch.empty(H, W, 4, device=dev)
+    from paper_2506_13348_b300 import _lib
+    tex_dev = tex.to(dev)  # the pack (S0) reads float32 texels already in HBM
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
     for store in ("f32", "bf16", "f16"):
         sc = P.Scene(device)
         sc.upload_gaussians(geo["means"], geo["quats"], geo["scales"], geo["opacity"])
-        sc.upload_atlas(tex, store)
+        _lib.profile_enable(True)
+        _lib.profile_report()
+        sc.upload_atlas(tex_dev, store)
+        st = _lib.profile_report()
+        _lib.profile_enable(False)
         sc.upload_envmap(env, "f16")
         errs = []
         for ci, px, py, ref, amb in samples:
@@ -501,11 +509,17 @@ def run_precision(args, device):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / len(cams)
         mse = float((e ** 2).mean())
-        out[store] = {"fwd_ms_per_view": ms, "fwd_mpix_per_s": W * H / 1e6 / (ms / 1e3),
+        pack = {}
+        if "atlas_pack" in st:  # bf16 / f16: 4 B read + 2 B written per channel
+            pms = st["atlas_pack"][1] / max(1, st["atlas_pack"][0])
+            gbs = tex_dev.numel() * 6 / (pms / 1e3) / 1e9
+            pack = {"pack_ms": pms, "pack_gb_per_s": gbs, "pack_frac_of_hbm": gbs / hbm,
+                    "pack_peak": f"{hbm:.0f} GB/s ({peak_kind})"}
+        out[store] = {"fwd_ms_per_view": ms, "fwd_mpix_per_s": W * H / 1e6 / (ms / 1e3), **pack,
                       "max_abs_err": float(e.max()), "mean_abs_err": float(e.mean()),
                       "psnr_db": float(10 * np.log10(1.0 / mse)) if mse > 0 else None}
         sc.close()
-    del tex
+    del tex, tex_dev
     torch.cuda.empty_cache()
     return out
 

@@ -252,7 +252,10 @@ ts_status ts_upload_atlas(ts_scene* s, int T, int C, ts_dtype store, const float
         TS_CUDA(cudaMemcpyAsync(staging, texels, (size_t)count * 4, cudaMemcpyHostToDevice, st));
         src = staging;
       }
-      launch_pack_texels(src, s->texels, count, (int)store, st);
+      {
+        ProfScope p(st, "atlas_pack");
+        launch_pack_texels(src, s->texels, count, (int)store, st);
+      }
       TS_CHECK_LAUNCH();
       if (staging) TS_CUDA(cudaFreeAsync(staging, st));
     }

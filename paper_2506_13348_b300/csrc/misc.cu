@@ -18,11 +18,48 @@ __global__ void k_pack_texels(const float* __restrict__ src, void* __restrict__ 
   }
 }
 
-void launch_pack_texels(const float* src, void* dst, long long n, int dtype, cudaStream_t st) {
-  if (n > 0) {
-    k_pack_texels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n, dtype);
-    note_launches(1);
+// Same, eight elements (one texel) per step: two 16-byte loads, one 16-byte
+// store (bf16 / f16) -- HBM-bound, grid-stride over a grid sized to the SMs.
+template <int DT>
+__global__ void __launch_bounds__(256) k_pack_texels8(const float4* __restrict__ src, uint4* __restrict__ dst,
+                                                      long long n8) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x) {
+    const float4 a = __ldcs(src + 2 * i), b = __ldcs(src + 2 * i + 1);
+    uint4 o;
+    if (DT == DT_BF16) {
+      const __nv_bfloat162 p0 = __floats2bfloat162_rn(a.x, a.y), p1 = __floats2bfloat162_rn(a.z, a.w);
+      const __nv_bfloat162 p2 = __floats2bfloat162_rn(b.x, b.y), p3 = __floats2bfloat162_rn(b.z, b.w);
+      o = make_uint4(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1),
+                     *reinterpret_cast<const uint32_t*>(&p2), *reinterpret_cast<const uint32_t*>(&p3));
+    } else {
+      const __half2 p0 = __floats2half2_rn(a.x, a.y), p1 = __floats2half2_rn(a.z, a.w);
+      const __half2 p2 = __floats2half2_rn(b.x, b.y), p3 = __floats2half2_rn(b.z, b.w);
+      o = make_uint4(*reinterpret_cast<const uint32_t*>(&p0), *reinterpret_cast<const uint32_t*>(&p1),
+                     *reinterpret_cast<const uint32_t*>(&p2), *reinterpret_cast<const uint32_t*>(&p3));
+    }
+    dst[i] = o;
   }
+}
+
+void launch_pack_texels(const float* src, void* dst, long long n, int dtype, cudaStream_t st) {
+  if (n <= 0) return;
+  const bool vec = dtype != DT_F32 && n % 8 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+  if (vec) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long n8 = n / 8;
+    const long long want = (n8 + 255) / 256;
+    const unsigned grid = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    if (dtype == DT_BF16)
+      k_pack_texels8<DT_BF16><<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(src), reinterpret_cast<uint4*>(dst), n8);
+    else
+      k_pack_texels8<DT_F16><<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(src), reinterpret_cast<uint4*>(dst), n8);
+  } else {
+    k_pack_texels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n, dtype);
+  }
+  note_launches(1);
 }
 
 void launch_pack_f16(const float* src, __half* dst, long long n, cudaStream_t st) {

@@ -552,6 +552,9 @@ def run_large_scene(args, device):
     for i in range(args.large_warmup):
         tr.step(cams[(i * V) % 40:(i * V) % 40 + V], targets, outs, dls)
     torch.cuda.synchronize()
+    from paper_2506_13348_b300 import _lib
+    _lib.profile_enable(True)
+    _lib.profile_report()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(args.large_steps):
@@ -559,14 +562,28 @@ def run_large_scene(args, device):
         tr.step(cams[j:j + V], targets, outs, dls)
     e1.record()
     torch.cuda.synchronize()
+    st = _lib.profile_report()
+    _lib.profile_enable(False)
     ms = e0.elapsed_time(e1) / args.large_steps
+    # per step: stage totals; Adam moves, per parameter, p g m v in (16 B), p m v
+    # out and g zeroed (16 B), plus the 2-byte stored copy of each texel
+    stage_ms = {k: round(v[1] / args.large_steps, 3) for k, v in st.items()}
+    n_tex = n * 8 * 8 * 8
+    n_geo = n * (3 + 4 + 2 + 1)
+    adam_bytes = (n_tex + n_geo) * 32 + n_tex * 2
+    peaks, peak_kind = load_peaks()
+    adam_ms = stage_ms.get("adam", float("nan"))
+    adam_gbs = adam_bytes / (adam_ms / 1e3) / 1e9
     peak = torch.cuda.max_memory_allocated(dev) / 1e9
     free, total = torch.cuda.mem_get_info(dev)
     out = {"workload": "cfg4: 3M splats in [-5,5]^3 (60% on 32 spheres, 40% uniform), 8x8 texels BF16 with "
                        "FP32 masters + Adam, 4 views of 1600x1064 per step",
            "splats": n, "steps": args.large_steps, "ms_per_step": ms,
            "mpix_per_s": V * W * H / 1e6 / (ms / 1e3),
-           "torch_peak_alloc_gb": peak, "device_used_gb": (total - free) / 1e9}
+           "torch_peak_alloc_gb": peak, "device_used_gb": (total - free) / 1e9,
+           "stages_ms_per_step": stage_ms,
+           "adam": {"ms_per_step": adam_ms, "bytes_per_step": adam_bytes, "gb_per_s": adam_gbs,
+                    "frac_of_hbm": adam_gbs / float(peaks.get("hbm_gbs", 6400.0)), "peak": peak_kind}}
     sc.close()
     del tr
     torch.cuda.empty_cache()

@@ -429,10 +429,11 @@ __global__ void __launch_bounds__(256) k_emit_pairs(ViewTable vt, const uint32_t
 void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_t* offsets,
                        const uint32_t* counts_sorted, const int4* rects, uint32_t* tile_keys,
                        uint32_t* pair_items, int n, cudaStream_t st) {
-  if (n > 0)
+  if (n > 0) {
     k_emit_pairs<<<ceil_div(n, 256), 256, 0, st>>>(vt, order, offsets, counts_sorted, rects, tile_keys,
                                                   pair_items, n);
     note_launches(1);
+  }
 }
 
 // Tile ranges from the sorted tile ids: 4 keys per thread (one 16-byte

@@ -163,3 +163,49 @@ def test_reduced_precision_atlas_with_both_features(P, store, tdt):
         bad = np.abs(g - r) > 1e-3 * scale + 1e-6
         assert not bad.any(), (name, int(bad.sum()), float(np.abs(g - r).max()), float(scale))
     saved.release()
+
+
+def test_features_on_edge_cases(P):
+    """Both features on: an empty scene, a fully culled scene (zero image,
+    zero gradients) and a single splat on a ragged 17 x 13 image (oracle)."""
+    env = sg.make_env(0, cube_res=8, irr_res=4, lut_res=16)
+    cam = sg.look_at_camera((4.0, 0.0, 0.0), 40, 24)
+    empty = dict(means=np.zeros((0, 3), np.float32), quats=np.zeros((0, 4), np.float32),
+                 scales=np.zeros((0, 2), np.float32), opacity=np.zeros(0, np.float32),
+                 texels=np.zeros((0, 4, 4, 8), np.float32), T=4, sh=np.zeros((0, 9, 3), np.float32),
+                 normal_encoding="xy")
+    vis = torch.full((24, 40), 0.5, device="cuda")
+    sc = P.Scene.from_arrays(empty, env)
+    out, saved = P.render(sc, dict(cam, vis=vis), save=True)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
+    saved.release()
+    # every splat behind the camera
+    culled = xy_scene(n=50)
+    culled["means"][:, 0] += 10.0
+    culled["sh"] = np.ones((50, 4, 3), np.float32)
+    sc = P.Scene.from_arrays(culled, env)
+    out, saved = P.render(sc, dict(cam, vis=vis), save=True)
+    grads = P.zero_grads(sc)
+    P.render_backward(saved, torch.ones(24, 40, 4, device="cuda"), grads)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
+    for k in ("means", "texels", "sh"):
+        assert torch.count_nonzero(grads[k]).item() == 0
+    saved.release()
+    # one splat, ragged image
+    one = xy_scene(n=1, seed=9)
+    one["means"][:] = 0.0
+    one["scales"][:] = 0.4
+    one["opacity"][:] = 0.9
+    one["sh"] = (np.random.default_rng(4).normal(size=(1, 9, 3)) * 0.3).astype(np.float32)
+    cam1 = sg.look_at_camera((3.0, 0.4, 0.2), 17, 13)
+    v1 = np.random.default_rng(5).uniform(0, 1, size=(13, 17)).astype(np.float32)
+    ref = R.render(one, cam1, env, vis=v1)
+    sc = P.Scene.from_arrays(one, env)
+    out, _ = P.render(sc, dict(cam1, vis=torch.from_numpy(v1).cuda()))
+    torch.cuda.synchronize()
+    amb = ref["ambiguous"].numpy()
+    assert (ref["A"].numpy() > 0).sum() > 20
+    err = np.abs(out.cpu().numpy().astype(np.float64) - ref["rgba"].numpy()).max(-1)
+    assert err[~amb].max() <= 1e-4

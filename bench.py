@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--sampling-views", type=int, default=40)
     ap.add_argument("--no-image-loss", action="store_true", help="skip the L1 + D-SSIM timing after the step")
     ap.add_argument("--no-fp32-probe", action="store_true", help="skip the FP32 rate probe after the step")
+    ap.add_argument("--hbm-kernels-only", action="store_true",
+                    help="time the atlas pack and Adam alone on 1 GiB of float32 (for profiling)")
     ap.add_argument("--no-features", action="store_true",
                     help="skip the indirect-light / two-component-normal step timings")
     ap.add_argument("--features-only", action="store_true")
@@ -773,6 +775,51 @@ def run_features(args, device):
     return res
 
 
+def run_hbm_kernels(args, device):
+    """The HBM-bound kernels alone: the atlas pack (float32 -> bf16) and one
+    Adam step with its bf16 stored copy, on 2^28 float32 values (1 GiB),
+    3 warm-up and 10 timed launches each, CUDA events."""
+    import torch
+
+    import paper_2506_13348_b300 as P
+    from paper_2506_13348_b300 import _lib
+    import scenegen as sg
+
+    dev = torch.device("cuda", device)
+    n = 1 << 28
+    T = 8
+    n_splats = n // (T * T * 8)
+    geo = sg.make_scene(1, n=n_splats, with_texels=False)
+    tex = torch.rand(n, device=dev)
+    sc = P.Scene(device)
+    sc.upload_gaussians(geo["means"], geo["quats"], geo["scales"], geo["opacity"])
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    out = {"values": n, "peak": f"{hbm:.0f} GB/s ({peak_kind})"}
+    _lib.profile_enable(True)
+    for i in range(13):
+        if i == 3:
+            _lib.profile_report()
+        _lib.check(_lib.lib().ts_upload_atlas(sc.handle, T, 8, 1, tex.data_ptr(), 1, None), "ts_upload_atlas")
+    st = _lib.profile_report()
+    pms = st["atlas_pack"][1] / st["atlas_pack"][0]
+    out["pack_bf16"] = {"ms": pms, "gb_per_s": n * 6 / (pms / 1e3) / 1e9, "frac": n * 6 / (pms / 1e3) / 1e9 / hbm}
+    p, g, m, v = tex, torch.rand(n, device=dev), torch.zeros(n, device=dev), torch.zeros(n, device=dev)
+    shadow, _, _ = P.scene_texels(sc)
+    for i in range(13):
+        if i == 3:
+            _lib.profile_report()
+        P.adam_update(p, g, m, v, i + 1, 1e-3, shadow_ptr=shadow, shadow_dtype="bf16", zero_grad=False)
+    st = _lib.profile_report()
+    _lib.profile_enable(False)
+    ams = st["adam"][1] / st["adam"][0]
+    # p g m v in, p m v out, the bf16 copy out (the gradient is kept here)
+    ab = n * (16 + 12 + 2)
+    out["adam_bf16_shadow"] = {"ms": ams, "gb_per_s": ab / (ams / 1e3) / 1e9, "frac": ab / (ams / 1e3) / 1e9 / hbm}
+    sc.close()
+    return out
+
+
 def run_sampling(args, device):
     """The shape of the paper's Table 3: forward-render throughput of textured
     splats relative to the same splats without textures, for T = 2, 4, 8, 16,
@@ -876,7 +923,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.serve_only or args.large_only or args.precision_only or args.sampling_only or args.features_only:
+    if (args.serve_only or args.large_only or args.precision_only or args.sampling_only or args.features_only
+            or args.hbm_kernels_only):
         import torch
         torch.cuda.set_device(dist_env()[2])
         res = {}
@@ -890,6 +938,8 @@ def main():
             res["texture_sampling"] = run_sampling(args, dist_env()[2])
         if args.features_only:
             res["features"] = run_features(args, dist_env()[2])
+        if args.hbm_kernels_only:
+            res["hbm_kernels"] = run_hbm_kernels(args, dist_env()[2])
         print(json.dumps(res))
         return 0
     return run_ours(args)

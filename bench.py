@@ -35,10 +35,15 @@ UNIT = "Mpix/s"
 N_SPLATS, T_TEX, RES, N_CAMS = 200_000, 8, 800, 100
 FP32_LANES_PER_SM, N_SM = 128, 148
 
-# FP32 operations per fragment of the algorithm ("roofline"):
-# every evaluated (pixel, splat) pair costs the homography and the support cut;
-# every blended fragment adds kernel/alpha, texel setup, 8-channel bilinear,
-# normal mapping and blending; the backward recomputes that and adds the adjoint.
+# FP32 operations per fragment of the algorithm (FMA = 2): every evaluated
+# (pixel, splat) pair costs the homography (6 FMA, a reciprocal, 2 mul) and the
+# support cut; every blended fragment adds kernel/alpha (8), texel setup (8),
+# the 8-channel bilinear filter (72 + weights), normal mapping (15) and
+# blending (19); the backward recomputes that and adds the adjoint (~260: the
+# tangent-normal pull-back, the corner dot products, alpha / (u, v) / depth
+# derivatives, the frame torque and the per-fragment texel and record sums).
+# Shading costs 150 per pixel forward (fused into the forward rasteriser) and
+# 400 per pixel in the adjoint (its own kernel).
 FLOP_EVAL = 15
 FLOP_BLEND_FWD = 124
 FLOP_BLEND_BWD = 124 + 260

@@ -71,7 +71,6 @@ def parse():
     ap.add_argument("--large-warmup", type=int, default=3)
     ap.add_argument("--no-precision", action="store_true", help="skip the reduced-precision atlas measurement")
     ap.add_argument("--precision-only", action="store_true")
-    ap.add_argument("--precision-samples", type=int, default=64)
     ap.add_argument("--no-sampling", action="store_true", help="skip the texture-sampler comparison (Table 3 shape)")
     ap.add_argument("--sampling-only", action="store_true")
     ap.add_argument("--sampling-views", type=int, default=40)
@@ -454,57 +453,46 @@ def run_serving(args, device):
 def run_precision(args, device):
     """Reduced-precision atlas: 500k sphere splats, 16x16 texels x 8
     channels, 1920x1080, 6-level 128 FP16 cube.  Per stored dtype (f32,
-    bf16, f16): forward Mpix/s over 10 views and the storage error of the
-    image against the FP64 oracle fed the float32 texels (sampled pixels of
-    2 views; the oracle uses the same FP16 cube, so only the atlas differs)."""
+    bf16, f16): forward Mpix/s over 10 views, the atlas pack's bandwidth,
+    and the storage error of the bf16 / f16 images against the f32 atlas's
+    images of the same views (whole images of views 0 and 5; the f32 path is
+    the one the parity tests hold within 1e-4 of the FP64 oracle)."""
     import numpy as np
     import torch
 
     import paper_2506_13348_b300 as P
+    from paper_2506_13348_b300 import _lib
     import scenegen as sg
-    from oracle import keys as K
-    from oracle import render as R
 
     dev = torch.device("cuda", device)
     geo = sg.make_scene(2, with_texels=False)
-    tex = sg.scenes.texels_torch(len(geo["opacity"]), 16, seed=2, device="cpu")
+    tex = sg.scenes.texels_torch(len(geo["opacity"]), 16, seed=2, device=dev)  # the pack reads HBM
     env = sg.make_env(2, cube_res=128, levels=6, irr_res=16, lut_res=128)
-    env16 = dict(env, spec=[m.astype(np.float16).astype(np.float32) for m in env["spec"]],
-                 irr=env["irr"].astype(np.float16).astype(np.float32))
     W, H = 1920, 1080
     cams = sg.fibonacci_cameras(10, 4.0, W, H)
-    scene64 = dict(geo, texels=tex.numpy(), T=16)
-    rng = np.random.default_rng(22)
-    samples = []
-    for ci in (0, 5):
-        px, py = rng.integers(0, W, args.precision_samples), rng.integers(0, H, args.precision_samples)
-        kl = K.build_keys(scene64, cams[ci])
-        ref = R.render_pixels(scene64, cams[ci], env16, px, py, keylist=kl)
-        samples.append((ci, px, py, ref["rgba"].detach().numpy(), ref["ambiguous"].numpy()))
+    err_views = (0, 5)
     out = {"workload": "cfg2: 500k splats, 16x16 texels x 8 ch, 1920x1080, 6-level 128 FP16 cube, 10 views",
-           "error_samples": f"{args.precision_samples} random pixels of views 0 and 5 vs the FP64 oracle with FP32 texels"}
+           "error_reference": "images of views 0 and 5 (RGB, every pixel) rendered from the f32 atlas"}
     img = torch.empty(H, W, 4, device=dev)
-    from paper_2506_13348_b300 import _lib
-    tex_dev = tex.to(dev)  # the pack (S0) reads float32 texels already in HBM
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
+    ref_imgs = {}
     for store in ("f32", "bf16", "f16"):
         sc = P.Scene(device)
         sc.upload_gaussians(geo["means"], geo["quats"], geo["scales"], geo["opacity"])
         _lib.profile_enable(True)
         _lib.profile_report()
-        sc.upload_atlas(tex_dev, store)
+        sc.upload_atlas(tex, store)
         st = _lib.profile_report()
         _lib.profile_enable(False)
         sc.upload_envmap(env, "f16")
         errs = []
-        for ci, px, py, ref, amb in samples:
+        for ci in err_views:
             P.render(sc, cams[ci], out=img)
-            torch.cuda.synchronize()
-            g = img.cpu().numpy()[py, px].astype(np.float64)
-            e = np.abs(g - ref)[~amb][:, :3]
-            errs.append(e)
-        e = np.concatenate(errs)
+            if store == "f32":
+                ref_imgs[ci] = img[..., :3].clone()
+            else:
+                errs.append((img[..., :3] - ref_imgs[ci]).abs().double().flatten())
         for i in range(2):
             P.render(sc, cams[i], out=img)
         torch.cuda.synchronize()
@@ -515,18 +503,20 @@ def run_precision(args, device):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / len(cams)
-        mse = float((e ** 2).mean())
-        pack = {}
+        res = {"fwd_ms_per_view": ms, "fwd_mpix_per_s": W * H / 1e6 / (ms / 1e3)}
         if "atlas_pack" in st:  # bf16 / f16: 4 B read + 2 B written per channel
             pms = st["atlas_pack"][1] / max(1, st["atlas_pack"][0])
-            gbs = tex_dev.numel() * 6 / (pms / 1e3) / 1e9
-            pack = {"pack_ms": pms, "pack_gb_per_s": gbs, "pack_frac_of_hbm": gbs / hbm,
-                    "pack_peak": f"{hbm:.0f} GB/s ({peak_kind})"}
-        out[store] = {"fwd_ms_per_view": ms, "fwd_mpix_per_s": W * H / 1e6 / (ms / 1e3), **pack,
-                      "max_abs_err": float(e.max()), "mean_abs_err": float(e.mean()),
-                      "psnr_db": float(10 * np.log10(1.0 / mse)) if mse > 0 else None}
+            gbs = tex.numel() * 6 / (pms / 1e3) / 1e9
+            res.update(pack_ms=pms, pack_gb_per_s=gbs, pack_frac_of_hbm=gbs / hbm,
+                       pack_peak=f"{hbm:.0f} GB/s ({peak_kind})")
+        if errs:
+            e = torch.cat(errs)
+            mse = float((e * e).mean())
+            res.update(max_abs_err=float(e.max()), mean_abs_err=float(e.mean()),
+                       psnr_db=float(10 * np.log10(1.0 / mse)) if mse > 0 else None)
+        out[store] = res
         sc.close()
-    del tex, tex_dev
+    del tex, ref_imgs
     torch.cuda.empty_cache()
     return out
 

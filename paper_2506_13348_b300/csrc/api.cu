@@ -482,19 +482,36 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     launch_gather_counts(order, counts, cs, n_items, st);
     launch_exclusive_scan(cs, offs, n_items, rtemp, st);
   }
+  // a batch whose pair count could pass 2^31 (n x tiles bound) also sums the
+  // counts in 64 bits: the 32-bit scan above would wrap
+  unsigned long long* d_total = nullptr;
+  {
+    long long bound = 0;
+    for (int i = 0; i < n_views; ++i) bound += (long long)vt.v[i].n_splats * vt.v[i].tiles_x * vt.v[i].tiles_y;
+    if (bound > INT32_MAX / 2) {
+      TS_CUDA_K(tmp.alloc((void**)&d_total, sizeof(unsigned long long)));
+      launch_sum_counts(cs, n_items, d_total, st);
+    }
+  }
   TS_CHECK_LAUNCH();
 
   // total pair count -> host (one synchronisation per batch)
-  static thread_local uint32_t* h_tail = nullptr;
-  if (!h_tail) TS_CUDA_K(cudaHostAlloc((void**)&h_tail, 2 * sizeof(uint32_t), cudaHostAllocDefault));
-  h_tail[0] = h_tail[1] = 0;
+  struct HostTail {
+    uint32_t tail[2];
+    unsigned long long total;
+  };
+  static thread_local HostTail* h_tail = nullptr;
+  if (!h_tail) TS_CUDA_K(cudaHostAlloc((void**)&h_tail, sizeof(HostTail), cudaHostAllocPortable));
+  h_tail->tail[0] = h_tail->tail[1] = 0;
+  h_tail->total = 0;
   if (n_items > 0) {
-    TS_CUDA_K(cudaMemcpyAsync(&h_tail[0], offs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
-    TS_CUDA_K(cudaMemcpyAsync(&h_tail[1], cs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
+    TS_CUDA_K(cudaMemcpyAsync(&h_tail->tail[0], offs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
+    TS_CUDA_K(cudaMemcpyAsync(&h_tail->tail[1], cs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
+    if (d_total) TS_CUDA_K(cudaMemcpyAsync(&h_tail->total, d_total, 8, cudaMemcpyDeviceToHost, st));
   }
   TS_CUDA_K(cudaStreamSynchronize(st));
-  const long long K = (long long)h_tail[0] + h_tail[1];
-  if (K > INT32_MAX / 2) {
+  const long long K = (long long)h_tail->tail[0] + h_tail->tail[1];
+  if (K > INT32_MAX / 2 || (d_total && h_tail->total > (unsigned long long)(INT32_MAX / 2))) {
     cleanup_keep();
     return fail(TS_ERR_CAPACITY, "ts_render_views: too many (tile, splat) pairs");
   }

@@ -36,6 +36,7 @@ int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int n
                    void* temp, cudaStream_t st);
 int radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
                    void* temp, cudaStream_t st);
+void launch_sum_counts(const uint32_t* counts, int n, unsigned long long* total, cudaStream_t st);
 void launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t* counts_sorted, int n,
                           cudaStream_t st);
 void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_t* offsets,

@@ -10,6 +10,8 @@
 // depths) inside each tile, so the result equals a sort of 64-bit
 // (tile << 32 | depth bits) keys with ties by item id, at a fraction of the
 // traffic: 8-byte pairs over 2 passes instead of 12-byte pairs over 6.
+#include <algorithm>
+
 #include "kernels.h"
 #include "prof.h"
 
@@ -362,6 +364,34 @@ __global__ void k_gather_counts(const uint32_t* __restrict__ order, const uint32
                                 uint32_t* __restrict__ out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = counts[order[i]];
+}
+
+// 64-bit total of the per-splat pair counts (the 32-bit scan would wrap past
+// 2^32 pairs): one reduction per block, one atomic per block.
+__global__ void __launch_bounds__(256) k_sum_counts(const uint32_t* __restrict__ counts, int n,
+                                                    unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long part[8];
+  unsigned long long s = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += counts[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    if (t) atomicAdd(total, t);
+  }
+}
+
+void launch_sum_counts(const uint32_t* counts, int n, unsigned long long* total, cudaStream_t st) {
+  cudaMemsetAsync(total, 0, sizeof(unsigned long long), st);
+  if (n > 0) {
+    const int blocks = std::min(ceil_div(n, 256), 148 * 4);
+    k_sum_counts<<<blocks, 256, 0, st>>>(counts, n, total);
+    note_launches(1);
+  }
 }
 
 void launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t* counts_sorted, int n,

@@ -169,3 +169,30 @@ def test_fp32_rate_probe(P):
     scalar, paired = _lib.measure_fp32_peak(0)
     assert 20.0 < scalar < 120.0, scalar
     assert 20.0 < paired < 240.0, paired
+
+
+def test_pair_count_past_32_bits_is_a_capacity_error(P):
+    """300k splats that each cover every tile of a 2048^2 view: 4.9e9
+    (tile, splat) pairs, past what the 32-bit count scan can hold.  The
+    64-bit total catches it before any pair buffer is sized from the
+    wrapped scan: TS_ERR_CAPACITY, and the scene still renders afterwards
+    with a camera that sees a few splats."""
+    n = 300_000
+    rng = np.random.default_rng(1)
+    means = np.zeros((n, 3), np.float32)
+    means[:, 2] = 5.0 + rng.uniform(0, 1, n).astype(np.float32)
+    scene = dict(means=means, quats=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                 scales=np.full((n, 2), 10.0, np.float32), opacity=np.full(n, 0.5, np.float32),
+                 texels=np.full((n, 1, 1, 8), 0.5, np.float32), T=1)
+    env = sg.make_env(0, cube_res=8, irr_res=4, lut_res=16)
+    cam = dict(R=np.eye(3, dtype=np.float32), t=np.zeros(3, np.float32), fx=np.float32(1024.0),
+               fy=np.float32(1024.0), cx=np.float32(1024.0), cy=np.float32(1024.0), W=2048, H=2048)
+    sc = P.Scene.from_arrays(scene, env)
+    with pytest.raises(P.TexSplatError, match="CAPACITY"):
+        P.render(sc, cam)
+    small = dict(cam, W=64, H=64, cx=np.float32(32.0), cy=np.float32(32.0), fx=np.float32(32.0),
+                 fy=np.float32(32.0))
+    # 16 tiles x 300k splats = 4.8e6 pairs: renders
+    out, _ = P.render(sc, small)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all() and out[..., 3].min().item() > 0.99

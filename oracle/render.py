@@ -224,7 +224,7 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
             # derivative kinks of blended fragments (value continuous, slope
             # not): bilinear cell boundaries at texel centres (incl. the
             # clamp edges) and the 0.99 opacity clamp
-            m_k = KINK_TEX
+            m_k = KINK_TEX * max(1.0, T / 8.0)  # texel coordinate = (u + 3) T / 6 - 1/2: error grows with T
             kink = torch.zeros_like(blended)
             for coord in (s * T - 0.5, t * T - 0.5):
                 fr_ = coord - torch.floor(coord)
@@ -243,7 +243,8 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
 
 # Half-widths (in texel units) of the bands around texture-lookup kinks that
 # the gradient comparison excludes: FP32 (u, v) error ~1e-6 relative maps to
-# ~4e-6 texel at T = 8.
+# ~4e-6 texel at T = 8; the band is KINK_TEX at T <= 8 and grows as T / 8
+# beyond (the texel coordinate scales u by T / 6).
 KINK_TEX = 1e-5
 # |cos| between view ray and splat normal below which gradients are excluded
 # (~1.7 deg from edge-on; isolated splats match to ~1e-6 up to 85 deg tilt,

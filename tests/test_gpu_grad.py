@@ -79,3 +79,36 @@ def test_grad_parity_bf16_atlas(P):
     env = sg.make_env(7, cube_res=8, irr_res=4, lut_res=16)
     cam = sg.look_at_camera((3.0, -1.0, 0.5), 80, 80)
     run_case(P, scene, env, cam, seed=3, store="bf16")
+
+
+@pytest.mark.parametrize("T", [1, 32])
+def test_grad_parity_texture_resolution_limits(P, T):
+    """The smallest (one texel: per-splat attributes) and the largest
+    texture resolution the ABI accepts."""
+    scene = sg.make_scene(1, n=300, T=T, seed=10 + T)
+    env = sg.make_env(8, cube_res=8, levels=2, irr_res=4, lut_res=16)
+    cam = sg.look_at_camera((2.4, -1.2, 0.9), 72, 60)
+    kl = K.build_keys(scene, cam)
+    sc = P.Scene.from_arrays(scene, env)
+    out, _ = P.render(sc, cam)
+    torch.cuda.synchronize()
+    ref = R.render(scene, cam, env, keylist=kl)
+    amb = ref["ambiguous"].numpy()
+    err = np.abs(out.cpu().numpy().astype(np.float64) - ref["rgba"].numpy()).max(-1)
+    assert err[~amb].max() <= 1e-4
+    run_case(P, scene, env, cam, seed=4)
+
+
+def test_batch_of_the_maximum_view_count_equals_alone_renders(P):
+    scene = sg.make_scene(1, n=2000, T=4, seed=12)
+    env = sg.make_env(9, cube_res=8, irr_res=4, lut_res=16)
+    cams = [sg.look_at_camera(tuple(np.asarray(c["R"]).T @ -np.asarray(c["t"])), 24 + (i % 5) * 7, 20 + (i % 3) * 9)
+            for i, c in enumerate(sg.fibonacci_cameras(32, 3.5, 8, 8))]
+    sc = P.Scene.from_arrays(scene, env)
+    outs, _ = P.render_views([sc] * 32, cams)
+    for c, o in zip(cams, outs):
+        a, _ = P.render(sc, c)
+        torch.cuda.synchronize()
+        assert torch.equal(a, o)
+    with pytest.raises(P.TexSplatError, match="TS_ERR_ARG"):
+        P.render_views([sc] * 33, cams + cams[:1])

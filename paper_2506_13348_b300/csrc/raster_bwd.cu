@@ -34,8 +34,8 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
   __shared__ __align__(16) float s_gi[8][kRecGrads][36];  // record gradients, value-major, per warp
   // indirect light: per lane dL/dl (3) and the SH basis (9), value-major
   __shared__ __align__(16) float s_sh[IND ? 8 : 1][12][36];
-  __shared__ float4 s_rec[8][32][5];               // the records of a chunk
-  __shared__ uint32_t s_item[8][32];
+  __shared__ __align__(16) float4 s_rec[8][2][32][5];  // the records of this chunk and the next
+  __shared__ uint32_t s_item[8][2][32];
   const int warp = threadIdx.x >> 5;
   const int tile = blockIdx.x;
   const int v = find_view(vt, tile);
@@ -87,42 +87,56 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
   const float bx0 = (float)(px - (lane & 7)) + 0.5f - V.cx, bx1 = bx0 + 7.f;
   const float by0 = (float)(py - (lane >> 3)) + 0.5f - V.cy, by1 = by0 + 3.f;
 
-  // The list is taken 32 entries at a time, back to front: lane t loads the
-  // record of entry ch - t and tests it against the warp's block; only the
-  // surviving entries are processed, in back-to-front order.
-  for (int ch = hi; ch >= lo; ch -= 32) {
+  // The list is taken 32 entries at a time, back to front: lane t's entry
+  // ch - t has its record copied into shared memory by cp.async one chunk
+  // ahead (the next chunk's copy runs while the warp works on this one; the
+  // item ids run one chunk further ahead in a register); the lane tests it
+  // against the warp's block and only the surviving entries are processed,
+  // in back-to-front order.
+  auto issue = [&](int b, int c, uint32_t it) {
+    if (c - lane >= lo) {
+      const float4* rp = reinterpret_cast<const float4*>(rec + it);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_rec[warp][b][lane][q]);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(rp + q) : "memory");
+      }
+      s_item[warp][b][lane] = it;
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  uint32_t it_next = (hi - lane >= lo) ? __ldg(pair_items + hi - lane) : 0u;
+  issue(0, hi, it_next);
+  it_next = (hi - 32 - lane >= lo) ? __ldg(pair_items + hi - 32 - lane) : 0u;
+  int buf = 0;
+  for (int ch = hi; ch >= lo; ch -= 32, buf ^= 1) {
+    issue(buf ^ 1, ch - 32, it_next);
+    it_next = (ch - 64 - lane >= lo) ? __ldg(pair_items + ch - 64 - lane) : 0u;
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncwarp();
     const int e = ch - lane;
     bool cand = false;
     if (e >= lo) {
-      const uint32_t it = __ldg(pair_items + e);
-      const float4* rp = reinterpret_cast<const float4*>(rec + it);
       Record c;
-      c.r0 = __ldg(rp);
-      c.r1 = __ldg(rp + 1);
-      c.r2 = __ldg(rp + 2);
+      c.r0 = s_rec[warp][buf][lane][0];
+      c.r1 = s_rec[warp][buf][lane][1];
+      c.r2 = s_rec[warp][buf][lane][2];
       cand = block_may_hit(c, bx0, bx1, by0, by1);
-      s_rec[warp][lane][0] = c.r0;
-      s_rec[warp][lane][1] = c.r1;
-      s_rec[warp][lane][2] = c.r2;
-      s_rec[warp][lane][3] = __ldg(rp + 3);
-      s_rec[warp][lane][4] = __ldg(rp + 4);
-      s_item[warp][lane] = it;
     }
     const unsigned cmask = __ballot_sync(FULL, cand);
-    __syncwarp();
   for (unsigned cm = cmask; cm; cm &= cm - 1) {
     const int t = __ffs(cm) - 1;
     const int j = ch - t;
-    const uint32_t item = s_item[warp][t];
+    const uint32_t item = s_item[warp][buf][t];
     Record r;
-    r.r0 = s_rec[warp][t][0];
-    r.r1 = s_rec[warp][t][1];
-    r.r2 = s_rec[warp][t][2];
+    r.r0 = s_rec[warp][buf][t][0];
+    r.r1 = s_rec[warp][buf][t][1];
+    r.r2 = s_rec[warp][buf][t][2];
     Frag f;
     const bool ok = (j <= last) && eval_frag(r, xp, yp, f);
     if (__any_sync(FULL, ok)) {
-      r.r3 = s_rec[warp][t][3];
-      r.r4 = s_rec[warp][t][4];
+      r.r3 = s_rec[warp][buf][t][3];
+      r.r4 = s_rec[warp][buf][t][4];
       const long long splat = (long long)item - V.item_off;
       float t8[8], w4[4] = {0.f, 0.f, 0.f, 0.f};
       TexSample ts_;
@@ -443,6 +457,7 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
   }
     __syncwarp();
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,

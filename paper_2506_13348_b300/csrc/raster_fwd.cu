@@ -3,11 +3,12 @@
 //
 // Each warp walks the tile's depth-sorted splat list front to back on its
 // own (no block-wide barrier), 32 entries at a time:
-//   0. lane t loads the first 48 bytes of entry t's record (the homography
-//      rows and the opacity), stages them in shared memory and tests the
-//      entry against the warp's whole pixel block (conservative, see
-//      block_may_hit); typically about half of the entries of a tile list
-//      miss a given block and are dropped here;
+//   0. lane t's entry has its first 48 bytes (the homography rows and the
+//      opacity) copied into shared memory by cp.async one chunk ahead (the
+//      copy of chunk k+1 runs while the warp works on chunk k); the lane
+//      tests the entry against the warp's whole pixel block (conservative,
+//      see block_may_hit): most entries of a tile list miss a given block
+//      and are dropped here;
 //   1. the warp takes the surviving entries in order: every lane evaluates
 //      the entry at its pixel (closed-form (u,v) of the splat, support cut,
 //      Gaussian, opacity -- Sec. 3.1, Eq. 2) and the lanes it covers blend
@@ -69,44 +70,60 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
   }
 
   // per-warp walk: no CTA barrier; lane t stages entry c0 + t's first 48
-  // bytes in shared memory for the block test and the lockstep loop
+  // bytes in shared memory for the block test and the lockstep loop.  The
+  // records of the next chunk are copied asynchronously (cp.async) while
+  // the warp works on the current one; the item ids run one chunk further
+  // ahead in a register.
   {
-    __shared__ float4 s_r[8][32][3];
-    __shared__ uint32_t s_it[8][32];
+    __shared__ __align__(16) float4 s_r[8][2][32][3];
+    __shared__ uint32_t s_it[8][2][32];
     const int warp = threadIdx.x >> 5;
-    for (unsigned c0 = range.x; c0 < range.y; c0 += 32) {
+    auto issue = [&](int b, unsigned c, uint32_t it) {
+      if (c + lane < range.y) {
+        const float4* rp = reinterpret_cast<const float4*>(rec + it);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_r[warp][b][lane][q]);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(rp + q) : "memory");
+        }
+        s_it[warp][b][lane] = it;
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    uint32_t it_next = (range.x + lane < range.y) ? __ldg(pair_items + range.x + lane) : 0u;
+    issue(0, range.x, it_next);
+    it_next = (range.x + 32 + lane < range.y) ? __ldg(pair_items + range.x + 32 + lane) : 0u;
+    int b = 0;
+    for (unsigned c0 = range.x; c0 < range.y; c0 += 32, b ^= 1) {
       if (__all_sync(FULL, done)) break;
+      issue(b ^ 1, c0 + 32, it_next);  // next chunk's records
+      it_next = (c0 + 64 + lane < range.y) ? __ldg(pair_items + c0 + 64 + lane) : 0u;
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this chunk's records are in
+      __syncwarp();
       const unsigned e = c0 + lane;
       bool cand = false;
       if (e < range.y) {
-        const uint32_t it = __ldg(pair_items + e);
-        const float4* rp = reinterpret_cast<const float4*>(rec + it);
         Record c;
-        c.r0 = __ldg(rp);
-        c.r1 = __ldg(rp + 1);
-        c.r2 = __ldg(rp + 2);
+        c.r0 = s_r[warp][b][lane][0];
+        c.r1 = s_r[warp][b][lane][1];
+        c.r2 = s_r[warp][b][lane][2];
         cand = block_may_hit(c, bx0, bx1, by0, by1);
-        s_r[warp][lane][0] = c.r0;
-        s_r[warp][lane][1] = c.r1;
-        s_r[warp][lane][2] = c.r2;
-        s_it[warp][lane] = it;
       }
       const unsigned cmask = __ballot_sync(FULL, cand);
-      __syncwarp();
       for (unsigned m = cmask; m; m &= m - 1) {
         const int t = __ffs(m) - 1;
         Record r;
-        r.r0 = s_r[warp][t][0];
-        r.r1 = s_r[warp][t][1];
-        r.r2 = s_r[warp][t][2];
+        r.r0 = s_r[warp][b][t][0];
+        r.r1 = s_r[warp][b][t][1];
+        r.r2 = s_r[warp][b][t][2];
         Frag f;
         const bool ok = !done && eval_frag(r, xp, yp, f);
         if (__any_sync(FULL, ok)) {
-          const float4* rp = reinterpret_cast<const float4*>(rec + s_it[warp][t]);
+          const float4* rp = reinterpret_cast<const float4*>(rec + s_it[warp][b][t]);
           r.r3 = __ldg(rp + 3);
           r.r4 = __ldg(rp + 4);
           if (ok) {
-            const long long splat = (long long)s_it[warp][t] - V.item_off;
+            const long long splat = (long long)s_it[warp][b][t] - V.item_off;
             float x[8];
             if (SMP == SMP_SOFTWARE) {
               const TexSample ts_ = tex_setup(f.u, f.v, T);
@@ -151,6 +168,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
       }
       __syncwarp();
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
 
   if (inside) {

@@ -19,7 +19,7 @@
 
 namespace ts {
 
-constexpr int SB_THREADS = 256;
+constexpr int SB_THREADS = 512;
 constexpr int SB_MAX_SMEM_FLOATS = 24 * 1024;  // 96 KB
 
 // Offsets of each level / the irradiance cube inside one flat gradient array.
@@ -133,7 +133,7 @@ __device__ __forceinline__ void warp_cell_scatter(const EnvTarget& tg, bool live
 // IND: the views blended per-splat indirect light (mixed by the visibility);
 // a separate instance so the plain path keeps its register budget.
 template <bool IND>
-__global__ void __launch_bounds__(SB_THREADS, 2) k_shade_bwd(ViewTable vt, long long n_pix, float4* __restrict__ gxa,
+__global__ void __launch_bounds__(SB_THREADS, 1) k_shade_bwd(ViewTable vt, long long n_pix, float4* __restrict__ gxa,
                                                              GradTable g, EnvGradLayout lay, int use_smem) {
   extern __shared__ float s_env[];
   const bool want_env = (g.irr != nullptr) || (g.spec[0] != nullptr);
@@ -254,7 +254,7 @@ void launch_shade_bwd(const ViewTable& vt, float4* gxa, const GradTable& g, cuda
   }
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long want = (n_pix + SB_THREADS - 1) / SB_THREADS;
-  const int per_sm = use_smem ? 2 : 8;
+  const int per_sm = use_smem ? 1 : 4;
   const int grid = (int)((want < (long long)sms * per_sm) ? want : (long long)sms * per_sm);
   // a batch's views are all rendered with or all without indirect light
   if (vt.v[0].gind && vt.v[0].gxind)

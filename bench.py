@@ -62,9 +62,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-view latency measurement")
     ap.add_argument("--serve-only", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=1000)
-    ap.add_argument("--serve-warmup", type=int, default=100)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=1.0, help="arrival rate / plain saturated fps")
+    ap.add_argument("--serve-sweep", type=float, nargs="*", default=[0.5, 0.8, 1.0, 1.5],
+                    help="further arrival-rate factors timed after the headline one")
     ap.add_argument("--no-large", action="store_true", help="skip the 3M-splat training-step measurement")
     ap.add_argument("--large-only", action="store_true")
     ap.add_argument("--large-steps", type=int, default=10)
@@ -372,7 +374,9 @@ def run_serving(args, device):
     'plain' = FP32 atlas, one request at a time, FIFO on one stream;
     'served' = BF16 atlas, continuous batching (2 streams, up to 8 views per
     batch).  Both see the same arrival schedule at rate = rate_factor x the
-    plain renderer's saturated throughput."""
+    plain renderer's saturated throughput; the headline factor (1.0) is
+    reported in full and the sweep (0.5, 0.8, 1.0, 1.5) as p50 / p99 / fps.
+    200 warm-up requests, then 2000 measured ones per run."""
     import threading
 
     import numpy as np
@@ -427,27 +431,41 @@ def run_serving(args, device):
         return server.stats()
 
     arena = 24 << 30
-    plain = P.Server(device=device, arena_bytes=arena, n_streams=1, max_batch=1)
-    sat = run(plain, plain_sc, None)  # all at once: saturated FIFO throughput
-    rate = args.serve_rate * sat["fps"]
-    gaps = np.random.default_rng(33).exponential(1.0 / rate, size=nreq)
-    p = run(plain, plain_sc, gaps)
-    plain.close()
-    served = P.Server(device=device, arena_bytes=arena, n_streams=2, max_batch=8)
-    s = run(served, served_sc, gaps)
-    s_sat = run(served, served_sc, None)
-    served.close()
     keep = ("p50_ms", "p99_ms", "mean_ms", "fps", "mpix_per_s", "mean_batch", "completed", "rejected")
+    plain = P.Server(device=device, arena_bytes=arena, n_streams=1, max_batch=1)
+    served = P.Server(device=device, arena_bytes=arena, n_streams=2, max_batch=8)
+    sat = run(plain, plain_sc, None)  # all at once: saturated FIFO throughput
+    s_sat = run(served, served_sc, None)
+    # the headline rate, then the other arrival rates of the sweep (the same
+    # Poisson schedule scaled), each for both servers
+    factors = [args.serve_rate] + [f for f in args.serve_sweep if f != args.serve_rate]
+    sweep = {}
+    for f in factors:
+        rate = f * sat["fps"]
+        gaps = np.random.default_rng(33).exponential(1.0 / rate, size=nreq)
+        p = run(plain, plain_sc, gaps)
+        s = run(served, served_sc, gaps)
+        sweep[f"{f:g}"] = {"arrival_rate_fps": rate, "plain_fp32_one_at_a_time": {k: p[k] for k in keep},
+                           "served_bf16_batched": {k: s[k] for k in keep}}
+    plain.close()
+    served.close()
     for sc in plain_sc + served_sc:
         sc.close()
+    head = sweep[f"{args.serve_rate:g}"]
+    p, s, rate = head["plain_fp32_one_at_a_time"], head["served_bf16_batched"], head["arrival_rate_fps"]
     return {"workload": "cfg3: scenes of 200k/500k/1M splats (8x8 texels), Poisson arrivals, "
                         "resolutions {400^2, 800^2, 1280x720, 1920x1080}, radius U[3.5,5]",
             "requests": args.serve_requests, "warmup_requests": args.serve_warmup,
             "arrival_rate_fps": rate, "rate_factor": args.serve_rate,
             "plain_saturated_fps": sat["fps"], "served_saturated_fps": s_sat["fps"],
             "served_saturated_mean_batch": s_sat["mean_batch"],
-            "plain_fp32_one_at_a_time": {k: p[k] for k in keep},
-            "served_bf16_batched": {k: s[k] for k in keep}}
+            "plain_fp32_one_at_a_time": p, "served_bf16_batched": s,
+            "rate_sweep": {f: {"plain_p50_ms": v["plain_fp32_one_at_a_time"]["p50_ms"],
+                               "plain_p99_ms": v["plain_fp32_one_at_a_time"]["p99_ms"],
+                               "served_p50_ms": v["served_bf16_batched"]["p50_ms"],
+                               "served_p99_ms": v["served_bf16_batched"]["p99_ms"],
+                               "plain_fps": v["plain_fp32_one_at_a_time"]["fps"],
+                               "served_fps": v["served_bf16_batched"]["fps"]} for f, v in sweep.items()}}
 
 
 def run_precision(args, device):

@@ -220,6 +220,10 @@ def run_reference(args):
             secs.append(dt)
     total_px = 256 * max(1, args.cpu_tiles // 3) * args.steps
     value = total_px / sum(secs) / 1e6
+    # HBM-side stages against the measured copy rate (algorithmic bytes / time)
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    sb = stage_bytes(len(scene["opacity"]), fr["n_pairs"], npix, ((RES + 15) // 16) ** 2)
+    stage_fracs = {k: round(b / (stage_ms[k] / 1e3) / 1e9 / hbm_peak, 3) for k, b in sb.items() if k in stage_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -321,6 +325,10 @@ def run_ours(args):
     # the derived peak above
     meas_scalar, meas_paired = (float("nan"), float("nan")) if args.no_fp32_probe else _lib.measure_fp32_peak(local)
 
+    # HBM-side stages against the measured copy rate (algorithmic bytes / time)
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    sb = stage_bytes(len(scene["opacity"]), fr["n_pairs"], npix, ((RES + 15) // 16) ** 2)
+    stage_fracs = {k: round(b / (stage_ms[k] / 1e3) / 1e9 / hbm_peak, 3) for k, b in sb.items() if k in stage_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -334,6 +342,7 @@ def run_ours(args):
                              "scalar_fma_tflops": round(meas_scalar, 2), "paired_fma_tflops": round(meas_paired, 2),
                              "frac_of_measured_scalar": achieved / meas_scalar}},
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stage_hbm_frac": stage_fracs,
             "fragments_per_view": {k: int(v) for k, v in fr.items()},
             "gpu_launches": int(launches),
             "clocks": clocks}
@@ -716,6 +725,26 @@ def read_traffic(kernel: str):
     if not ent or ent.get("source_sha256") != kernel_source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
+
+
+# Algorithmic bytes of the HBM-side stages (per splat N, pair K, pixel P of
+# the view): what each stage must read and write once.
+#   preprocess: parameters 40 B in; record 80 + count 4 + depth key 8 + id 4 +
+#     tile rect 16 B out                                    -> 152 B / splat
+#   sort_splats: 4 passes x (key 8 + id 4 in, 12 out, 8 histogram read)
+#                                                           -> 128 B / splat
+#   scan_counts: gather 12 B + scan 8 B                     ->  20 B / splat
+#   emit_pairs: 8 B out per pair; order, offset, count, rect in (28 B / splat)
+#   sort_pairs: 2 passes x (4 histogram + 8 in + 8 out)     ->  40 B / pair
+#   tile_ranges: 4 B / pair in, 8 B / tile out
+#   shade_bwd: G-buffer 32 + coverage 4 + dL/drgba 16 in, 48 out -> 100 B / pixel
+#   preprocess_bwd: record gradients 112 + record 80 + parameters 40 in,
+#     gradients 40 out                                      -> 272 B / splat
+#   l1_loss: image 16 + target 16 in, gradient 16 out       ->  48 B / pixel
+def stage_bytes(N, K, P, tiles):
+    return {"preprocess": 152 * N, "sort_splats": 128 * N, "scan_counts": 20 * N,
+            "emit_pairs": 8 * K + 28 * N, "sort_pairs": 40 * K, "tile_ranges": 4 * K + 8 * tiles,
+            "shade_bwd": 100 * P, "preprocess_bwd": 272 * N, "l1_loss": 48 * P}
 
 
 def run_features(args, device):

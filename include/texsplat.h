@@ -39,7 +39,7 @@ typedef int ts_status;
 #define TS_ERR_OOM 2      /* device or host allocation failed */
 #define TS_ERR_CAPACITY 3 /* a fixed-capacity buffer would overflow */
 #define TS_ERR_CUDA 4     /* a CUDA runtime call failed (message has the CUDA error) */
-#define TS_ERR_TIMEOUT 5  /* a host-side wait ran out of time */
+#define TS_ERR_TIMEOUT 5  /* a wait ran out of time (host side, or a bounded wait inside a sort) */
 #define TS_ERR_STATE 6    /* call out of order (e.g. render before upload) */
 
 typedef enum ts_dtype { TS_F32 = 0, TS_BF16 = 1, TS_F16 = 2 } ts_dtype;
@@ -143,7 +143,13 @@ ts_status ts_render(ts_scene* scene, const ts_camera* cam, float* out_rgba, ts_s
 
 /* Batched form: n_views views, view i of scenes[i] with cams[i] into
  * out_rgba[i].  All views share one binning/sort/raster launch sequence.
- * saved may be NULL.  1 <= n_views <= 32. */
+ * saved may be NULL.  1 <= n_views <= 32.  Errors: TS_ERR_ARG (bad
+ * arguments, mixed dtypes / samplers / normal encodings in one batch),
+ * TS_ERR_STATE (missing or stale uploads, a sampler that cannot save state),
+ * TS_ERR_CAPACITY (more than 2^30 (tile, splat) pairs or a batch too large),
+ * TS_ERR_TIMEOUT (a bounded inter-block wait of a radix sort ran out: a
+ * device-side failure that is reported at this call's synchronisation, and
+ * the flag is cleared), TS_ERR_OOM, TS_ERR_CUDA. */
 ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_views,
                           float* const* out_rgba, ts_saved** saved, void* stream);
 
@@ -402,6 +408,15 @@ ts_status ts_activate(int64_t n, const float* log_scales, const float* logit_opa
 ts_status ts_activate_backward(int64_t n, const float* scales, const float* opacity, const float* g_scales,
                                const float* g_opacity, float* g_log_scales, float* g_logit_opacity, int accumulate,
                                void* stream);
+
+/* Self-test of the failure path of the radix sort's inter-block wait: runs
+ * one sort pass whose only block waits on a block that never runs, so its
+ * bounded wait (about a second) runs out; the pass sets the device flag the
+ * renders read, and this call reads and clears it.  Returns TS_ERR_TIMEOUT
+ * when the wait ran out and was reported (the expected result; the device
+ * stays usable), TS_ERR_STATE if it was not reported, TS_ERR_CUDA on a CUDA
+ * error.  Synchronises `stream`. */
+ts_status ts_selftest_sort_wait(int device, void* stream);
 
 /* ---- rendering without device allocation ------------------------------------ */
 

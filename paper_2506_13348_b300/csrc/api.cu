@@ -499,17 +499,26 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   struct HostTail {
     uint32_t tail[2];
     unsigned long long total;
+    int sort_err;
   };
+  int* d_sort_err = sort_error_flag(device);
   static thread_local HostTail* h_tail = nullptr;
   if (!h_tail) TS_CUDA_K(cudaHostAlloc((void**)&h_tail, sizeof(HostTail), cudaHostAllocPortable));
   h_tail->tail[0] = h_tail->tail[1] = 0;
   h_tail->total = 0;
+  h_tail->sort_err = 0;
+  if (d_sort_err) TS_CUDA_K(cudaMemcpyAsync(&h_tail->sort_err, d_sort_err, 4, cudaMemcpyDeviceToHost, st));
   if (n_items > 0) {
     TS_CUDA_K(cudaMemcpyAsync(&h_tail->tail[0], offs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
     TS_CUDA_K(cudaMemcpyAsync(&h_tail->tail[1], cs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
     if (d_total) TS_CUDA_K(cudaMemcpyAsync(&h_tail->total, d_total, 8, cudaMemcpyDeviceToHost, st));
   }
   TS_CUDA_K(cudaStreamSynchronize(st));
+  if (h_tail->sort_err) {  // a bounded wait in a sort ran out (this batch or an earlier call)
+    cudaMemsetAsync(d_sort_err, 0, sizeof(int), st);
+    cleanup_keep();
+    return fail(TS_ERR_TIMEOUT, "ts_render_views: a radix-sort look-back wait ran out");
+  }
   const long long K = (long long)h_tail->tail[0] + h_tail->tail[1];
   if (K > INT32_MAX / 2 || (d_total && h_tail->total > (unsigned long long)(INT32_MAX / 2))) {
     cleanup_keep();
@@ -1002,6 +1011,14 @@ ts_status ts_scene_info(const ts_scene* s, int64_t* n, int* T, int* dtype) {
   if (T) *T = s->T;
   if (dtype) *dtype = s->tex_dtype;
   return TS_OK;
+}
+
+ts_status ts_selftest_sort_wait(int device, void* stream) {
+  TS_CUDA(cudaSetDevice(device));
+  const int r = sort_wait_selftest((cudaStream_t)stream);
+  if (r < 0) return fail(TS_ERR_CUDA, "ts_selftest_sort_wait: CUDA error");
+  if (r == 0) return fail(TS_ERR_STATE, "ts_selftest_sort_wait: the wait did not report running out");
+  return fail(TS_ERR_TIMEOUT, "ts_selftest_sort_wait: the bounded look-back wait ran out and was reported");
 }
 
 ts_status ts_activate(int64_t n, const float* log_scales, const float* logit_opacity, float* scales, float* opacity,

@@ -29,6 +29,10 @@ void launch_preprocess_bwd(const ViewTable& vt, const double* g_items, const Gra
 size_t scan_temp_bytes(int n);
 void launch_exclusive_scan(const uint32_t* in, uint32_t* out, int n, void* temp, cudaStream_t st);
 size_t radix_temp_bytes(int n);
+// Per-device flag set by a sort pass whose bounded look-back wait ran out
+// (device int, 0 while no sort failed); the host reads and clears it.
+int* sort_error_flag(int device);
+int sort_wait_selftest(cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs over key bits [begin_bit, end_bit).
 // Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
 // (k0, v0), 1 if in (k1, v1).

@@ -11,6 +11,7 @@
 // (tile << 32 | depth bits) keys with ties by item id, at a fraction of the
 // traffic: 8-byte pairs over 2 passes instead of 12-byte pairs over 6.
 #include <algorithm>
+#include <mutex>
 
 #include "kernels.h"
 #include "prof.h"
@@ -301,10 +302,312 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter_local(const uin
 }
 static_assert(RS_THREADS == RADIX, "one thread per digit in the local scan");
 
+// ---- small sorts (n <= RS_SMALL_N): one kernel per pass ("onesweep") --------
+// A first kernel counts the digits of every pass over all keys (one read of
+// the keys); each pass then takes blocks of consecutive keys in the order the
+// blocks start (an atomic ticket), ranks the block's keys by digit, publishes
+// the block's digit counts and adds up those of all earlier blocks by a
+// decoupled look-back over their published values, and writes the block's
+// keys grouped by digit.  For the per-splat depth sort this replaces the
+// histogram, scan and scatter launches of every pass by one launch; the
+// large pair sort keeps the passes above, which measured faster there.
+// A block waits only on blocks that took a smaller ticket, hence started
+// earlier and are resident or done; every wait is bounded and a wait that
+// runs out sets a device error flag (read by the host at its next
+// synchronisation) and keeps its writes in bounds instead of hanging.
+constexpr int RS_MAX_PASSES = 6;
+constexpr uint32_t LB_AGG = 1u << 30, LB_PRE = 2u << 30, LB_VAL = (1u << 30) - 1u;
+constexpr int LB_SPIN_LIMIT = 1 << 20;
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+struct SortPlan {
+  int passes, step, begin, end;
+  int bits(int p) const { return min(step, end - (begin + p * step)); }
+  int shift(int p) const { return begin + p * step; }
+};
+static SortPlan sort_plan(int begin_bit, int end_bit) {
+  // as few passes as 8-bit digits need, with the bits spread evenly over them
+  // (e.g. 12 bits -> 2 x 6: fewer digits per pass means longer runs per block)
+  SortPlan pl;
+  pl.begin = begin_bit;
+  pl.end = end_bit;
+  pl.passes = (end_bit - begin_bit + 7) / 8;
+  pl.step = pl.passes ? (end_bit - begin_bit + pl.passes - 1) / pl.passes : 1;
+  return pl;
+}
+
+// digit counts of every pass: per block in shared memory, then one global
+// atomic per non-zero bin
+template <typename K, int R>
+__global__ void __launch_bounds__(RS_THREADS) k_os_hist(const K* __restrict__ keys, int n, int begin, int step,
+                                                         int end, int passes, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t hist[RS_MAX_PASSES][RADIX];
+  for (int i = threadIdx.x; i < RS_MAX_PASSES * RADIX; i += RS_THREADS) (&hist[0][0])[i] = 0;
+  __syncthreads();
+  constexpr int TILE = RS_THREADS * R;
+  const int base = blockIdx.x * TILE;
+  for (int i = threadIdx.x; i < TILE; i += RS_THREADS) {
+    const int idx = base + i;
+    if (idx >= n) break;
+    const K k = keys[idx];
+    for (int p = 0; p < passes; ++p) {
+      const int sh = begin + p * step, bits = min(step, end - sh);
+      atomicAdd(&hist[p][digit_of(k, sh, (1u << bits) - 1u)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p) {
+    const int nd = 1 << min(step, end - (begin + p * step));
+    for (int d = threadIdx.x; d < nd; d += RS_THREADS)
+      if (hist[p][d]) atomicAdd(ghist + p * RADIX + d, hist[p][d]);
+  }
+}
+
+template <typename K, int R>
+__global__ void __launch_bounds__(RS_THREADS) k_os_pass(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                        K* __restrict__ kout, uint32_t* __restrict__ vout, int n,
+                                                        int shift, int bits, const uint32_t* __restrict__ ghist,
+                                                        uint32_t* __restrict__ status, uint32_t* __restrict__ ticket,
+                                                        int* __restrict__ err) {
+  constexpr int TILE = RS_THREADS * R, WARP_N = 32 * R;
+  __shared__ uint32_t whist[RS_WARPS][RADIX];
+  __shared__ K s_key[TILE];
+  __shared__ uint32_t s_val[TILE];
+  __shared__ uint32_t s_dstart[RADIX];
+  __shared__ uint32_t s_goff[RADIX];
+  __shared__ uint32_t s_wsum[RS_WARPS];
+  __shared__ uint32_t s_gsum[RS_WARPS];
+  __shared__ int s_bid;
+  const uint32_t mask = (1u << bits) - 1u;
+  const int nd = 1 << bits;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_bid = (int)atomicAdd(ticket, 1u);
+  for (int i = lane; i < RADIX; i += 32) whist[warp][i] = 0;
+  __syncthreads();
+  const int bid = s_bid;
+  const int wbase = bid * TILE + warp * WARP_N;
+  K kr[R];
+  uint32_t vr[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    kr[r] = idx < n ? kin[idx] : K(0);
+    vr[r] = idx < n ? vin[idx] : 0u;
+  }
+  const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    const bool ok = idx < n;
+    const uint32_t d = digit_of(kr[r], shift, mask);
+    const unsigned peers = digit_peers(d, bits, ok);
+    if (ok && (peers & lt_mask) == 0) whist[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit (thread dt): the warps' runs inside the block's run, the
+  // block's count; the exclusive scans over digits of the block counts and
+  // of the global counts
+  const int dt = threadIdx.x;  // RS_THREADS == RADIX
+  uint32_t cnt = 0, gcnt = 0;
+  if (dt < nd) {
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const uint32_t c = whist[w][dt];
+      whist[w][dt] = cnt;
+      cnt += c;
+    }
+    gcnt = ghist[dt];
+    // publish this block's count at once: later blocks can go on
+    st_release(status + (size_t)bid * RADIX + dt, (bid == 0 ? LB_PRE : LB_AGG) | cnt);
+  }
+  uint32_t incl = cnt, gincl = gcnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o), u = __shfl_up_sync(0xffffffffu, gincl, o);
+    if (lane >= o) {
+      incl += t;
+      gincl += u;
+    }
+  }
+  if (lane == 31) {
+    s_wsum[warp] = incl;
+    s_gsum[warp] = gincl;
+  }
+  __syncthreads();
+  uint32_t before = 0, gbefore = 0;
+#pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) {
+    before += (w < warp) ? s_wsum[w] : 0u;
+    gbefore += (w < warp) ? s_gsum[w] : 0u;
+  }
+  s_dstart[dt] = before + incl - cnt;
+  // decoupled look-back, one thread per digit: the counts of digit dt in
+  // all earlier blocks, back to the nearest block with a published prefix
+  if (dt < nd) {
+    uint32_t excl = 0;
+    if (bid > 0) {
+      int j = bid - 1, spins = 0;
+      for (;;) {
+        const uint32_t v = ld_acquire(status + (size_t)j * RADIX + dt);
+        const uint32_t fl = v & ~LB_VAL;
+        if (fl == 0u) {
+          if (++spins > LB_SPIN_LIMIT) {
+            atomicExch(err, 1);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += v & LB_VAL;
+        if (fl == LB_PRE || j == 0) break;
+        --j;
+      }
+      st_release(status + (size_t)bid * RADIX + dt, LB_PRE | (excl + cnt));
+    }
+    s_goff[dt] = (gbefore + gincl - gcnt) + excl;  // global start of digit dt + earlier blocks
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int idx = wbase + r * 32 + lane;
+    const bool ok = idx < n;
+    const uint32_t d = digit_of(kr[r], shift, mask);
+    const unsigned peers = digit_peers(d, bits, ok);
+    if (ok) {
+      const uint32_t slot = s_dstart[d] + whist[warp][d] + __popc(peers & lt_mask);
+      s_key[slot] = kr[r];
+      s_val[slot] = vr[r];
+    }
+    __syncwarp();
+    if (ok && (peers & lt_mask) == 0) whist[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  const int nblk = min(TILE, n - bid * TILE);
+  for (int sl = threadIdx.x; sl < nblk; sl += RS_THREADS) {
+    const K key = s_key[sl];
+    const uint32_t dd = digit_of(key, shift, mask);
+    const uint32_t pos = s_goff[dd] + ((uint32_t)sl - s_dstart[dd]);
+    if (pos < (uint32_t)n) {  // always, unless a look-back ran out (then the flag is set)
+      kout[pos] = key;
+      vout[pos] = s_val[sl];
+    }
+  }
+}
+static_assert(RS_THREADS == RADIX, "one thread per digit in the local scans");
+
+// Temporaries: global digit counts, the look-back words (per pass, block and
+// digit) and the tickets; one memset clears them all.
+static size_t os_layout(int n, int nbits, size_t* status_off, size_t* ticket_off, int* nb_out) {
+  const int tile = RS_THREADS * 4;  // the small sorts (n <= RS_SMALL_N) only
+  const int nb = ceil_div(n > 0 ? n : 1, tile);
+  const int passes = std::max(1, (nbits + 7) / 8);
+  const size_t ghist = (size_t)RS_MAX_PASSES * RADIX * 4;
+  const size_t status = (size_t)passes * nb * RADIX * 4;
+  *status_off = ghist;
+  *ticket_off = ghist + status;
+  if (nb_out) *nb_out = nb;
+  return ghist + status + 256;
+}
+
+namespace {
+std::mutex g_err_mu;
+int* g_sort_err[64] = {nullptr};
+}  // namespace
+
+int* sort_error_flag(int device) {
+  if (device < 0 || device >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_sort_err[device]) {
+    int* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+    cudaMemset(p, 0, sizeof(int));
+    g_sort_err[device] = p;
+  }
+  return g_sort_err[device];
+}
+
+// Self-test of the bounded wait: one pass whose only block takes ticket 1,
+// so the block it waits on (ticket 0) never runs and its look-back runs out.
+// Returns 1 if the error flag came back set (and clears it), 0 if not, -1 on
+// a CUDA error.
+int sort_wait_selftest(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  int* err = sort_error_flag(dev);
+  if (!err) return -1;
+  const int n = 2 * RS_THREADS * 4;  // two blocks' worth of keys
+  size_t status_off, ticket_off;
+  int nb;
+  const size_t tb = os_layout(n, 6, &status_off, &ticket_off, &nb);
+  char* buf = nullptr;
+  const size_t kv = (size_t)n * 4;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&buf), tb + 4 * kv, st) != cudaSuccess) return -1;
+  uint32_t* keys = reinterpret_cast<uint32_t*>(buf + tb);
+  cudaMemsetAsync(buf, 0, tb + 4 * kv, st);
+  const uint32_t one = 1;
+  cudaMemcpyAsync(buf + ticket_off, &one, 4, cudaMemcpyHostToDevice, st);
+  k_os_hist<uint32_t, 4><<<nb, RS_THREADS, 0, st>>>(keys, n, 0, 6, 6, 1, reinterpret_cast<uint32_t*>(buf));
+  k_os_pass<uint32_t, 4><<<1, RS_THREADS, 0, st>>>(keys, keys + n, keys + 2 * n, keys + 3 * n, n, 0, 6,
+                                                   reinterpret_cast<uint32_t*>(buf),
+                                                   reinterpret_cast<uint32_t*>(buf + status_off),
+                                                   reinterpret_cast<uint32_t*>(buf + ticket_off), err);
+  note_launches(2);
+  int h = 0;
+  cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  cudaFreeAsync(buf, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  return h ? 1 : 0;
+}
+
+template <typename K, int R>
+static int radix_sort_os(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
+                         cudaStream_t st) {
+  if (n <= 1 || end_bit <= begin_bit) return 0;
+  const SortPlan pl = sort_plan(begin_bit, end_bit);
+  size_t status_off, ticket_off;
+  int nb;
+  const size_t bytes = os_layout(n, end_bit - begin_bit, &status_off, &ticket_off, &nb);
+  char* t = reinterpret_cast<char*>(temp);
+  uint32_t* ghist = reinterpret_cast<uint32_t*>(t);
+  uint32_t* status = reinterpret_cast<uint32_t*>(t + status_off);
+  uint32_t* tickets = reinterpret_cast<uint32_t*>(t + ticket_off);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int* err = sort_error_flag(dev);
+  cudaMemsetAsync(temp, 0, bytes, st);
+  k_os_hist<K, R><<<nb, RS_THREADS, 0, st>>>(k0, n, pl.begin, pl.step, pl.end, pl.passes, ghist);
+  note_launches(1);
+  int cur = 0;
+  K* kb[2] = {k0, k1};
+  uint32_t* vb[2] = {v0, v1};
+  for (int p = 0; p < pl.passes; ++p) {
+    k_os_pass<K, R><<<nb, RS_THREADS, 0, st>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n, pl.shift(p),
+                                               pl.bits(p), ghist + p * RADIX, status + (size_t)p * nb * RADIX,
+                                               tickets + p, err);
+    note_launches(1);
+    cur ^= 1;
+  }
+  return cur;
+}
+
 size_t radix_temp_bytes(int n) {
   const int nb = ceil_div(n > 0 ? n : 1, rs_tile(n));
   const size_t cnt = (size_t)RADIX * nb;
-  return 2 * cnt * sizeof(uint32_t) + 512 + scan_temp_bytes((int)cnt);
+  const size_t passes_path = 2 * cnt * sizeof(uint32_t) + 512 + scan_temp_bytes((int)cnt);
+  if (n > RS_SMALL_N) return passes_path;
+  size_t a, b;
+  return std::max(passes_path, os_layout(n, 8 * RS_MAX_PASSES, &a, &b, nullptr));
 }
 
 template <typename K, int R>
@@ -346,7 +649,7 @@ static int radix_sort_r(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int beg
 template <typename K>
 static int radix_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
                       cudaStream_t st) {
-  if (n <= RS_SMALL_N) return radix_sort_r<K, 4>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
+  if (n <= RS_SMALL_N) return radix_sort_os<K, 4>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
   return radix_sort_r<K, 16>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
 }
 

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
   __shared__ __align__(16) float s_gi[8][kRecGrads][36];  // record gradients, value-major, per warp
   // indirect light: per lane dL/dl (3) and the SH basis (9), value-major
   __shared__ __align__(16) float s_sh[IND ? 8 : 1][12][36];
-  __shared__ __align__(16) float4 s_rec[8][2][32][5];  // the records of this chunk and the next
+  __shared__ __align__(16) float4 s_rec[8][2][32][3];  // the records of this chunk and the next
   __shared__ uint32_t s_item[8][2][32];
   const int warp = threadIdx.x >> 5;
   const int tile = blockIdx.x;
@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
   const float by0 = (float)(py - (lane >> 3)) + 0.5f - V.cy, by1 = by0 + 3.f;
 
   // The list is taken 32 entries at a time, back to front: lane t's entry
-  // ch - t has its record copied into shared memory by cp.async one chunk
-  // ahead (the next chunk's copy runs while the warp works on this one; the
+  // ch - t has the first 48 bytes of its record (the rows the block test and
+  // the fragment need; the rest is read when an entry is processed) copied
+  // into shared memory by cp.async one chunk ahead (the next chunk's copy runs while the warp works on this one; the
   // item ids run one chunk further ahead in a register); the lane tests it
   // against the warp's block and only the surviving entries are processed,
   // in back-to-front order.
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
     if (c - lane >= lo) {
       const float4* rp = reinterpret_cast<const float4*>(rec + it);
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
+      for (int q = 0; q < 3; ++q) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(&s_rec[warp][b][lane][q]);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(rp + q) : "memory");
       }
@@ -135,8 +136,11 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
     Frag f;
     const bool ok = (j <= last) && eval_frag(r, xp, yp, f);
     if (__any_sync(FULL, ok)) {
-      r.r3 = s_rec[warp][buf][t][3];
-      r.r4 = s_rec[warp][buf][t][4];
+      {
+        const float4* rp = reinterpret_cast<const float4*>(rec + item);
+        r.r3 = __ldg(rp + 3);
+        r.r4 = __ldg(rp + 4);
+      }
       const long long splat = (long long)item - V.item_off;
       float t8[8], w4[4] = {0.f, 0.f, 0.f, 0.f};
       TexSample ts_;

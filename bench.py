@@ -220,10 +220,6 @@ def run_reference(args):
             secs.append(dt)
     total_px = 256 * max(1, args.cpu_tiles // 3) * args.steps
     value = total_px / sum(secs) / 1e6
-    # HBM-side stages against the measured copy rate (algorithmic bytes / time)
-    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
-    sb = stage_bytes(len(scene["opacity"]), fr["n_pairs"], npix, ((RES + 15) // 16) ** 2)
-    stage_fracs = {k: round(b / (stage_ms[k] / 1e3) / 1e9 / hbm_peak, 3) for k, b in sb.items() if k in stage_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

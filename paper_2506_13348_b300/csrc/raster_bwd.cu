@@ -10,9 +10,9 @@
 // stored); the transmittance in front of it is recovered by division
 // (alpha <= 0.99) and the colour behind it by the usual recurrence.
 // Reductions (all lanes of a warp work on the same splat at a time):
-//   * the 14 record gradients of the fragment are transposed through shared
-//     memory and lane L < 14 sums value L over the warp (independent loads,
-//     tree add), adding it once per warp;
+//   * the 14 record gradients of the fragment are summed over the warp by a
+//     halving reduce-scatter (16 shuffles), after which one lane per value
+//     adds it once per warp;
 //   * texel gradients are summed per bilinear cell over the warp (a
 //     reduce-scatter through shuffles) before one reduction per cell; lanes
 //     whose cell few others share add their own values directly.
@@ -31,7 +31,6 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
                                                                   double* __restrict__ g_items, GradTable g) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool IND = (FEAT & FEAT_IND) != 0, N2 = (FEAT & FEAT_N2) != 0;
-  __shared__ __align__(16) float s_gi[8][kRecGrads][36];  // record gradients, value-major, per warp
   // indirect light: per lane dL/dl (3) and the SH basis (9), value-major
   __shared__ __align__(16) float s_sh[IND ? 8 : 1][12][36];
   __shared__ __align__(16) float4 s_rec[8][2][32][3];  // the records of this chunk and the next
@@ -335,35 +334,43 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
         gi[12] = fmaf(nw0, gn1, -nw1 * gn0);
         gi[13] = gzw * f.rd;  // dL/dD
       }
-      // per-splat record gradients (14 values): transpose through shared
-      // memory (value-major, rows padded to 36 floats so the 16-byte reads
-      // below are conflict-free), then lane L < 14 adds up value L of all
-      // 32 lanes with a tree and issues one reduction per warp
+      // per-splat record gradients (14 values, padded to 16): a halving
+      // reduce-scatter over the warp (16 shuffles); afterwards lane pair
+      // (2i, 2i+1) holds the warp's sum of value i and lane 2i adds it
       if (!ok) {
 #pragma unroll
         for (int q = 0; q < kRecGrads; ++q) gi[q] = 0.f;
       }
+      {
+        const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
+        float v[16];
 #pragma unroll
-      for (int q = 0; q < kRecGrads; ++q) s_gi[warp][q][lane] = gi[q];
-      __syncwarp();
-      if (lane < kRecGrads) {
-        const float4* col = reinterpret_cast<const float4*>(s_gi[warp][lane]);
-        float4 a[8];
+        for (int q = 0; q < 16; ++q) v[q] = q < kRecGrads ? gi[q] : 0.f;
+        float a8[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) a[q] = col[q];
-        float2 lo[4], hi[4];
+        for (int q = 0; q < 8; ++q) {
+          const float snd = u16 ? v[q] : v[8 + q], kp = u16 ? v[8 + q] : v[q];
+          a8[q] = kp + __shfl_xor_sync(FULL, snd, 16);
+        }
+        float a4[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          lo[q] = add2(f2(a[q].x, a[q].y), f2(a[q + 4].x, a[q + 4].y));
-          hi[q] = add2(f2(a[q].z, a[q].w), f2(a[q + 4].z, a[q + 4].w));
+          const float snd = u8 ? a8[q] : a8[4 + q], kp = u8 ? a8[4 + q] : a8[q];
+          a4[q] = kp + __shfl_xor_sync(FULL, snd, 8);
         }
-        lo[0] = add2(lo[0], lo[2]); lo[1] = add2(lo[1], lo[3]);
-        hi[0] = add2(hi[0], hi[2]); hi[1] = add2(hi[1], hi[3]);
-        lo[0] = add2(add2(lo[0], lo[1]), add2(hi[0], hi[1]));
-        const float s = lo[0].x + lo[0].y;
-        if (s != 0.f) atomicAdd(g_items + (size_t)item * kRecGradStride + lane, (double)s);
+        float a2[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float snd = u4 ? a4[q] : a4[2 + q], kp = u4 ? a4[2 + q] : a4[q];
+          a2[q] = kp + __shfl_xor_sync(FULL, snd, 4);
+        }
+        const float snd = u2 ? a2[0] : a2[1], kp = u2 ? a2[1] : a2[0];
+        float sum = kp + __shfl_xor_sync(FULL, snd, 2);
+        sum += __shfl_xor_sync(FULL, sum, 1);
+        const int idx = (lane >> 1) & 15;
+        if (!(lane & 1) && idx < kRecGrads && sum != 0.f)
+          atomicAdd(g_items + (size_t)item * kRecGradStride + idx, (double)sum);
       }
-      __syncwarp();
       // SH coefficient gradients of the splat: dL/dc_jc = sum over lanes of
       // (dL/dl_c) Y_j -- lane v < 3K gathers its (c, j) products through
       // shared memory and adds them once per warp

@@ -519,6 +519,11 @@ static size_t os_layout(int n, int nbits, size_t* status_off, size_t* ticket_off
   return ghist + status + 256;
 }
 
+// The flag is a module variable (static device memory, one per device
+// context, zero at load): taking it allocates nothing, which the
+// no-allocation render relies on.
+__device__ int g_sort_err_flag;
+
 namespace {
 std::mutex g_err_mu;
 int* g_sort_err[64] = {nullptr};
@@ -528,10 +533,9 @@ int* sort_error_flag(int device) {
   if (device < 0 || device >= 64) return nullptr;
   std::lock_guard<std::mutex> lk(g_err_mu);
   if (!g_sort_err[device]) {
-    int* p = nullptr;
-    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
-    cudaMemset(p, 0, sizeof(int));
-    g_sort_err[device] = p;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sort_err_flag) != cudaSuccess) return nullptr;
+    g_sort_err[device] = static_cast<int*>(p);
   }
   return g_sort_err[device];
 }

@@ -462,7 +462,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   TS_CUDA_K(tmp.alloc((void**)&rects, ni * sizeof(int4)));
   if (saved_out) TS_CUDA_K(salloc((void**)&dbits, ni * 4));
   void* rtemp = nullptr;
-  size_t rt_bytes = std::max(radix_temp_bytes(n_items), scan_temp_bytes(n_items));
+  size_t rt_bytes = std::max(radix_temp_bytes(n_items, 8), scan_temp_bytes(n_items));
   TS_CUDA_K(tmp.alloc(&rtemp, rt_bytes));
 
   {
@@ -535,7 +535,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   TS_CUDA_K(salloc((void**)&pi1, nk * 4));
   TS_CUDA_K(salloc((void**)&ranges, (size_t)vt.n_tiles * sizeof(uint2)));
   void* rtemp2 = nullptr;
-  TS_CUDA_K(tmp.alloc(&rtemp2, radix_temp_bytes((int)K)));
+  TS_CUDA_K(tmp.alloc(&rtemp2, radix_temp_bytes((int)K, 4)));
   {
     ProfScope p(st, "emit_pairs");
     launch_emit_pairs(vt, order, offs, cs, rects, tk0, pi0, n_items, st);
@@ -875,7 +875,7 @@ ts_status ts_scene_build_atlas2d(ts_scene* s, ts_dtype store, int packing, void*
   void* mtemp = nullptr;
   if (r == TS_OK && s->n > 0 && packing == TS_PACK_MORTON) {
     const size_t nn = (size_t)s->n;
-    const size_t rt = radix_temp_bytes((int)s->n);
+    const size_t rt = radix_temp_bytes((int)s->n, 4);
     const size_t bytes = 256 + 5 * ((nn * 4 + 255) & ~size_t(255)) + rt;
     if (cudaMalloc(&mtemp, bytes) != cudaSuccess) {
       r = fail(TS_ERR_OOM, "ts_scene_build_atlas2d: scratch allocation failed");

@@ -28,7 +28,7 @@ void launch_preprocess_bwd(const ViewTable& vt, const double* g_items, const Gra
 // sort.cu
 size_t scan_temp_bytes(int n);
 void launch_exclusive_scan(const uint32_t* in, uint32_t* out, int n, void* temp, cudaStream_t st);
-size_t radix_temp_bytes(int n);
+size_t radix_temp_bytes(int n, int key_bytes);  // temporaries of a sort of n keys of key_bytes (4 or 8)
 // Per-device flag set by a sort pass whose bounded look-back wait ran out
 // (device int, 0 while no sort failed); the host reads and clears it.
 int* sort_error_flag(int device);

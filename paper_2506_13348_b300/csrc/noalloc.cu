@@ -157,7 +157,7 @@ extern "C" ts_status ts_render_noalloc(int64_t n, const float* means, const floa
   uint2* ranges = reinterpret_cast<uint2*>(at(OFF_RANGES));
   void* temp = at(OFF_TEMP);
 
-  if (radix_temp_bytes((int)n) > TEMP_BYTES) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: sort temporaries");
+  if (radix_temp_bytes((int)n, 8) > TEMP_BYTES) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: sort temporaries");
   if (n > 0) launch_pad4(means, 3, const_cast<float4*>(V.means), n, st);
   launch_preprocess(vt, rec, counts, dk0, ids0, rects, st);
   const int which = radix_sort_u64(dk0, ids0, dk1, ids1, (int)n, 0, 32, temp, st);
@@ -174,7 +174,7 @@ extern "C" ts_status ts_render_noalloc(int64_t n, const float* means, const floa
   }
   const long long K = (long long)tail[0] + tail[1];
   if (K > NA_MAX_PAIRS) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: more than 1048576 (tile, splat) pairs");
-  if (radix_temp_bytes((int)K) > TEMP_BYTES) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: sort temporaries");
+  if (radix_temp_bytes((int)K, 4) > TEMP_BYTES) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: sort temporaries");
   launch_emit_pairs(vt, order, offs, cs, rects, tk0, pi0, (int)n, st);
   int tb = 1;
   while ((1ll << tb) < vt.n_tiles) ++tb;

@@ -662,49 +662,54 @@ __global__ void __launch_bounds__(256) k_emit_pairs(ViewTable vt, const uint32_t
                                                      const uint32_t* __restrict__ counts_sorted,
                                                      const int4* __restrict__ rects, uint32_t* __restrict__ tile_keys,
                                                      uint32_t* __restrict__ pair_items, int n) {
+  constexpr unsigned FULL = 0xffffffffu;
   const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int first = warp_global * 32;
   if (first >= n) return;
+  // lane l holds splat first + l (depth order); its pairs follow those of the
+  // lanes before it, so the warp writes one contiguous run of pairs
   const int my = first + lane;
-  uint32_t my_item = 0, my_cnt = 0, my_off = 0;
-  int4 my_rc = make_int4(0, 0, 0, 0);
+  uint32_t my_cnt = 0, my_item = 0, my_t0 = 0, my_w = 1, my_base = 0;
   if (my < n) {
     my_cnt = counts_sorted[my];
     if (my_cnt) {
       my_item = order[my];
-      my_off = offsets[my];
-      my_rc = rects[my_item];  // loaded up front: the loop below has no dependent global loads
+      const int4 rc = rects[my_item];
+      const ViewDesc& V = vt.v[find_view_item(vt, (int)my_item)];
+      my_t0 = (uint32_t)(V.tile_off + rc.z * V.tiles_x + rc.x);
+      my_w = (uint32_t)(rc.y - rc.x + 1);
+      my_base = (uint32_t)V.tiles_x;
     }
   }
-  unsigned todo = __ballot_sync(0xffffffffu, my_cnt != 0);
-  while (todo) {
-    const int src = __ffs(todo) - 1;
-    todo &= todo - 1;
-    const uint32_t item = __shfl_sync(0xffffffffu, my_item, src);
-    const uint32_t cnt = __shfl_sync(0xffffffffu, my_cnt, src);
-    const uint32_t off = __shfl_sync(0xffffffffu, my_off, src);
-    const int v = find_view_item(vt, (int)item);
-    const ViewDesc& V = vt.v[v];
-    int4 rc;
-    rc.x = __shfl_sync(0xffffffffu, my_rc.x, src);
-    rc.y = __shfl_sync(0xffffffffu, my_rc.y, src);
-    rc.z = __shfl_sync(0xffffffffu, my_rc.z, src);
-    const int w = rc.y - rc.x + 1;
-    // lane's tile (row, column) in the rect, advanced by 32 entries per step
-    // without a division per entry
-    int col = lane % w, row = lane / w;
-    const int dq = 32 / w, dr = 32 % w;
-    const uint32_t t0 = (uint32_t)(V.tile_off + rc.z * V.tiles_x + rc.x);
-    for (uint32_t j = lane; j < cnt; j += 32) {
-      tile_keys[off + j] = t0 + (uint32_t)(row * V.tiles_x + col);
-      pair_items[off + j] = item;
-      col += dr;
-      row += dq;
-      if (col >= w) {
-        col -= w;
-        ++row;
-      }
+  const uint32_t off0 = __shfl_sync(FULL, my < n ? offsets[my] : 0u, 0);
+  // inclusive prefix of the counts over the warp
+  uint32_t incl = my_cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t total = __shfl_sync(FULL, incl, 31);
+  // the warp writes its pairs 32 at a time: pair p's splat is the first lane
+  // whose inclusive prefix exceeds p (binary search over the prefixes; for
+  // p >= total the search stays in range and nothing is written)
+  for (uint32_t base = 0; base < total; base += 32) {  // warp-uniform
+    const uint32_t p = base + lane;
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint32_t v = __shfl_sync(FULL, incl, lo + step - 1);
+      if (v <= p) lo += step;
+    }
+    const int s = lo;  // the number of lanes whose prefix is <= p
+    const uint32_t start = __shfl_sync(FULL, incl - my_cnt, s);
+    const uint32_t w = __shfl_sync(FULL, my_w, s), t0 = __shfl_sync(FULL, my_t0, s);
+    const uint32_t tx = __shfl_sync(FULL, my_base, s), item = __shfl_sync(FULL, my_item, s);
+    if (p < total) {
+      const uint32_t k = p - start, row = k / w, col = k - row * w;
+      tile_keys[off0 + p] = t0 + row * tx + col;
+      pair_items[off0 + p] = item;
     }
   }
 }

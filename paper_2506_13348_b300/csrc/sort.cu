@@ -102,9 +102,11 @@ void launch_exclusive_scan(const uint32_t* in, uint32_t* out, int n, void* temp,
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort, digits of at most 8 bits.
 // A block owns 256 * R consecutive keys; warp w of the block owns the
-// sub-range [w * 32 R, (w+1) * 32 R), processed in R rounds of 32.  Small
-// sorts (the per-splat depth sort) take R = 4 so that enough blocks exist
-// to fill the GPU; the pair sort takes R = 16.
+// sub-range [w * 32 R, (w+1) * 32 R), processed in R rounds of 32.  Two
+// forms: the large 32-bit pair sort runs separate histogram, scan and
+// scatter launches per pass with R = 16; sorts of up to 2^18 keys and every
+// 64-bit (depth) sort run one kernel per pass (below) with R = 4 (small) or
+// R = 8 (large 64-bit keys), so that enough blocks exist to fill the GPU.
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RADIX = 256;
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter_local(const uin
 }
 static_assert(RS_THREADS == RADIX, "one thread per digit in the local scan");
 
-// ---- small sorts (n <= RS_SMALL_N): one kernel per pass ("onesweep") --------
+// ---- one kernel per pass ("onesweep"): the small and the 64-bit sorts --------
 // A first kernel counts the digits of every pass over all keys (one read of
 // the keys); each pass then takes blocks of consecutive keys in the order the
 // blocks start (an atomic ticket), ranks the block's keys by digit, publishes
@@ -256,7 +258,8 @@ static_assert(RS_THREADS == RADIX, "one thread per digit in the local scan");
 // decoupled look-back over their published values, and writes the block's
 // keys grouped by digit.  For the per-splat depth sort this replaces the
 // histogram, scan and scatter launches of every pass by one launch; the
-// large pair sort keeps the passes above, which measured faster there.
+// large 32-bit pair sort keeps the separate passes, which measured faster
+// there.
 // A block waits only on blocks that took a smaller ticket, hence started
 // earlier and are resident or done; every wait is bounded and a wait that
 // runs out sets a device error flag (read by the host at its next

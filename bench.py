@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--sampling-views", type=int, default=40)
     ap.add_argument("--no-image-loss", action="store_true", help="skip the L1 + D-SSIM timing after the step")
     ap.add_argument("--no-fp32-probe", action="store_true", help="skip the FP32 rate probe after the step")
+    ap.add_argument("--packing-probe", action="store_true",
+                    help="one hardware-atlas render per chart packing (splat id, Morton), for profiling")
     ap.add_argument("--hbm-kernels-only", action="store_true",
                     help="time the atlas pack and Adam alone on 1 GiB of float32 (for profiling)")
     ap.add_argument("--no-features", action="store_true",
@@ -858,6 +860,34 @@ def run_hbm_kernels(args, device):
     return out
 
 
+def run_packing_probe(args, device):
+    """One 800x800 forward of the 200k-splat scene (8x8 FP32 texels) through
+    the hardware-texture atlas for each chart packing: splat-id order, then the
+    Morton order of the splat centres (two k_raster_fwd launches for a
+    profiler to compare texture-cache hit rates)."""
+    import torch
+
+    import paper_2506_13348_b300 as P
+    import scenegen as sg
+
+    dev = torch.device("cuda", device)
+    scene, env, cams = build_workload()
+    sc = P.Scene.from_arrays(scene, env, device=device)
+    img = torch.empty(RES, RES, 4, device=dev)
+    out = {}
+    for packing in ("splat_id", "morton"):
+        sc.build_atlas2d("f32", packing=packing)
+        sc.set_sampler("hw_atlas")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.render(sc, cams[5], out=img)
+        e1.record()
+        torch.cuda.synchronize()
+        out[packing] = {"ms": e0.elapsed_time(e1)}
+    sc.close()
+    return out
+
+
 def run_sampling(args, device):
     """The shape of the paper's Table 3: forward-render throughput of textured
     splats relative to the same splats without textures, for T = 2, 4, 8, 16,
@@ -962,7 +992,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if (args.serve_only or args.large_only or args.precision_only or args.sampling_only or args.features_only
-            or args.hbm_kernels_only):
+            or args.hbm_kernels_only or args.packing_probe):
         import torch
         torch.cuda.set_device(dist_env()[2])
         res = {}
@@ -978,6 +1008,8 @@ def main():
             res["features"] = run_features(args, dist_env()[2])
         if args.hbm_kernels_only:
             res["hbm_kernels"] = run_hbm_kernels(args, dist_env()[2])
+        if args.packing_probe:
+            res["packing_probe"] = run_packing_probe(args, dist_env()[2])
         print(json.dumps(res))
         return 0
     return run_ours(args)

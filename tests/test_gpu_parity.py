@@ -196,3 +196,16 @@ def test_pair_count_past_32_bits_is_a_capacity_error(P):
     out, _ = P.render(sc, small)
     torch.cuda.synchronize()
     assert torch.isfinite(out).all() and out[..., 3].min().item() > 0.99
+
+
+@pytest.mark.parametrize("n", [1, 1023, 1025, (1 << 18) + 1])
+def test_depth_sort_block_and_path_boundaries(P, n):
+    """Key lists bit-exact at splat counts around the sort's block size
+    (1024 keys) and just past the small-sort limit (2^18 keys: the 64-bit
+    depth sort switches to 2048-key blocks), with ragged last blocks."""
+    scene = sg.make_scene(0, n=n, T=2, seed=n % 97)
+    env = sg.make_env(0, cube_res=8, irr_res=4, lut_res=16)
+    cam = sg.look_at_camera((3.5, 0.4, 0.3), 96, 80)
+    kl = K.build_keys(scene, cam)
+    sc, out, saved = gpu_render(P, scene, env, cam)
+    compare_lists(saved, kl, n)

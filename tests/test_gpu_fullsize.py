@@ -34,11 +34,11 @@ def sample_pixels(rng, W, H, n):
     return rng.integers(0, W, size=n), rng.integers(0, H, size=n)
 
 
-def check_sampled(out, ref, px, py, tol=IMG_TOL):
+def check_sampled(out, ref, px, py, tol=IMG_TOL, max_amb=0.01):
     g = out.cpu().numpy()[py, px].astype(np.float64)
     r = ref["rgba"].detach().numpy()
     amb = ref["ambiguous"].numpy()
-    assert amb.mean() <= 0.01, amb.mean()
+    assert amb.mean() <= max_amb, amb.mean()
     err = np.abs(g - r).max(-1)
     bad = (err > tol) & ~amb
     assert not bad.any(), (int(bad.sum()), float(err[~amb].max()))
@@ -187,3 +187,45 @@ def test_cfg1_full_size_with_indirect_light_and_two_component_normals(P):
     kl = K.build_keys(scene, cam)
     ref = R.render_pixels(scene, cam, env, px, py, keylist=kl, vis=vis)
     check_sampled(out, ref, px, py)
+
+
+def test_cfg4_scale_batch_keys_and_sampled_pixels(P):
+    """3M splats in the 10^3 box (cfg4 geometry, 2x2 BF16 texels to keep the
+    oracle's copy small), a batch of 2 views of 1600x1064 from the radius-12
+    camera set: the whole key lists bit-exact and sampled pixels within 1e-4
+    of the oracle fed the same rounded texels.  Exercises the large depth
+    sort (2048-key blocks), past-2^31-bound pair counting and batching."""
+    geo = sg.make_scene(4, with_texels=False)
+    n = len(geo["opacity"])
+    tex = sg.scenes.texels_torch(n, 2, seed=4, device="cpu")
+    tex_r = tex.to(torch.bfloat16).float().numpy()
+    env = sg.make_env(4, cube_res=32, levels=1, irr_res=8, lut_res=128)
+    cams = sg.fibonacci_cameras(40, 12.0, 1600, 1064)[3:5]
+    sc = P.Scene(0)
+    sc.upload_gaussians(geo["means"], geo["quats"], geo["scales"], geo["opacity"])
+    sc.upload_atlas(tex, "bf16")
+    sc.upload_envmap(env)
+    outs, saved = P.render_views([sc, sc], cams, save=True)
+    torch.cuda.synchronize()
+    scene_r = dict(geo, texels=tex_r, T=2)
+    rng = np.random.default_rng(8)
+    ids, rng_t, _ = saved.lists(2 * n)
+    k_off = 0
+    t_off = 0
+    for v, cam in enumerate(cams):
+        kl = K.build_keys(scene_r, cam)
+        kv = kl["ids"].size
+        assert kv > 1_000_000
+        # view v's lists follow view v-1's: items are v * n + splat, positions shifted
+        np.testing.assert_array_equal(ids[k_off:k_off + kv], kl["ids"].astype(np.int64) + v * n)
+        ref_rng = kl["tile_ranges"]
+        nt = ref_rng.shape[0]
+        ne = ref_rng[:, 1] > ref_rng[:, 0]
+        np.testing.assert_array_equal(rng_t[t_off:t_off + nt][ne], ref_rng[ne] + k_off)
+        k_off += kv
+        t_off += nt
+        px, py = sample_pixels(rng, 1600, 1064, 128)
+        ref = R.render_pixels(scene_r, cam, env, px, py, keylist=kl)
+        # deep pixels of this dense scene sit near a threshold more often
+        check_sampled(outs[v], ref, px, py, max_amb=0.04)
+    saved.release()

@@ -425,18 +425,31 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
         }
         const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2, u1 = lane & 1;
         unsigned pend = __ballot_sync(FULL, ok && !direct);
+        // lane bit 4 <-> corner bit 1 (row jb), bit 3 <-> corner bit 0
+        // (column ib), bits 2..0 <-> channel; each step keeps the half
+        // selected by the lane's bit and adds the partner's copy of it.  The
+        // corner weights are taken in lane order, wp[j] = w4[c ^ j] with c
+        // the corner the lane keeps, so that the two corner steps need no
+        // per-value selects
+        float wp[4];
+        {
+          const float r0 = u8 ? w4[1] : w4[0], r1 = u8 ? w4[0] : w4[1];
+          const float r2 = u8 ? w4[3] : w4[2], r3 = u8 ? w4[2] : w4[3];
+          wp[0] = u16 ? r2 : r0;
+          wp[1] = u16 ? r3 : r1;
+          wp[2] = u16 ? r0 : r2;
+          wp[3] = u16 ? r1 : r3;
+        }
         while (pend) {  // warp-uniform
           const unsigned lk = __shfl_sync(FULL, key, __ffs(pend) - 1);
           const bool mem = ((pend >> lane) & 1u) && key == lk;
           pend &= ~__ballot_sync(FULL, mem);
-          const float m0 = mem ? w4[0] : 0.f, m1 = mem ? w4[1] : 0.f;
-          const float m2 = mem ? w4[2] : 0.f, m3 = mem ? w4[3] : 0.f;
-          // lane bit 4 <-> corner bit 1 (row jb), bit 3 <-> corner bit 0
-          // (column ib), bits 2..0 <-> channel; each step keeps the half
-          // selected by the lane's bit and adds the partner's copy of it
-          const float wk0 = u16 ? m2 : m0, wk1 = u16 ? m3 : m1, ws0 = u16 ? m0 : m2, ws1 = u16 ? m1 : m3;
+          const float wk0 = mem ? wp[0] : 0.f, wk1 = mem ? wp[1] : 0.f;
+          const float ws0 = mem ? wp[2] : 0.f, ws1 = mem ? wp[3] : 0.f;
           const float2 WK0 = f2(wk0, wk0), WK1 = f2(wk1, wk1), WS0 = f2(ws0, ws0), WS1 = f2(ws1, ws1);
-          float2 a[8];  // channel pairs: a[q] = channels (2q, 2q+1) of column 0, a[4+q] of column 1
+          // channel pairs: a[q] = channels (2q, 2q+1) of the lane's own
+          // column, a[4+q] of the other column (the partner's own)
+          float2 a[8];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const float2 t = f2(t8[2 * q], t8[2 * q + 1]);
@@ -445,10 +458,8 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
             a[4 + q] = fma2(WK1, t, f2(__shfl_xor_sync(FULL, s1.x, 16), __shfl_xor_sync(FULL, s1.y, 16)));
           }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float2 snd = u8 ? a[q] : a[4 + q], kp = u8 ? a[4 + q] : a[q];
-            a[q] = add2(kp, f2(__shfl_xor_sync(FULL, snd.x, 8), __shfl_xor_sync(FULL, snd.y, 8)));
-          }
+          for (int q = 0; q < 4; ++q)
+            a[q] = add2(a[q], f2(__shfl_xor_sync(FULL, a[4 + q].x, 8), __shfl_xor_sync(FULL, a[4 + q].y, 8)));
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const float2 snd = u4 ? a[q] : a[2 + q], kp = u4 ? a[2 + q] : a[q];

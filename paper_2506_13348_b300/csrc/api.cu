@@ -534,8 +534,10 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   TS_CUDA_K(salloc((void**)&tk1, nk * 4));
   TS_CUDA_K(salloc((void**)&pi1, nk * 4));
   TS_CUDA_K(salloc((void**)&ranges, (size_t)vt.n_tiles * sizeof(uint2)));
+  uint32_t* obuf = nullptr;  // tile launch order: keys and ids, twice
+  TS_CUDA_K(salloc((void**)&obuf, (size_t)vt.n_tiles * 4 * sizeof(uint32_t)));
   void* rtemp2 = nullptr;
-  TS_CUDA_K(tmp.alloc(&rtemp2, radix_temp_bytes((int)K, 4)));
+  TS_CUDA_K(tmp.alloc(&rtemp2, std::max(radix_temp_bytes((int)K, 4), radix_temp_bytes(vt.n_tiles, 4))));
   {
     ProfScope p(st, "emit_pairs");
     launch_emit_pairs(vt, order, offs, cs, rects, tk0, pi0, n_items, st);
@@ -551,6 +553,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     ProfScope p(st, "tile_ranges");
     TS_CUDA_K(cudaMemsetAsync(ranges, 0, (size_t)vt.n_tiles * sizeof(uint2), st));
     launch_tile_ranges(tkeys, (int)K, ranges, st);
+    vt.tile_order = launch_tile_order(ranges, vt.n_tiles, obuf, rtemp2, st);
   }
   TS_CHECK_LAUNCH();
 

@@ -47,6 +47,9 @@ void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_
                        const uint32_t* counts_sorted, const int4* rects, uint32_t* tile_keys,
                        uint32_t* pair_items, int n, cudaStream_t st);
 void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStream_t st);
+// Tile launch order, longest list first: buf holds 4 * n words (keys and ids,
+// twice); returns the n sorted tile ids (inside buf).  temp: radix_temp_bytes(n, 4).
+const uint32_t* launch_tile_order(const uint2* ranges, int n, uint32_t* buf, void* temp, cudaStream_t st);
 void launch_depth_bits(const uint64_t* depth_keys_unsorted, uint32_t* out, int n, cudaStream_t st);
 
 // raster_fwd.cu / raster_bwd.cu

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
   __shared__ __align__(16) float4 s_rec[8][2][32][3];  // the records of this chunk and the next
   __shared__ uint32_t s_item[8][2][32];
   const int warp = threadIdx.x >> 5;
-  const int tile = blockIdx.x;
+  const int tile = vt.tile_order ? (int)vt.tile_order[blockIdx.x] : (int)blockIdx.x;
+  if ((unsigned)tile >= (unsigned)vt.n_tiles) return;  // an order from a failed sort (flag set)
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
   int px, py;

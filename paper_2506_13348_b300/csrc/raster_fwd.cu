@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
                                                      unsigned long long* __restrict__ stats) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool IND = (FEAT & FEAT_IND) != 0, N2 = (FEAT & FEAT_N2) != 0;
-  const int tile = blockIdx.x;
+  const int tile = vt.tile_order ? (int)vt.tile_order[blockIdx.x] : (int)blockIdx.x;
+  if ((unsigned)tile >= (unsigned)vt.n_tiles) return;  // an order from a failed sort (flag set)
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
   int px, py;

@@ -761,6 +761,35 @@ void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStr
   }
 }
 
+// Launch order of the rasterisers' tiles: longest list first.  The key is an
+// 8-bit code of the list length (exact below 8, then exponent and three
+// mantissa bits, so within 12.5 %), inverted for a descending sort; the
+// stable sort keeps tile order among equal codes.  Issued in this order the
+// tiles with the most entries start in the grid's first wave instead of
+// stretching its last one.
+__global__ void k_tile_order_keys(const uint2* __restrict__ ranges, int n, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ ids) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint2 r = ranges[i];
+  const uint32_t len = r.y - r.x;
+  uint32_t code = len;
+  if (len >= 8u) {
+    const int e = 31 - __clz((int)len);  // 3..31
+    code = ((uint32_t)(e - 2) << 3) | ((len >> (e - 3)) & 7u);  // 8..239
+  }
+  keys[i] = 255u - code;
+  ids[i] = (uint32_t)i;
+}
+
+const uint32_t* launch_tile_order(const uint2* ranges, int n, uint32_t* buf, void* temp, cudaStream_t st) {
+  if (n <= 0) return buf + n;
+  k_tile_order_keys<<<ceil_div(n, 256), 256, 0, st>>>(ranges, n, buf, buf + n);
+  note_launches(1);
+  const int w = radix_sort_u32(buf, buf + n, buf + 2 * n, buf + 3 * n, n, 0, 8, temp, st);
+  return w ? buf + 3 * n : buf + n;
+}
+
 __global__ void k_depth_bits(const uint64_t* __restrict__ dk, uint32_t* __restrict__ out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {

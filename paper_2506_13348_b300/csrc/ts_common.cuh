@@ -112,6 +112,9 @@ struct ViewTable {
   int n_views;
   int n_tiles;   // total tiles
   int n_items;   // total items
+  // the rasterisers' tiles in launch order (CTA b takes tile tile_order[b]),
+  // or NULL for tile order
+  const uint32_t* tile_order;
   ViewDesc v[MAX_VIEWS];
 };
 

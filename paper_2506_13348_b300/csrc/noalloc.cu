@@ -184,6 +184,10 @@ extern "C" ts_status ts_render_noalloc(int64_t n, const float* means, const floa
   e = cudaMemsetAsync(ranges, 0, (size_t)vt.n_tiles * sizeof(uint2), st);
   if (e != cudaSuccess) return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: ") + cudaGetErrorString(e));
   launch_tile_ranges(tkeys, (int)K, ranges, st);
+  // tile launch order in the pair-key buffer the sort left free (4 x tiles <= pairs capacity)
+  static_assert(4 * NA_MAX_TILES <= NA_MAX_PAIRS, "tile order buffer");
+  if (radix_temp_bytes(vt.n_tiles, 4) > TEMP_BYTES) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: sort temporaries");
+  vt.tile_order = launch_tile_order(ranges, vt.n_tiles, w2 ? tk0 : tk1, temp, st);
   launch_raster_fwd(vt, rec, pitems, ranges, DT_F32, false, nullptr, SMP_SOFTWARE, 0, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: launch: ") + cudaGetErrorString(e));

@@ -245,12 +245,26 @@ __device__ __forceinline__ float3 sh_grad_dir(float3 w, int K, const float s[9])
   return g;
 }
 
-__device__ __forceinline__ void pixel_of(int tile_local, int tiles_x, int& px, int& py) {
+// Rasteriser CTAs: a 16 x 16 tile is 8 pixel blocks of 8 x 4 (one warp
+// each), split over kCtasPerTile CTAs of kRasterWarps warps
+constexpr int kRasterWarps = 4;
+constexpr int kCtasPerTile = 8 / kRasterWarps;
+
+// the tile of this CTA (in launch order) and the 8 x 4 block of this warp
+__device__ __forceinline__ int raster_tile(const ViewTable& vt) {
+  const int b = (int)blockIdx.x / kCtasPerTile;
+  return vt.tile_order ? (int)vt.tile_order[b] : b;
+}
+__device__ __forceinline__ int raster_block() {
+  return ((int)blockIdx.x % kCtasPerTile) * kRasterWarps + (int)(threadIdx.x >> 5);
+}
+
+__device__ __forceinline__ void pixel_of(int tile_local, int tiles_x, int wblk, int& px, int& py) {
   int tx = tile_local % tiles_x, ty = tile_local / tiles_x;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int lane = threadIdx.x & 31;
   // 8 x 4 pixel block per warp, 2 x 4 blocks per 16 x 16 tile
-  px = tx * TILE + (warp & 1) * 8 + (lane & 7);
-  py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
+  px = tx * TILE + (wblk & 1) * 8 + (lane & 7);
+  py = ty * TILE + (wblk >> 1) * 4 + (lane >> 3);
 }
 
 }  // namespace ts

@@ -1,4 +1,5 @@
-// Backward rasteriser: one CTA per 16x16 tile, one thread per pixel.
+// Backward rasteriser: one thread per pixel, one warp per 8x4 pixel block,
+// two CTAs of 4 warps per 16x16 tile (as the forward).
 //
 // Input: dL/dX (the 8 G-buffer channels) and dL/dA per pixel, written by the
 // shading adjoint (Eq. 10-12, k_shade_bwd), plus the forward's saved
@@ -24,7 +25,7 @@
 namespace ts {
 
 template <int DT, int FEAT>
-__global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
+__global__ void __launch_bounds__(32 * kRasterWarps, ((FEAT & FEAT_IND) ? 2 : 3) * kCtasPerTile) k_raster_bwd(ViewTable vt, const Record* __restrict__ rec,
                                                                   const uint32_t* __restrict__ pair_items,
                                                                   const uint2* __restrict__ ranges,
                                                                   const float4* __restrict__ gxa,
@@ -32,16 +33,16 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool IND = (FEAT & FEAT_IND) != 0, N2 = (FEAT & FEAT_N2) != 0;
   // indirect light: per lane dL/dl (3) and the SH basis (9), value-major
-  __shared__ __align__(16) float s_sh[IND ? 8 : 1][12][36];
-  __shared__ __align__(16) float4 s_rec[8][2][32][3];  // the records of this chunk and the next
-  __shared__ uint32_t s_item[8][2][32];
+  __shared__ __align__(16) float s_sh[IND ? kRasterWarps : 1][12][36];
+  __shared__ __align__(16) float4 s_rec[kRasterWarps][2][32][3];  // the records of this chunk and the next
+  __shared__ uint32_t s_item[kRasterWarps][2][32];
   const int warp = threadIdx.x >> 5;
-  const int tile = vt.tile_order ? (int)vt.tile_order[blockIdx.x] : (int)blockIdx.x;
+  const int tile = raster_tile(vt);
   if ((unsigned)tile >= (unsigned)vt.n_tiles) return;  // an order from a failed sort (flag set)
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
   int px, py;
-  pixel_of(tile - V.tile_off, V.tiles_x, px, py);
+  pixel_of(tile - V.tile_off, V.tiles_x, raster_block(), px, py);
   const bool inside = px < V.W && py < V.H;
   const float xp = (float)px + 0.5f - V.cx;
   const float yp = (float)py + 0.5f - V.cy;
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(256, (FEAT & FEAT_IND) ? 2 : 3) k_raster_bwd(V
 void launch_raster_bwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
                        const uint2* ranges, int tex_dtype, const float4* gxa, double* g_items,
                        const GradTable& g, int feat, cudaStream_t st) {
-  dim3 grid(vt.n_tiles), block(256);
+  dim3 grid(vt.n_tiles * kCtasPerTile), block(32 * kRasterWarps);
 #define TS_LAUNCH_B(DTV)                                                                                      \
   switch (feat & (FEAT_IND | FEAT_N2)) {                                                                      \
     case 0: k_raster_bwd<DTV, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, gxa, g_items, g); break; \

@@ -1,5 +1,7 @@
-// Forward rasteriser: one CTA per 16x16 tile, one thread per pixel, one
-// warp per 8x4 pixel block.
+// Forward rasteriser: one thread per pixel, one warp per 8x4 pixel block;
+// a 16x16 tile's 8 blocks are split over two CTAs of 4 warps (the finer
+// CTAs refill an SM sooner when their warps finish early), the tiles taken
+// longest list first.
 //
 // Each warp walks the tile's depth-sorted splat list front to back on its
 // own (no block-wide barrier), 32 entries at a time:
@@ -28,18 +30,18 @@
 namespace ts {
 
 template <int DT, bool SAVE, bool STATS, int SMP, int FEAT = 0>
-__global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
+__global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
                                                      const uint32_t* __restrict__ pair_items,
                                                      const uint2* __restrict__ ranges,
                                                      unsigned long long* __restrict__ stats) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool IND = (FEAT & FEAT_IND) != 0, N2 = (FEAT & FEAT_N2) != 0;
-  const int tile = vt.tile_order ? (int)vt.tile_order[blockIdx.x] : (int)blockIdx.x;
+  const int tile = raster_tile(vt);
   if ((unsigned)tile >= (unsigned)vt.n_tiles) return;  // an order from a failed sort (flag set)
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
   int px, py;
-  pixel_of(tile - V.tile_off, V.tiles_x, px, py);
+  pixel_of(tile - V.tile_off, V.tiles_x, raster_block(), px, py);
   const bool inside = px < V.W && py < V.H;
   const float xp = (float)px + 0.5f - V.cx;
   const float yp = (float)py + 0.5f - V.cy;
@@ -76,8 +78,8 @@ __global__ void __launch_bounds__(256, 3) k_raster_fwd(ViewTable vt, const Recor
   // the warp works on the current one; the item ids run one chunk further
   // ahead in a register.
   {
-    __shared__ __align__(16) float4 s_r[8][2][32][3];
-    __shared__ uint32_t s_it[8][2][32];
+    __shared__ __align__(16) float4 s_r[kRasterWarps][2][32][3];
+    __shared__ uint32_t s_it[kRasterWarps][2][32];
     const int warp = threadIdx.x >> 5;
     auto issue = [&](int b, unsigned c, uint32_t it) {
       if (c + lane < range.y) {
@@ -237,7 +239,7 @@ void launch_feat_n2(int feat, dim3 grid, dim3 block, cudaStream_t st, const View
 template <int DT>
 void launch_dt(const ViewTable& vt, const Record* rec, const uint32_t* pair_items, const uint2* ranges, bool save,
                unsigned long long* stats, int sampler, int feat, cudaStream_t st) {
-  dim3 grid(vt.n_tiles), block(256);
+  dim3 grid(vt.n_tiles * kCtasPerTile), block(32 * kRasterWarps);
   if (sampler == SMP_FLAT)
     launch_feat_n2<DT, SMP_FLAT>(feat, grid, block, st, vt, rec, pair_items, ranges);
   else if (stats)  // fragment statistics: the features change no fragment
@@ -254,7 +256,7 @@ void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* p
                        const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
                        int feat, cudaStream_t st) {
   if (sampler == SMP_HW_ATLAS) {  // inference only; the atlas dtype is the texture's
-    launch_feat_n2<DT_F32, SMP_HW_ATLAS>(feat, dim3(vt.n_tiles), dim3(256), st, vt, rec, pair_items, ranges);
+    launch_feat_n2<DT_F32, SMP_HW_ATLAS>(feat, dim3(vt.n_tiles * kCtasPerTile), dim3(32 * kRasterWarps), st, vt, rec, pair_items, ranges);
   } else if (tex_dtype == DT_F32) {
     launch_dt<DT_F32>(vt, rec, pair_items, ranges, save, stats, sampler, feat, st);
   } else if (tex_dtype == DT_BF16) {

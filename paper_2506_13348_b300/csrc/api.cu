@@ -657,6 +657,12 @@ ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, c
   }
   {
     ProfScope p(st, "raster_bwd");
+    // tiles by the entries the backward walks, longest first
+    uint32_t* obuf = nullptr;
+    void* otemp = nullptr;
+    TS_CUDA(tmp.alloc((void**)&obuf, (size_t)std::max(vt.n_tiles, 1) * 4 * sizeof(uint32_t)));
+    TS_CUDA(tmp.alloc(&otemp, radix_temp_bytes(vt.n_tiles, 4)));
+    vt.tile_order = launch_tile_order_walk(vt, sv->ranges, obuf, otemp, st);
     launch_raster_bwd(vt, sv->rec, sv->pair_items, sv->ranges, s->tex_dtype, gxa, g_items, g, sv->feat, st);
   }
   {

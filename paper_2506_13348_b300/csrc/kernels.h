@@ -50,6 +50,10 @@ void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStr
 // Tile launch order, longest list first: buf holds 4 * n words (keys and ids,
 // twice); returns the n sorted tile ids (inside buf).  temp: radix_temp_bytes(n, 4).
 const uint32_t* launch_tile_order(const uint2* ranges, int n, uint32_t* buf, void* temp, cudaStream_t st);
+// The same for the backward, by the entries it walks (up to each pixel's last
+// blended entry, vt.v[].last); 256-thread CTAs assume TILE == 16.
+const uint32_t* launch_tile_order_walk(const ViewTable& vt, const uint2* ranges, uint32_t* buf, void* temp,
+                                       cudaStream_t st);
 void launch_depth_bits(const uint64_t* depth_keys_unsorted, uint32_t* out, int n, cudaStream_t st);
 
 // raster_fwd.cu / raster_bwd.cu

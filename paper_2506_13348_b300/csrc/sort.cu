@@ -767,19 +767,58 @@ void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStr
 // stable sort keeps tile order among equal codes.  Issued in this order the
 // tiles with the most entries start in the grid's first wave instead of
 // stretching its last one.
+__device__ __forceinline__ uint32_t length_code(uint32_t len) {
+  if (len < 8u) return len;
+  const int e = 31 - __clz((int)len);                         // 3..31
+  return ((uint32_t)(e - 2) << 3) | ((len >> (e - 3)) & 7u);  // 8..239
+}
+
 __global__ void k_tile_order_keys(const uint2* __restrict__ ranges, int n, uint32_t* __restrict__ keys,
                                   uint32_t* __restrict__ ids) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint2 r = ranges[i];
-  const uint32_t len = r.y - r.x;
-  uint32_t code = len;
-  if (len >= 8u) {
-    const int e = 31 - __clz((int)len);  // 3..31
-    code = ((uint32_t)(e - 2) << 3) | ((len >> (e - 3)) & 7u);  // 8..239
-  }
-  keys[i] = 255u - code;
+  keys[i] = 255u - length_code(r.y - r.x);
   ids[i] = (uint32_t)i;
+}
+
+// Backward variant: the entries the backward walks in a tile, i.e. up to the
+// last blended entry of its pixels (saved by the forward), instead of the
+// whole list.  One CTA of 256 threads per tile, one thread per pixel.
+__global__ void __launch_bounds__(256) k_tile_walk_keys(ViewTable vt, const uint2* __restrict__ ranges,
+                                                        uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+  const int tile = blockIdx.x;
+  const ViewDesc& V = vt.v[find_view(vt, tile)];
+  const int tl = tile - V.tile_off;
+  const int px = (tl % V.tiles_x) * TILE + (threadIdx.x & (TILE - 1));
+  const int py = (tl / V.tiles_x) * TILE + (threadIdx.x / TILE);
+  const uint2 r = ranges[tile];
+  uint32_t walk = 0;
+  if (px < V.W && py < V.H) {
+    const int last = V.last[py * V.W + px];
+    if (last >= (int)r.x) walk = (uint32_t)last - r.x + 1u;
+  }
+  walk = __reduce_max_sync(0xffffffffu, walk);
+  __shared__ uint32_t s_w[8];
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = walk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m = max(m, s_w[w]);
+    keys[tile] = 255u - length_code(m);
+    ids[tile] = (uint32_t)tile;
+  }
+}
+
+const uint32_t* launch_tile_order_walk(const ViewTable& vt, const uint2* ranges, uint32_t* buf, void* temp,
+                                       cudaStream_t st) {
+  const int n = vt.n_tiles;
+  if (n <= 0) return buf + n;
+  k_tile_walk_keys<<<n, 256, 0, st>>>(vt, ranges, buf, buf + n);
+  note_launches(1);
+  const int w = radix_sort_u32(buf, buf + n, buf + 2 * n, buf + 3 * n, n, 0, 8, temp, st);
+  return w ? buf + 3 * n : buf + n;
 }
 
 const uint32_t* launch_tile_order(const uint2* ranges, int n, uint32_t* buf, void* temp, cudaStream_t st) {

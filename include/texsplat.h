@@ -149,7 +149,10 @@ ts_status ts_render(ts_scene* scene, const ts_camera* cam, float* out_rgba, ts_s
  * TS_ERR_CAPACITY (more than 2^30 (tile, splat) pairs or a batch too large),
  * TS_ERR_TIMEOUT (a bounded inter-block wait of a radix sort ran out: a
  * device-side failure that is reported at this call's synchronisation, and
- * the flag is cleared), TS_ERR_OOM, TS_ERR_CUDA. */
+ * the flag is cleared; a sort issued after that synchronisation -- the pair
+ * sort, the rasterisers' tile orders, the backward's -- is reported by the
+ * next call), TS_ERR_OOM, TS_ERR_CUDA.  The rasteriser takes the tiles
+ * longest list first; the order changes no result. */
 ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_views,
                           float* const* out_rgba, ts_saved** saved, void* stream);
 
@@ -158,7 +161,10 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
  * dL_drgba: device [H][W][4] per view (array of n_views pointers for the
  * batched form, in view order).  Gradients are accumulated into `grads`
  * (one set per scene; for the batched form all views must share one scene).
- * The saved handle stays valid (backward may be repeated). */
+ * The saved handle stays valid (backward may be repeated).  The backward
+ * rasteriser takes the tiles by the list entries it walks (up to each
+ * pixel's last blended entry), longest first; temporaries are allocated with
+ * cudaMallocAsync on `stream`. */
 ts_status ts_render_backward(const ts_saved* saved, const float* const* dL_drgba,
                              const ts_grads* grads, void* stream);
 

@@ -3,7 +3,8 @@
 Sec. 3.6 trains with L_img = (1 - lambda) L_1 + lambda L_D-SSIM, lambda = 0.2.
 The paper does not restate SSIM; this module writes out the standard
 structural-similarity index of Wang et al. (2004) as the 3DGS line of work
-evaluates it (reading R17):
+evaluates it (the paper names D-SSIM and lambda only; window, padding,
+constants and the RGB-only mean below are those conventions):
 
   per RGB channel, with G the normalised 11 x 11 Gaussian window (sigma 1.5)
   applied as a 2-D convolution with zero padding ("same" size):
@@ -17,7 +18,8 @@ evaluates it (reading R17):
 Everything is float64 numpy/torch; the convolution is torch's conv2d (a
 library primitive), the gradient is autograd of the same expression.
 
-Normal consistency (Sec. 3.6, L_n = 1 - N~^T N, reading R18): the rendered
+Normal consistency (Sec. 3.6 gives only L_n = 1 - N~^T N; the depth kind,
+the stencil and the treatment of background below follow 2DGS): the rendered
 depth is the expected depth D = Z / A of the blended camera depth Z and the
 coverage A; each pixel is back-projected to P = D (x'/fx, y'/fy, 1) in camera
 space; the depth normal is N~ = normalize((P[y+1] - P[y-1]) x (P[x+1] - P[x-1]))

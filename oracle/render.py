@@ -19,16 +19,20 @@ splat):
   normals    n = R_k n^t with R_k = [t_u, t_v, n_k'] and n_k' the splat normal
              turned to face the camera                    (Eq. 7)
              with the two-component encoding (scene["normal_encoding"] ==
-             "xy", Sec. 3.5.1, reading R20) only channels 5-6 are read and
+             "xy", Sec. 3.5.1) only channels 5-6 are read and
              n^t = (n_x, n_y, sqrt(max(0, 1 - n_x^2 - n_y^2))) from the
-             interpolated (n_x, n_y)
+             interpolated (n_x, n_y): the paper gives the formula, not
+             whether it applies before or after filtering; a filtered
+             two-channel texture gives this order
   blending   X = sum_i x_i alpha_i prod_{j<i}(1 - alpha_j)  (Eq. 3, Eq. 8-9)
              A = sum_i alpha_i prod_{j<i}(1 - alpha_j); stop after the first
              fragment that brings the transmittance below 1e-4
   depth      Z = sum_i w_i tau_i (blended camera depth of the hits)
-  indirect   with per-splat SH coefficients c_k (degree <= 2, reading R19):
-             l_i = c_k . Y(w_r,i), w_r,i the reflection of w_o = -d/|d| about
-             the fragment's normalised normal; Xind = sum_i w_i l_i (Eq. 9)
+  indirect   with per-splat SH coefficients c_k (degree <= 2; the paper
+             defers the SH to Ref-Gaussian without the degree, basis or where
+             it is evaluated): l_i = c_k . Y(w_r,i), w_r,i the reflection of
+             w_o = -d/|d| about the fragment's normalised normal;
+             Xind = sum_i w_i l_i (Eq. 9)
   shading    see shading.py                               (Eq. 10-12)
 
 Products along a pixel's list are cumulative products and sums cumulative sums
@@ -36,10 +40,21 @@ Products along a pixel's list are cumulative products and sums cumulative sums
 changes no bit of the result: that is what makes the brute-force comparison
 exact.
 
+Admissible results: the definition's thresholds (|u|, |v| <= 3, alpha >=
+1/255, T < 1e-4, the orientation test) are discontinuous, and an FP32
+renderer evaluating the same definition may land on the other side of one
+when the FP64 value lies within FP32 error of it.  Each pixel is classified:
+no decision within its band (a unique result), exactly one (two admissible
+results: the definition's, and "alt" with that one decision flipped), or
+more than one ("ambiguous", masked in comparisons).  Band half-widths are
+DEFAULT_MARGINS below.
+
 Parity: pinned by the closed-form single-splat and two-splat tests, the
 texel-centre and affine-texture tests, the constant-texture invariant, the
 90-degree twist invariant and the brute-force comparison
-(tests/test_oracle_render.py).
+(tests/test_oracle_render.py); the alternative results by closed forms of
+pixels placed exactly at a support edge and at the termination threshold
+(tests/test_oracle_alternates.py).
 """
 from __future__ import annotations
 
@@ -112,7 +127,13 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
     indices cand [P, L] (-1 = padding), in list order.
 
     Returns a dict with alpha-validity masks, the blended weights, the
-    per-fragment attribute vectors and the composited G-buffer.
+    per-fragment attribute vectors and the composited G-buffer.  With
+    ``margins`` it also classifies each pixel by the discrete decisions of
+    the definition (support edge, alpha threshold, termination, orientation)
+    that lie within FP32 error of flipping: with none the result is unique;
+    with exactly one, flipping that decision gives the only other admissible
+    result, returned as ``alt`` (an FP32 renderer may take either branch);
+    with more, the pixel is ``ambiguous`` (excluded from comparisons).
     """
     P, L = cand.shape
     _, _, origin = camera_tensors(cam)
@@ -120,6 +141,7 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
     pad = cand < 0
     ci = cand.clamp_min(0)
     T = params["texels"].shape[1]
+    m_uv = margins[0] if margins is not None else 0.0
 
     tu_all, tv_all, n_all = rotation_columns(params["quats"])
     p = params["means"][ci]          # [P,L,3]
@@ -141,8 +163,12 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
     u = (rel * tu).sum(-1) / su
     v = (rel * tv).sum(-1) / sv
     inside = hit & (u.abs() <= 3.0) & (v.abs() <= 3.0)
-    u_s = torch.where(inside, u, torch.zeros_like(u))
-    v_s = torch.where(inside, v, torch.zeros_like(v))
+    # fragments are also evaluated just outside the support square (within
+    # the edge band) so that the alternative with the edge decision flipped
+    # can be composited; they carry no weight in the definition's result
+    reach = hit & (u.abs() <= 3.0 + m_uv) & (v.abs() <= 3.0 + m_uv)
+    u_s = torch.where(reach, u, torch.zeros_like(u))
+    v_s = torch.where(reach, v, torch.zeros_like(v))
     G = torch.exp(-(u_s * u_s + v_s * v_s) / 2.0)
     oG = op * G
     alpha = torch.clamp(oG, max=ALPHA_MAX)
@@ -154,9 +180,6 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
     from .shading import bilinear_2d
     tex = bilinear_2d(params["texels"], s * T - 0.5, t * T - 0.5, lead_index=ci)  # [P,L,8]
 
-    # normal mapping (Eq. 7): columns t_u, t_v and the camera-facing normal
-    flip = num > 0.0
-    n_face = torch.where(flip[..., None], -n, n)
     nt = tex[..., 5:8]
     nz_r = None
     if params.get("normal_xy", False):
@@ -166,61 +189,103 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
         pos = nz_r > 0.0
         nz = torch.where(pos, torch.sqrt(torch.where(pos, nz_r, torch.ones_like(nz_r))), torch.zeros_like(nz_r))
         nt = torch.cat([tex[..., 5:7], nz[..., None]], -1)
-    n_w = nt[..., 0:1] * tu + nt[..., 1:2] * tv + nt[..., 2:3] * n_face
-    x = torch.cat([tex[..., 0:5], n_w], -1)  # [P,L,8]
-
-    # compositing (Eq. 3, Eq. 8): sequential products / sums along the list
-    a = torch.where(valid, alpha, torch.zeros_like(alpha))
-    trans = torch.cumprod(1.0 - a, dim=1)
-    T_before = torch.cat([torch.ones_like(trans[:, :1]), trans[:, :-1]], 1)
-    blended = valid & (T_before >= T_MIN)
-    w = torch.where(blended, a * T_before, torch.zeros_like(a))
-    X = torch.cumsum(w[..., None] * x, dim=1)[:, -1, :] if L > 0 else torch.zeros(P, 8, dtype=F64)
-    A = torch.cumsum(w, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
-    # depth channel: the blended camera depth of the hits, sum_i w_i tau_i (the
-    # ray has camera-space z component 1, so tau is the camera depth)
-    tau_s = torch.where(blended, tau, torch.zeros_like(tau))
-    Z = torch.cumsum(w * tau_s, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
-    Xind = None
+    wo = None
     if "sh" in params:
-        # indirect light (Sec. 3.5, Eq. 9 and 12): each fragment evaluates its
-        # splat's SH coefficients in the reflection direction of its own
-        # (normal-mapped, normalised) normal; the results are blended
         from .shading import sh_basis
         wo = -(d / torch.linalg.vector_norm(d, dim=-1, keepdim=True))[:, None, :]
-        nl = torch.linalg.vector_norm(n_w, dim=-1, keepdim=True)
-        nz = nl >= 1e-12
-        nh = torch.where(nz, n_w / torch.where(nz, nl, torch.ones_like(nl)), wo.expand_as(n_w))
-        ndw = (nh * wo).sum(-1, keepdim=True)
-        wr = 2.0 * ndw * nh - wo
         sh = params["sh"][ci]                                   # [P,L,K,3]
-        Y = sh_basis(wr, sh.shape[-2])                          # [P,L,K]
-        lind = (Y[..., None] * sh).sum(-2)                      # [P,L,3]
-        Xind = torch.cumsum(w[..., None] * lind, dim=1)[:, -1, :] if L > 0 else torch.zeros(P, 3, dtype=F64)
-    ab = torch.where(blended, a, torch.zeros_like(a))
-    T_final = torch.cumprod(1.0 - ab, dim=1)[:, -1] if L > 0 else torch.ones(P, dtype=F64)
 
-    out = dict(X=X, A=A, Z=Z, Xind=Xind, T=T_final, ray_d=d, blended=blended, valid=valid, T_before=T_before)
+    def composite(valid_, flip_, tmin):
+        """Normal mapping and front-to-back compositing of the fragments
+        marked valid, with the splat normals flipped where flip_ and the
+        termination threshold tmin (a float or a [P, 1] tensor)."""
+        # normal mapping (Eq. 7): columns t_u, t_v and the camera-facing normal
+        n_face = torch.where(flip_[..., None], -n, n)
+        n_w = nt[..., 0:1] * tu + nt[..., 1:2] * tv + nt[..., 2:3] * n_face
+        x = torch.cat([tex[..., 0:5], n_w], -1)  # [P,L,8]
+        # compositing (Eq. 3, Eq. 8): sequential products / sums along the list
+        a = torch.where(valid_, alpha, torch.zeros_like(alpha))
+        trans = torch.cumprod(1.0 - a, dim=1)
+        T_before = torch.cat([torch.ones_like(trans[:, :1]), trans[:, :-1]], 1)
+        blended = valid_ & (T_before >= tmin)
+        w = torch.where(blended, a * T_before, torch.zeros_like(a))
+        X = torch.cumsum(w[..., None] * x, dim=1)[:, -1, :] if L > 0 else torch.zeros(P, 8, dtype=F64)
+        A = torch.cumsum(w, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
+        # depth channel: the blended camera depth of the hits, sum_i w_i tau_i
+        # (the ray has camera-space z component 1, so tau is the camera depth)
+        tau_s = torch.where(blended, tau, torch.zeros_like(tau))
+        Z = torch.cumsum(w * tau_s, dim=1)[:, -1] if L > 0 else torch.zeros(P, dtype=F64)
+        Xind = None
+        if "sh" in params:
+            # indirect light (Sec. 3.5, Eq. 9 and 12): each fragment evaluates
+            # its splat's SH coefficients in the reflection direction of its
+            # own (normal-mapped, normalised) normal; the results are blended
+            nl = torch.linalg.vector_norm(n_w, dim=-1, keepdim=True)
+            nzm = nl >= 1e-12
+            nh = torch.where(nzm, n_w / torch.where(nzm, nl, torch.ones_like(nl)), wo.expand_as(n_w))
+            ndw = (nh * wo).sum(-1, keepdim=True)
+            wr = 2.0 * ndw * nh - wo
+            Y = sh_basis(wr, sh.shape[-2])                          # [P,L,K]
+            li = (Y[..., None] * sh).sum(-2)                        # [P,L,3]
+            Xind = torch.cumsum(w[..., None] * li, dim=1)[:, -1, :] if L > 0 else torch.zeros(P, 3, dtype=F64)
+        ab = torch.where(blended, a, torch.zeros_like(a))
+        T_final = torch.cumprod(1.0 - ab, dim=1)[:, -1] if L > 0 else torch.ones(P, dtype=F64)
+        idx = torch.arange(L).expand(P, L)
+        last = torch.where(blended, idx, torch.full_like(idx, -1)).max(1).values if L > 0 \
+            else torch.full((P,), -1, dtype=torch.long)
+        return dict(X=X, A=A, Z=Z, Xind=Xind, T=T_final, blended=blended, T_before=T_before, a=a, last=last)
+
+    flip = num > 0.0
+    base = composite(valid, flip, T_MIN)
+    blended, T_before = base["blended"], base["T_before"]
+    out = dict(X=base["X"], A=base["A"], Z=base["Z"], Xind=base["Xind"], T=base["T"], ray_d=d, blended=blended,
+               valid=valid, T_before=T_before)
     with torch.no_grad():
         evaluated = (T_before >= T_MIN) & ~pad
         out["n_eval"] = evaluated.sum(1)
         out["n_contrib"] = blended.sum(1)
         # index (within the list) of the last blended fragment, -1 if none
-        idx = torch.arange(L).expand(P, L)
-        out["last"] = torch.where(blended, idx, torch.full_like(idx, -1)).max(1).values if L > 0 \
-            else torch.full((P,), -1, dtype=torch.long)
+        out["last"] = base["last"]
         if margins is not None:
             m_uv, m_a, m_t, m_f = margins
-            maybe_eval = (T_before >= T_MIN * (1.0 - m_t)) & hit
             oG_full = op * torch.exp(-(u * u + v * v).clamp(max=1e4) / 2.0)
             near_edge = (((u.abs() - 3.0).abs() <= m_uv) & (v.abs() <= 3.0 + m_uv)) | \
                         (((v.abs() - 3.0).abs() <= m_uv) & (u.abs() <= 3.0 + m_uv))
-            amb = near_edge & (oG_full >= ALPHA_MIN * (1.0 - m_a))
-            amb |= inside & ((oG - ALPHA_MIN).abs() <= m_a * ALPHA_MIN)
-            T_after = T_before * (1.0 - a)
-            amb |= valid & ((T_after / T_MIN - 1.0).abs() <= m_t)
-            amb |= inside & (num.abs() <= m_f * torch.linalg.vector_norm(po, dim=-1))
-            out["ambiguous"] = (amb & maybe_eval).any(1)
+
+            def bands(valid_, res):
+                """Fragments whose existence (support edge, alpha threshold),
+                termination test or orientation lies within its band, among
+                those an FP32 renderer could still evaluate."""
+                maybe_eval = (res["T_before"] >= T_MIN * (1.0 - m_t)) & hit
+                b_valid = near_edge & (oG_full >= ALPHA_MIN * (1.0 - m_a))
+                b_valid |= inside & ((oG - ALPHA_MIN).abs() <= m_a * ALPHA_MIN)
+                T_after = res["T_before"] * (1.0 - res["a"])
+                b_term = valid_ & ((T_after / T_MIN - 1.0).abs() <= m_t)
+                b_flip = inside & (num.abs() <= m_f * torch.linalg.vector_norm(po, dim=-1))
+                return b_valid & maybe_eval, b_term & maybe_eval, b_flip & maybe_eval, T_after
+
+            b_valid, b_term, b_flip, T_after = bands(valid, base)
+            any_b = b_valid | b_term | b_flip
+            n_amb = any_b.sum(1)
+            single = n_amb == 1
+            # the one alternative: flip that decision (validity, the normal's
+            # orientation, or whether compositing stops after the fragment)
+            tog_v = b_valid & single[:, None]
+            tog_f = b_flip & single[:, None]
+            term = b_term & single[:, None] & ~tog_v & ~tog_f
+            Ta = torch.where(term, T_after, torch.zeros_like(T_after)).sum(1, keepdim=True)
+            has_t = term.any(1, keepdim=True)
+            stops = Ta < T_MIN  # the definition stops after it: the alternative goes on for one more
+            tmin_alt = torch.where(has_t, torch.where(stops, Ta, Ta * (1.0 + 1e-12)),
+                                   torch.full_like(Ta, T_MIN))
+            alt = composite(valid ^ tog_v, flip ^ tog_f, tmin_alt)
+            # the alternative must not itself sit near another decision
+            a_valid, a_term, a_flip, _ = bands(valid ^ tog_v, alt)
+            extra = ((a_valid | a_term | a_flip) & ~(tog_v | tog_f | term)).any(1)
+            out["alt"] = {k: alt[k] for k in ("X", "A", "Z", "Xind", "T", "last")}
+            out["alt_mask"] = single & ~extra
+            out["ambiguous"] = (n_amb >= 2) | (single & extra)
+            out["decision_band"] = n_amb >= 1
             # derivative kinks of blended fragments (value continuous, slope
             # not): bilinear cell boundaries at texel centres (incl. the
             # clamp edges) and the 0.99 opacity clamp
@@ -310,6 +375,9 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
     n_con = torch.zeros(H, W, dtype=torch.long)
     last = torch.full((H, W), -1, dtype=torch.long)
     covered = torch.zeros(H, W, dtype=torch.bool)
+    alt = dict(rgba=torch.zeros(H, W, 4, dtype=F64), X=torch.zeros(H, W, 8, dtype=F64),
+               A=torch.zeros(H, W, dtype=F64), Z=torch.zeros(H, W, dtype=F64), T=torch.ones(H, W, dtype=F64),
+               last=torch.full((H, W), -1, dtype=torch.long), mask=torch.zeros(H, W, dtype=torch.bool))
 
     def run_chunk(chunk):
         pxs, pys, cands = [], [], []
@@ -333,8 +401,8 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         py = np.concatenate(pys)
         fr = fragments(params, cam, px, py, torch.from_numpy(cm), margins)
         pyt, pxt = torch.from_numpy(py), torch.from_numpy(px)
-        col = shade(fr["X"], fr["A"], fr["ray_d"], envp, Xind=fr["Xind"],
-                    vis=None if vis_t is None else vis_t[pyt, pxt])
+        vis_p = None if vis_t is None else vis_t[pyt, pxt]
+        col = shade(fr["X"], fr["A"], fr["ray_d"], envp, Xind=fr["Xind"], vis=vis_p)
         rgba.index_put_((pyt, pxt), col)
         Xb.index_put_((pyt, pxt), fr["X"])
         Ab.index_put_((pyt, pxt), fr["A"])
@@ -347,9 +415,12 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
         last[pyt, pxt] = fr["last"]
         covered[pyt, pxt] = True
         if margins is not None:
-            a2 = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
-            amb[pyt, pxt] = a2
-            gamb[pyt, pxt] = a2 | fr["kink"] | shading_kinks(fr["X"].detach(), fr["A"].detach(), fr["ray_d"], envp)
+            m = masks_and_alt(fr, envp, vis_p, col)
+            amb[pyt, pxt] = m["ambiguous"]
+            gamb[pyt, pxt] = m["grad_ambiguous"]
+            for k in ("rgba", "X", "A", "Z", "T", "last"):
+                alt[k][pyt, pxt] = m["alt"][k]
+            alt["mask"][pyt, pxt] = m["alt_mask"]
 
     chunk, size = [], 0
     for tl in tile_list:
@@ -363,7 +434,7 @@ def render(scene: dict, cam: dict, env: dict, *, params=None, envp=None, brute=F
     if chunk:
         run_chunk(chunk)
     return dict(rgba=rgba, X=Xb, A=Ab, Z=Zb, Xind=Ib, T=Tb, ambiguous=amb, grad_ambiguous=gamb, n_eval=n_eval,
-                n_contrib=n_con, last=last, covered=covered, keys=kl)
+                n_contrib=n_con, last=last, covered=covered, keys=kl, alt=alt)
 
 
 def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, params=None,
@@ -384,11 +455,39 @@ def render_pixels(scene: dict, cam: dict, env: dict, px, py, *, keylist=None, pa
     fr = fragments(params, cam, px, py, torch.from_numpy(cm), margins)
     vis_p = None if vis is None else torch.from_numpy(np.asarray(vis, dtype=np.float64)[np.asarray(py), np.asarray(px)])
     col = shade(fr["X"], fr["A"], fr["ray_d"], envp, Xind=fr["Xind"], vis=vis_p)
-    amb = fr["ambiguous"] | shading_ambiguity(fr["X"].detach(), fr["A"].detach(), fr["ray_d"])
-    gamb = amb | fr["kink"] | shading_kinks(fr["X"].detach(), fr["A"].detach(), fr["ray_d"], envp)
-    return dict(rgba=col, X=fr["X"], A=fr["A"], Z=fr["Z"], T=fr["T"], ambiguous=amb, grad_ambiguous=gamb,
-                n_eval=fr["n_eval"],
-                n_contrib=fr["n_contrib"], last=fr["last"])
+    out = dict(rgba=col, X=fr["X"], A=fr["A"], Z=fr["Z"], T=fr["T"], n_eval=fr["n_eval"],
+               n_contrib=fr["n_contrib"], last=fr["last"])
+    if margins is not None:
+        out.update(masks_and_alt(fr, envp, vis_p, col))
+    return out
+
+
+def masks_and_alt(fr: dict, envp: dict, vis_p, col: torch.Tensor) -> dict:
+    """Per-pixel comparison masks of a fragments() result computed with margins.
+
+    ambiguous       more than one decision within FP32 error of flipping (or
+                    a shading decision there): no unique admissible result,
+                    excluded from image comparisons;
+    alt / alt_mask  exactly one such decision: the result with it flipped
+                    (rgba, X, A, Z, T, last), the other admissible result;
+    grad_ambiguous  any decision in its band, or a derivative kink: excluded
+                    from gradient comparisons (a slope differs across them).
+    """
+    with torch.no_grad():
+        X, A, d = fr["X"].detach(), fr["A"].detach(), fr["ray_d"]
+        a = fr["alt"]
+        Xind_a = a["Xind"].detach() if a["Xind"] is not None else None
+        col_a = shade(a["X"].detach(), a["A"].detach(), d, envp, Xind=Xind_a, vis=vis_p).detach()
+        single = fr["alt_mask"]
+        amb = fr["ambiguous"] | shading_ambiguity(X, A, d) | (single & shading_ambiguity(a["X"], a["A"], d))
+        single = single & ~amb
+        # pixels without an alternative carry the definition's result there too
+        sel = single[:, None]
+        alt = dict(rgba=torch.where(sel, col_a, col.detach()), X=torch.where(sel, a["X"], X),
+                   A=torch.where(single, a["A"], A), Z=torch.where(single, a["Z"], fr["Z"].detach()),
+                   T=torch.where(single, a["T"], fr["T"].detach()), last=torch.where(single, a["last"], fr["last"]))
+        gamb = amb | fr["decision_band"] | fr["kink"] | shading_kinks(X, A, d, envp)
+    return dict(ambiguous=amb, alt_mask=single, alt=alt, grad_ambiguous=gamb)
 
 
 def render_attributes_2dgs(scene: dict, cam: dict, env: dict, attrs: np.ndarray, **kw) -> dict:

@@ -2,7 +2,8 @@
 by one), the 1k-splat gradient slice, and GPU central differences.
 
 * 200k splats, 800x800 (the benchmarked training view): the whole tile/sort
-  list bit-exact, sampled pixels within 1e-4;
+  list bit-exact, 4096 sampled pixels within 1e-4 of an admissible oracle
+  result (at most 0.1 % masked, the fraction printed);
 * 500k splats, 16x16 texels, 1920x1080, 6-level FP16 cube, BF16 / FP16
   atlases: sampled pixels within 1e-4 of an oracle fed the same rounded
   texels and cube;
@@ -19,9 +20,11 @@ import scenegen as sg
 from oracle import grad as G
 from oracle import keys as K
 from oracle import render as R
+from tests.helpers import check_admissible
 
 pytestmark = pytest.mark.gpu
 IMG_TOL = 1e-4
+N_SAMPLES = 4096  # sampled pixels per full-size view: 0.1 % is 4 pixels
 
 
 @pytest.fixture(scope="module")
@@ -34,15 +37,18 @@ def sample_pixels(rng, W, H, n):
     return rng.integers(0, W, size=n), rng.integers(0, H, size=n)
 
 
-def check_sampled(out, ref, px, py, tol=IMG_TOL, max_amb=0.01):
+def oracle_pixels(scene, cam, env, px, py, kl, chunk=256, **kw):
+    """The oracle's sampled pixels, in chunks (bounded host memory)."""
+    parts = [R.render_pixels(scene, cam, env, px[i:i + chunk], py[i:i + chunk], keylist=kl, **kw)
+             for i in range(0, len(px), chunk)]
+    out = {k: torch.cat([p[k] for p in parts]) for k in ("rgba", "ambiguous", "alt_mask")}
+    out["alt"] = {"rgba": torch.cat([p["alt"]["rgba"] for p in parts])}
+    return out
+
+
+def check_sampled(out, ref, px, py, tol=IMG_TOL, max_masked=1e-3, label=""):
     g = out.cpu().numpy()[py, px].astype(np.float64)
-    r = ref["rgba"].detach().numpy()
-    amb = ref["ambiguous"].numpy()
-    assert amb.mean() <= max_amb, amb.mean()
-    err = np.abs(g - r).max(-1)
-    bad = (err > tol) & ~amb
-    assert not bad.any(), (int(bad.sum()), float(err[~amb].max()))
-    return float(err[~amb].max())
+    return check_admissible(g, ref, tol, max_masked, label)["max_err"]
 
 
 def test_cfg1_full_size_keys_and_sampled_pixels(P):
@@ -57,9 +63,9 @@ def test_cfg1_full_size_keys_and_sampled_pixels(P):
     assert np.array_equal(ids, kl["ids"])
     ne = kl["tile_ranges"][:, 1] > kl["tile_ranges"][:, 0]
     assert np.array_equal(rng_t[ne], kl["tile_ranges"][ne])
-    px, py = sample_pixels(np.random.default_rng(5), 800, 800, 160)
-    ref = R.render_pixels(scene, cam, env, px, py, keylist=kl)
-    check_sampled(out, ref, px, py)
+    px, py = sample_pixels(np.random.default_rng(5), 800, 800, N_SAMPLES)
+    ref = oracle_pixels(scene, cam, env, px, py, kl)
+    check_sampled(out, ref, px, py, label="cfg1 800x800")
 
 
 @pytest.mark.parametrize("store", ["bf16", "f16"])
@@ -80,9 +86,9 @@ def test_cfg2_full_size_reduced_precision_sampled(P, store):
     torch.cuda.synchronize()
     scene_r = dict(geo, texels=tex_r, T=16)
     kl = K.build_keys(scene_r, cam)
-    px, py = sample_pixels(np.random.default_rng(6), 1920, 1080, 96)
-    ref = R.render_pixels(scene_r, cam, env16, px, py, keylist=kl)
-    check_sampled(out, ref, px, py)
+    px, py = sample_pixels(np.random.default_rng(6), 1920, 1080, N_SAMPLES)
+    ref = oracle_pixels(scene_r, cam, env16, px, py, kl)
+    check_sampled(out, ref, px, py, label=f"cfg2 1920x1080 {store}")
 
 
 def test_grad_parity_cfg1_1k_slice(P):
@@ -183,10 +189,10 @@ def test_cfg1_full_size_with_indirect_light_and_two_component_normals(P):
     sc = P.Scene.from_arrays(scene, env)
     out, _ = P.render(sc, dict(cam, vis=torch.from_numpy(vis).cuda()))
     torch.cuda.synchronize()
-    px, py = sample_pixels(np.random.default_rng(6), 800, 800, 160)
+    px, py = sample_pixels(np.random.default_rng(6), 800, 800, N_SAMPLES)
     kl = K.build_keys(scene, cam)
-    ref = R.render_pixels(scene, cam, env, px, py, keylist=kl, vis=vis)
-    check_sampled(out, ref, px, py)
+    ref = oracle_pixels(scene, cam, env, px, py, kl, vis=vis)
+    check_sampled(out, ref, px, py, label="cfg1 indirect + two-component normals")
 
 
 def test_cfg4_scale_batch_keys_and_sampled_pixels(P):
@@ -224,8 +230,7 @@ def test_cfg4_scale_batch_keys_and_sampled_pixels(P):
         np.testing.assert_array_equal(rng_t[t_off:t_off + nt][ne], ref_rng[ne] + k_off)
         k_off += kv
         t_off += nt
-        px, py = sample_pixels(rng, 1600, 1064, 128)
-        ref = R.render_pixels(scene_r, cam, env, px, py, keylist=kl)
-        # deep pixels of this dense scene sit near a threshold more often
-        check_sampled(outs[v], ref, px, py, max_amb=0.04)
+        px, py = sample_pixels(rng, 1600, 1064, N_SAMPLES)
+        ref = oracle_pixels(scene_r, cam, env, px, py, kl)
+        check_sampled(outs[v], ref, px, py, label=f"cfg4 view {v}")
     saved.release()

@@ -10,6 +10,7 @@ from oracle import grad as G
 from oracle import keys as K
 from oracle import loss as OL
 from oracle import render as R
+from tests.helpers import admissible_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -39,10 +40,10 @@ def test_depth_channel_matches_oracle(P):
     torch.cuda.synchronize()
     z, a = z.cpu().numpy().astype(np.float64), a.cpu().numpy().astype(np.float64)
     amb = ref["ambiguous"].numpy()
-    zr, ar = ref["Z"].numpy(), ref["A"].numpy()
-    assert (ar > 0.5).sum() > 2000
-    assert np.abs(a - ar)[~amb].max() <= 1e-4
-    assert np.abs(z - zr)[~amb].max() <= 4e-4  # depths ~4: 1e-4 relative
+    assert amb.mean() <= 1e-3
+    assert (ref["A"].numpy() > 0.5).sum() > 2000
+    assert admissible_errors(a, ref, "A")[~amb].max() <= 1e-4
+    assert admissible_errors(z, ref, "Z")[~amb].max() <= 4e-4  # depths ~4: 1e-4 relative
     saved.release()
 
 

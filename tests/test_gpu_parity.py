@@ -1,8 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Bar: tile/sort lists bit-exact; images within 1e-4 max-abs on pixels the
-oracle does not flag as ambiguous (a threshold decision within a hair of
-flipping between FP32 and FP64), with at most 0.1 % of pixels flagged.
+Bar: tile/sort lists bit-exact; images within 1e-4 max-abs of an admissible
+oracle result on every pixel: the definition's result, or, where exactly one
+threshold decision of the pixel lies within FP32 error of flipping, the
+result with that decision flipped.  Pixels with several such decisions are
+masked, at most 0.1 % of them.
 """
 import numpy as np
 import pytest
@@ -11,6 +13,7 @@ import torch
 import scenegen as sg
 from oracle import keys as K
 from oracle import render as R
+from tests.helpers import admissible_errors, check_admissible
 
 pytestmark = pytest.mark.gpu
 
@@ -44,15 +47,8 @@ def compare_lists(saved, kl, n):
     assert np.all(db[~vis] == 0xFFFFFFFF)
 
 
-def compare_image(gpu_rgba, ref, tol=IMG_TOL, max_masked=1e-3):
-    g = gpu_rgba.detach().cpu().numpy().astype(np.float64)
-    r = ref["rgba"].detach().numpy()
-    amb = ref["ambiguous"].numpy()
-    assert amb.mean() <= max_masked, amb.mean()
-    err = np.abs(g - r).max(-1)
-    bad = (err > tol) & ~amb
-    assert not bad.any(), (int(bad.sum()), float(err[~amb].max()), np.argwhere(bad)[:5])
-    return float(err[~amb].max())
+def compare_image(gpu_rgba, ref, tol=IMG_TOL, max_masked=1e-3, label=""):
+    return check_admissible(gpu_rgba.detach().cpu().numpy(), ref, tol, max_masked, label)["max_err"]
 
 
 def test_cfg0_keys_bit_exact_and_image(P):
@@ -63,19 +59,21 @@ def test_cfg0_keys_bit_exact_and_image(P):
     sc, out, saved = gpu_render(P, scene, env, cam)
     compare_lists(saved, kl, len(scene["opacity"]))
     ref = R.render(scene, cam, env, keylist=kl)
-    compare_image(out, ref)
-    # per-pixel forward state
+    compare_image(out, ref, label="cfg0")
+    # per-pixel forward state, against the same admissible results
     g, tr, last = saved.pixels(0)
     amb = ref["ambiguous"].numpy()
-    np.testing.assert_allclose(g.cpu().numpy()[~amb], ref["X"].numpy()[~amb], atol=IMG_TOL)
-    np.testing.assert_allclose(tr.cpu().numpy()[~amb], ref["T"].numpy()[~amb], atol=IMG_TOL)
+    assert admissible_errors(g.cpu().numpy(), ref, "X")[~amb].max() <= IMG_TOL
+    assert admissible_errors(tr.cpu().numpy(), ref, "T")[~amb].max() <= IMG_TOL
     # last blended fragment: oracle index is within the tile list
     tiles_x = kl["view"]["tiles_x"]
     yy, xx = np.meshgrid(np.arange(128), np.arange(128), indexing="ij")
     start = kl["tile_ranges"][(yy // 16) * tiles_x + xx // 16, 0]
-    ol = ref["last"].numpy()
-    exp_last = np.where(ol >= 0, start + ol, -1)
-    np.testing.assert_array_equal(last.cpu().numpy()[~amb], exp_last[~amb])
+    gl = last.cpu().numpy()
+    ok = np.zeros_like(amb)
+    for ol in (ref["last"].numpy(), ref["alt"]["last"].numpy()):
+        ok |= gl == np.where(ol >= 0, start + ol, -1)
+    assert (ok | amb).all()
 
 
 @pytest.mark.parametrize("seed,W,H,eye", [(3, 100, 77, (2.5, 1.5, 1.0)), (5, 64, 48, (0.0, -3.0, 2.0)),
@@ -87,7 +85,7 @@ def test_small_scenes_ragged_sizes(P, seed, W, H, eye):
     kl = K.build_keys(scene, cam)
     sc, out, saved = gpu_render(P, scene, env, cam)
     compare_lists(saved, kl, 600)
-    compare_image(out, R.render(scene, cam, env, keylist=kl))
+    compare_image(out, R.render(scene, cam, env, keylist=kl), label=f"ragged {W}x{H}")
 
 
 def test_empty_and_culled_scenes(P):
@@ -132,7 +130,7 @@ def test_reduced_precision_atlas_pipeline_parity(P, store):
     rounded = tt.to(torch.bfloat16 if store == "bf16" else torch.float16).float().numpy()
     sc, out, saved = gpu_render(P, scene, env, cam, store=store)
     ref = R.render(dict(scene, texels=rounded), cam, env)
-    compare_image(out, ref)
+    compare_image(out, ref, label=f"{store} atlas")
 
 
 def test_fragment_counts_match_oracle(P):
@@ -145,12 +143,13 @@ def test_fragment_counts_match_oracle(P):
     sc, out, saved = gpu_render(P, scene, env, cam)
     st = saved.frag_stats()
     ref = R.render(scene, cam, env, keylist=kl)
-    amb = ref["ambiguous"].numpy()
+    # pixels with a decision near its switching point may count differently
+    amb = ref["ambiguous"].numpy() | ref["alt"]["mask"].numpy()
     tiles_x = kl["view"]["tiles_x"]
     yy, xx = np.meshgrid(np.arange(128), np.arange(128), indexing="ij")
     rng = kl["tile_ranges"][(yy // 16) * tiles_x + xx // 16]
     list_len = rng[..., 1] - rng[..., 0]
-    slack = int(list_len[amb].sum())  # ambiguous pixels may count differently
+    slack = int(list_len[amb].sum())
     e_ref = int(ref["n_eval"].sum())
     c_ref = int(ref["n_contrib"].sum())
     assert st["n_pairs"] == kl["ids"].size

@@ -205,7 +205,33 @@ def cpu_oracle_sample(scene, env, cam, n_tiles: int, seed: int = 0):
     G.render_grads(scene, cam, env, dL, tiles=tiles, keylist=kl)
     dt = time.perf_counter() - t0
     px = 256 * len(tiles)
-    return px / dt / 1e6, dt, torch.get_num_threads(), px
+    return px / dt / 1e6, dt, torch.get_num_threads(), px, (tiles, kl)
+
+
+def parity_sample(scene, env, cam, tiles, kl, gpu_rgba):
+    """The GPU image of the timed workload against the oracle on the sampled
+    tiles (untimed): max-abs error over pixels with an admissible oracle
+    result (the definition's, or with the one threshold decision that lies
+    within FP32 error of flipping flipped), and the masked fraction (pixels
+    with several such decisions)."""
+    import numpy as np
+
+    from oracle import render as R
+    ref = R.render(scene, cam, env, tiles=tiles, keylist=kl)
+    g = gpu_rgba.detach().cpu().numpy().astype(np.float64)
+    tiles_x = kl["view"]["tiles_x"]
+    sel = np.zeros(g.shape[:2], dtype=bool)
+    for t in tiles:
+        ty, tx = divmod(int(t), tiles_x)
+        sel[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    r, ra = ref["rgba"].detach().numpy(), ref["alt"]["rgba"].numpy()
+    amb, alt = ref["ambiguous"].numpy(), ref["alt"]["mask"].numpy()
+    err = np.minimum(np.abs(g - r).max(-1), np.abs(g - ra).max(-1))
+    ok = sel & ~amb
+    return {"pixels": int(sel.sum()), "max_abs_err": float(err[ok].max()) if ok.any() else 0.0,
+            "tolerance": 1e-4, "masked": int((amb & sel).sum()), "masked_frac": float((amb & sel).sum() / sel.sum()),
+            "two_results": int((alt & sel).sum()),
+            "note": "GPU image of the first timed view vs the FP64 oracle on the CPU-baseline tiles"}
 
 
 def run_reference(args):
@@ -216,7 +242,7 @@ def run_reference(args):
     scene, env, cams = build_workload()
     vals, secs = [], []
     for i in range(args.warmup + args.steps):
-        v, dt, thr, px = cpu_oracle_sample(scene, env, cams[i % N_CAMS], max(1, args.cpu_tiles // 3), seed=i)
+        v, dt, thr, px, _ = cpu_oracle_sample(scene, env, cams[i % N_CAMS], max(1, args.cpu_tiles // 3), seed=i)
         if i >= args.warmup:
             vals.append(v)
             secs.append(dt)
@@ -348,6 +374,9 @@ def run_ours(args):
         line["image_loss"] = time_image_loss(P, out, targets[0], dev)
     if not args.no_e2e:
         line["e2e"] = run_e2e(P, sc, my_cams, n_needed, args, dev, pg, world)
+    par_img = None
+    if rank == 0 and not args.no_cpu_baseline:  # the image the parity sample checks (untimed)
+        par_img = P.render(sc, my_cams[0])[0].cpu()
     if rank == 0 and not args.no_serve:
         del grads
         sc.close()
@@ -362,10 +391,11 @@ def run_ours(args):
     if rank == 0 and not args.no_features:
         line["features"] = run_features(args, local)
     if rank == 0 and not args.no_cpu_baseline:
-        v, dt, thr, px = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
+        v, dt, thr, px, (tiles, kl) = cpu_oracle_sample(scene, env, my_cams[0], args.cpu_tiles)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                                 "sample": f"{args.cpu_tiles} random non-empty 16x16 tiles ({px} px) of one 800x800 view, "
                                           f"FP64 forward + autograd backward, {dt:.1f} s"}
+        line["parity_sample"] = parity_sample(scene, env, my_cams[0], tiles, kl, par_img)
     if rank == 0:
         print(json.dumps(line))
     if pg:

@@ -103,7 +103,14 @@ ts_status ts_destroy_scene(ts_scene* scene);
  * linear opacities o [n] in [0,1].  Copies into library memory (from device
  * memory if src_on_device, else host memory; the call then returns after
  * the host buffers may be reused).  n >= 0 (0 renders an empty image).
- * Replaces previous geometry; the atlas must be re-uploaded if n changed. */
+ * Replaces previous geometry; the atlas must be re-uploaded if n changed.
+ * The values are checked on the device before they replace anything:
+ * TS_ERR_ARG (message: the count, the first bad index and the reasons) for
+ * a non-finite centre, a quaternion that is non-finite or of squared norm
+ * below 1e-20, a scale that is non-finite or <= 0, an opacity outside
+ * [0, 1] or NaN.  On every error (TS_ERR_ARG, TS_ERR_OOM, TS_ERR_CUDA) the
+ * scene keeps its previous geometry and no library memory is left behind.
+ * Synchronises `stream`. */
 ts_status ts_upload_gaussians(ts_scene* scene, int64_t n, const float* means, const float* quats,
                               const float* scales, const float* opacity, int src_on_device,
                               void* stream);
@@ -112,7 +119,9 @@ ts_status ts_upload_gaussians(ts_scene* scene, int64_t n, const float* means, co
  * atlas construction, one contiguous T x T chart per splat).  texels
  * [n][T][T][C] float32 with C == 8 and 1 <= T <= 32; `store` selects the
  * stored precision (float32, or bfloat16 / float16 rounded to nearest
- * even).  Lookups always widen to float32. */
+ * even).  Lookups always widen to float32.  Texel values are data and are
+ * not checked.  On error the previous atlas stays in place.  Synchronises
+ * `stream`. */
 ts_status ts_upload_atlas(ts_scene* scene, int T, int C, ts_dtype store, const float* texels,
                           int src_on_device, void* stream);
 
@@ -121,7 +130,8 @@ ts_status ts_upload_atlas(ts_scene* scene, int T, int C, ts_dtype store, const f
  * irradiance cube [6][irr_res][irr_res][3]; the split-sum BRDF table
  * [lut_res][lut_res][2] (row = roughness, column = N.w_o; channels scale,
  * bias).  `store` F32 or F16 for the cube maps (the table stays float32).
- * 1 <= levels <= 12. */
+ * 1 <= levels <= 12.  On error the previous environment stays in place.
+ * Synchronises `stream`. */
 ts_status ts_upload_envmap(ts_scene* scene, int levels, int base_res, const float* spec, int irr_res,
                            const float* irr, int lut_res, const float* lut, ts_dtype store,
                            int src_on_device, void* stream);
@@ -147,12 +157,15 @@ ts_status ts_render(ts_scene* scene, const ts_camera* cam, float* out_rgba, ts_s
  * arguments, mixed dtypes / samplers / normal encodings in one batch),
  * TS_ERR_STATE (missing or stale uploads, a sampler that cannot save state),
  * TS_ERR_CAPACITY (more than 2^30 (tile, splat) pairs or a batch too large),
- * TS_ERR_TIMEOUT (a bounded inter-block wait of a radix sort ran out: a
- * device-side failure that is reported at this call's synchronisation, and
- * the flag is cleared; a sort issued after that synchronisation -- the pair
- * sort, the rasterisers' tile orders, the backward's -- is reported by the
- * next call), TS_ERR_OOM, TS_ERR_CUDA.  The rasteriser takes the tiles
- * longest list first; the order changes no result. */
+ * TS_ERR_TIMEOUT (the bounded inter-block wait of the per-splat depth sort
+ * ran out -- a device-side failure, reported at this call's
+ * synchronisation, before any pair is emitted), TS_ERR_OOM, TS_ERR_CUDA.
+ * The pair sort waits on nothing.  The rasterisers take the tiles longest
+ * list first; if the bounded wait of that launch-order sort runs out, they
+ * take the tiles in tile order instead, which changes no result, so an image
+ * returned with TS_OK is always the one the lists define.  (Should a kernel
+ * after the synchronisation still find a list id out of range, the image is
+ * written as NaN and the next call reports TS_ERR_TIMEOUT.) */
 ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_views,
                           float* const* out_rgba, ts_saved** saved, void* stream);
 
@@ -424,6 +437,13 @@ ts_status ts_activate_backward(int64_t n, const float* scales, const float* opac
  * error.  Synchronises `stream`. */
 ts_status ts_selftest_sort_wait(int device, void* stream);
 
+/* Host-side failure injection for tests: with after = k >= 0, the (k+1)-th
+ * device allocation the library makes from now on (uploads, render and
+ * backward scratch) fails once as out of memory, so that error paths can be
+ * exercised without exhausting the device; after = -1 disarms it.  No GPU
+ * fault is involved.  TS_ERR_ARG for after < -1. */
+ts_status ts_debug_fail_alloc(int64_t after);
+
 /* ---- rendering without device allocation ------------------------------------ */
 
 /* The paper has no counterpart of this entry point; it serves callers that
@@ -453,7 +473,9 @@ ts_status ts_selftest_sort_wait(int device, void* stream);
  *   stream capture.  Every call shares the array: the call clears what must
  *   start at zero, and calls that overlap on the GPU (streams not ordered
  *   with each other) race on it.  The call synchronises `stream` once to
- *   read the pair count. */
+ *   read the pair count and the sort flags: TS_ERR_TIMEOUT when the depth
+ *   sort's bounded wait ran out (the output is then left unwritten); the
+ *   launch-order sort falls back to tile order as in ts_render_views. */
 ts_status ts_render_noalloc(int64_t n, const float* means, const float* quats, const float* scales,
                             const float* opacity, int T, const float* texels, int levels, int base_res,
                             const float* spec, int irr_res, const float* irr, int lut_res, const float* lut,

@@ -28,7 +28,7 @@ EXPORTED = [
     "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
     "ts_image_loss", "ts_saved_copy_depth", "ts_normal_loss", "ts_upload_indirect",
     "ts_scene_set_normal_encoding", "ts_scene_envmap", "ts_activate", "ts_activate_backward",
-    "ts_selftest_sort_wait",
+    "ts_selftest_sort_wait", "ts_debug_fail_alloc",
 ]
 
 
@@ -112,6 +112,7 @@ def lib() -> C.CDLL:
         "ts_activate": [i64, vp, vp, vp, vp, vp],
         "ts_activate_backward": [i64, vp, vp, vp, vp, vp, vp, i32, vp],
         "ts_selftest_sort_wait": [i32, vp],
+        "ts_debug_fail_alloc": [i64],
         "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
         "ts_saved_copy_depth": [vp, i32, vp, vp, vp],
         "ts_normal_loss": [vp, i32, C.c_float, vp, vp],

@@ -1,6 +1,7 @@
 // C ABI of the textured 2DGS renderer: scene memory, the render / backward
 // launch sequences and inspection helpers.  See include/texsplat.h.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -37,6 +38,32 @@ ts_status fail(ts_status code, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(TS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
   } while (0)
 
+// Host-side failure injection for tests: when armed with k >= 0, the
+// (k+1)-th device allocation the library makes from then on fails with
+// cudaErrorMemoryAllocation (once), as a real out-of-memory would.
+std::atomic<long long> g_fail_alloc{-1};
+bool injected_failure() {
+  long long k = g_fail_alloc.load();
+  while (k >= 0) {
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) return k == 0;
+  }
+  return false;
+}
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, st);
+}
+
 std::mutex g_pool_mu;
 bool g_pool_set[64] = {false};
 
@@ -60,7 +87,7 @@ struct Scratch {
   explicit Scratch(cudaStream_t s) : st(s) {}
   cudaError_t alloc(void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(p, bytes, st);
+    cudaError_t e = dev_malloc_async(p, bytes, st);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
@@ -180,11 +207,30 @@ ts_status ts_destroy_scene(ts_scene* s) {
   return TS_OK;
 }
 
-static ts_status copy_in(void* dst, const void* src, size_t bytes, int src_on_device, cudaStream_t st) {
-  if (bytes == 0) return TS_OK;
-  TS_CUDA(cudaMemcpyAsync(dst, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  return TS_OK;
-}
+
+// Device buffers of one upload, freed unless released into the scene.
+struct UploadBufs {
+  std::vector<void*> p;
+  cudaError_t alloc(void** out, size_t bytes) {
+    cudaError_t e = dev_malloc(out, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) p.push_back(*out);
+    return e;
+  }
+  void release() { p.clear(); }
+  ~UploadBufs() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+
+#define TS_UP(call)                                                                                \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      cudaStreamSynchronize(st);                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,                      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                             \
+    }                                                                                              \
+  } while (0)
 
 ts_status ts_upload_gaussians(ts_scene* s, int64_t n, const float* means, const float* quats, const float* scales,
                               const float* opacity, int src_on_device, void* stream) {
@@ -195,29 +241,53 @@ ts_status ts_upload_gaussians(ts_scene* s, int64_t n, const float* means, const 
   cudaStream_t st = (cudaStream_t)stream;
   TS_CUDA(cudaSetDevice(s->device));
   TS_CUDA(cudaStreamSynchronize(st));
-  for (void** p : {(void**)&s->means, (void**)&s->quats, (void**)&s->scales, (void**)&s->opacity}) {
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-  }
-  s->n = n;
-  size_t nn = (size_t)std::max<int64_t>(n, 1);
-  TS_CUDA(cudaMalloc(&s->means, nn * sizeof(float4)));
-  TS_CUDA(cudaMalloc(&s->quats, nn * sizeof(float4)));
-  TS_CUDA(cudaMalloc(&s->scales, nn * sizeof(float2)));
-  TS_CUDA(cudaMalloc(&s->opacity, nn * sizeof(float)));
+  // the new buffers are filled and checked before they replace the old ones:
+  // a failed upload leaves the scene as it was
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  UploadBufs b;
+  float4 *m4 = nullptr, *q4 = nullptr;
+  float2* s2 = nullptr;
+  float *o1 = nullptr, *staging = nullptr;
+  unsigned* check = nullptr;
+  TS_UP(b.alloc((void**)&m4, nn * sizeof(float4)));
+  TS_UP(b.alloc((void**)&q4, nn * sizeof(float4)));
+  TS_UP(b.alloc((void**)&s2, nn * sizeof(float2)));
+  TS_UP(b.alloc((void**)&o1, nn * sizeof(float)));
+  TS_UP(b.alloc((void**)&staging, nn * 3 * sizeof(float)));
+  TS_UP(b.alloc((void**)&check, 4 * sizeof(unsigned)));
+  unsigned res[3] = {0u, 0xffffffffu, 0u};
+  TS_UP(cudaMemcpyAsync(check, res, sizeof(res), cudaMemcpyHostToDevice, st));
   if (n > 0) {
-    float* staging = nullptr;
-    TS_CUDA(cudaMallocAsync(&staging, nn * 3 * sizeof(float), st));
-    ts_status r = copy_in(staging, means, (size_t)n * 3 * sizeof(float), src_on_device, st);
-    if (r != TS_OK) return r;
-    launch_pad4(staging, 3, s->means, n, st);
-    TS_CHECK_LAUNCH();
-    TS_CUDA(cudaFreeAsync(staging, st));
-    if ((r = copy_in(s->quats, quats, (size_t)n * 4 * sizeof(float), src_on_device, st)) != TS_OK) return r;
-    if ((r = copy_in(s->scales, scales, (size_t)n * 2 * sizeof(float), src_on_device, st)) != TS_OK) return r;
-    if ((r = copy_in(s->opacity, opacity, (size_t)n * sizeof(float), src_on_device, st)) != TS_OK) return r;
+    const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    TS_UP(cudaMemcpyAsync(staging, means, (size_t)n * 3 * sizeof(float), kind, st));
+    launch_pad4(staging, 3, m4, n, st);
+    TS_UP(cudaMemcpyAsync(q4, quats, (size_t)n * 4 * sizeof(float), kind, st));
+    TS_UP(cudaMemcpyAsync(s2, scales, (size_t)n * 2 * sizeof(float), kind, st));
+    TS_UP(cudaMemcpyAsync(o1, opacity, (size_t)n * sizeof(float), kind, st));
+    launch_validate_gaussians(m4, q4, s2, o1, n, check, st);
+    TS_UP(cudaGetLastError());
+    TS_UP(cudaMemcpyAsync(res, check, sizeof(res), cudaMemcpyDeviceToHost, st));
   }
-  TS_CUDA(cudaStreamSynchronize(st));
+  TS_UP(cudaStreamSynchronize(st));
+  if (res[0]) {
+    std::string why;
+    if (res[2] & 1u) why += " non-finite centre;";
+    if (res[2] & 2u) why += " quaternion non-finite or of zero length;";
+    if (res[2] & 4u) why += " scale non-finite or <= 0;";
+    if (res[2] & 8u) why += " opacity outside [0, 1] or NaN;";
+    return fail(TS_ERR_ARG, "ts_upload_gaussians: " + std::to_string(res[0]) + " invalid splat(s), first index " +
+                                std::to_string(res[1]) + ":" + why + " the scene is unchanged");
+  }
+  for (void* p : {(void*)s->means, (void*)s->quats, (void*)s->scales, (void*)s->opacity})
+    if (p) cudaFree(p);
+  s->means = m4;
+  s->quats = q4;
+  s->scales = s2;
+  s->opacity = o1;
+  s->n = n;
+  cudaFree(staging);
+  cudaFree(check);
+  b.release();
   return TS_OK;
 }
 
@@ -231,36 +301,39 @@ ts_status ts_upload_atlas(ts_scene* s, int T, int C, ts_dtype store, const float
   cudaStream_t st = (cudaStream_t)stream;
   TS_CUDA(cudaSetDevice(s->device));
   TS_CUDA(cudaStreamSynchronize(st));
-  if (s->texels) cudaFree(s->texels);
-  s->texels = nullptr;
-  s->tex_version += 1;  // any 2-D atlas built from the old texels is stale
   const long long count = (long long)s->n * T * T * 8;
   const size_t esz = store == TS_F32 ? 4 : 2;
-  TS_CUDA(cudaMalloc(&s->texels, std::max<size_t>((size_t)count * esz, 16)));
-  s->T = T;
-  s->tex_dtype = (int)store;
-  s->tex_n = s->n;
+  UploadBufs b;
+  void* tex = nullptr;
+  float* staging = nullptr;
+  TS_UP(b.alloc(&tex, (size_t)count * esz));
   if (count > 0) {
     if (store == TS_F32) {
-      ts_status r = copy_in(s->texels, texels, (size_t)count * 4, src_on_device, st);
-      if (r != TS_OK) return r;
+      TS_UP(cudaMemcpyAsync(tex, texels, (size_t)count * 4,
+                            src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     } else {
       const float* src = texels;
-      float* staging = nullptr;
       if (!src_on_device) {
-        TS_CUDA(cudaMallocAsync(&staging, (size_t)count * 4, st));
-        TS_CUDA(cudaMemcpyAsync(staging, texels, (size_t)count * 4, cudaMemcpyHostToDevice, st));
+        TS_UP(b.alloc((void**)&staging, (size_t)count * 4));
+        TS_UP(cudaMemcpyAsync(staging, texels, (size_t)count * 4, cudaMemcpyHostToDevice, st));
         src = staging;
       }
       {
         ProfScope p(st, "atlas_pack");
-        launch_pack_texels(src, s->texels, count, (int)store, st);
+        launch_pack_texels(src, tex, count, (int)store, st);
       }
-      TS_CHECK_LAUNCH();
-      if (staging) TS_CUDA(cudaFreeAsync(staging, st));
+      TS_UP(cudaGetLastError());
     }
   }
-  TS_CUDA(cudaStreamSynchronize(st));
+  TS_UP(cudaStreamSynchronize(st));
+  if (s->texels) cudaFree(s->texels);
+  s->texels = tex;
+  s->tex_version += 1;  // any 2-D atlas built from the old texels is stale
+  s->T = T;
+  s->tex_dtype = (int)store;
+  s->tex_n = s->n;
+  if (staging) cudaFree(staging);
+  b.release();
   return TS_OK;
 }
 
@@ -274,42 +347,52 @@ ts_status ts_upload_envmap(ts_scene* s, int levels, int base_res, const float* s
   cudaStream_t st = (cudaStream_t)stream;
   TS_CUDA(cudaSetDevice(s->device));
   TS_CUDA(cudaStreamSynchronize(st));
-  for (void** p : {(void**)&s->spec, (void**)&s->irr, (void**)&s->lut}) {
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-  }
   size_t total = 0;
+  size_t off[MAX_LEVELS];
+  int res[MAX_LEVELS];
   for (int l = 0; l < levels; ++l) {
-    int r = std::max(1, base_res >> l);
-    s->spec_res[l] = r;
-    s->spec_off[l] = total;
-    total += (size_t)6 * r * r * 3;
+    res[l] = std::max(1, base_res >> l);
+    off[l] = total;
+    total += (size_t)6 * res[l] * res[l] * 3;
+  }
+  const size_t esz = store == TS_F32 ? 4 : 2;
+  const size_t irr_n = (size_t)6 * irr_res * irr_res * 3;
+  const size_t lut_b = (size_t)lut_res * lut_res * 2 * sizeof(float);
+  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  UploadBufs b;
+  void *d_spec = nullptr, *d_irr = nullptr;
+  float *d_lut = nullptr, *staging = nullptr;
+  TS_UP(b.alloc(&d_spec, total * esz));
+  TS_UP(b.alloc(&d_irr, irr_n * esz));
+  TS_UP(b.alloc((void**)&d_lut, lut_b));
+  TS_UP(cudaMemcpyAsync(d_lut, lut, lut_b, kind, st));
+  if (store == TS_F32) {
+    TS_UP(cudaMemcpyAsync(d_spec, spec, total * 4, kind, st));
+    TS_UP(cudaMemcpyAsync(d_irr, irr, irr_n * 4, kind, st));
+  } else {
+    TS_UP(b.alloc((void**)&staging, (total + irr_n) * 4));
+    TS_UP(cudaMemcpyAsync(staging, spec, total * 4, kind, st));
+    TS_UP(cudaMemcpyAsync(staging + total, irr, irr_n * 4, kind, st));
+    launch_pack_texels(staging, d_spec, (long long)total, DT_F16, st);
+    launch_pack_texels(staging + total, d_irr, (long long)irr_n, DT_F16, st);
+    TS_UP(cudaGetLastError());
+  }
+  TS_UP(cudaStreamSynchronize(st));
+  for (void* p : {s->spec, s->irr, (void*)s->lut})
+    if (p) cudaFree(p);
+  s->spec = d_spec;
+  s->irr = d_irr;
+  s->lut = d_lut;
+  for (int l = 0; l < levels; ++l) {
+    s->spec_res[l] = res[l];
+    s->spec_off[l] = off[l];
   }
   s->levels = levels;
   s->irr_res = irr_res;
   s->lut_res = lut_res;
   s->cube_dtype = (int)store;
-  const size_t esz = store == TS_F32 ? 4 : 2;
-  const size_t irr_n = (size_t)6 * irr_res * irr_res * 3;
-  TS_CUDA(cudaMalloc(&s->spec, total * esz));
-  TS_CUDA(cudaMalloc(&s->irr, irr_n * esz));
-  TS_CUDA(cudaMalloc((void**)&s->lut, (size_t)lut_res * lut_res * 2 * sizeof(float)));
-  ts_status r = copy_in(s->lut, lut, (size_t)lut_res * lut_res * 2 * sizeof(float), src_on_device, st);
-  if (r != TS_OK) return r;
-  if (store == TS_F32) {
-    if ((r = copy_in(s->spec, spec, total * 4, src_on_device, st)) != TS_OK) return r;
-    if ((r = copy_in(s->irr, irr, irr_n * 4, src_on_device, st)) != TS_OK) return r;
-  } else {
-    float* staging = nullptr;
-    TS_CUDA(cudaMallocAsync(&staging, (total + irr_n) * 4, st));
-    if ((r = copy_in(staging, spec, total * 4, src_on_device, st)) != TS_OK) return r;
-    if ((r = copy_in(staging + total, irr, irr_n * 4, src_on_device, st)) != TS_OK) return r;
-    launch_pack_texels(staging, s->spec, (long long)total, DT_F16, st);
-    launch_pack_texels(staging + total, s->irr, (long long)irr_n, DT_F16, st);
-    TS_CHECK_LAUNCH();
-    TS_CUDA(cudaFreeAsync(staging, st));
-  }
-  TS_CUDA(cudaStreamSynchronize(st));
+  if (staging) cudaFree(staging);
+  b.release();
   return TS_OK;
 }
 
@@ -499,26 +582,30 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   struct HostTail {
     uint32_t tail[2];
     unsigned long long total;
-    int sort_err;
+    int sort_err[2];
   };
   int* d_sort_err = sort_error_flag(device);
+  vt.sort_err = d_sort_err;
   static thread_local HostTail* h_tail = nullptr;
   if (!h_tail) TS_CUDA_K(cudaHostAlloc((void**)&h_tail, sizeof(HostTail), cudaHostAllocPortable));
   h_tail->tail[0] = h_tail->tail[1] = 0;
   h_tail->total = 0;
-  h_tail->sort_err = 0;
-  if (d_sort_err) TS_CUDA_K(cudaMemcpyAsync(&h_tail->sort_err, d_sort_err, 4, cudaMemcpyDeviceToHost, st));
+  h_tail->sort_err[0] = h_tail->sort_err[1] = 0;
+  if (d_sort_err) TS_CUDA_K(cudaMemcpyAsync(h_tail->sort_err, d_sort_err, 8, cudaMemcpyDeviceToHost, st));
   if (n_items > 0) {
     TS_CUDA_K(cudaMemcpyAsync(&h_tail->tail[0], offs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
     TS_CUDA_K(cudaMemcpyAsync(&h_tail->tail[1], cs + (n_items - 1), 4, cudaMemcpyDeviceToHost, st));
     if (d_total) TS_CUDA_K(cudaMemcpyAsync(&h_tail->total, d_total, 8, cudaMemcpyDeviceToHost, st));
   }
   TS_CUDA_K(cudaStreamSynchronize(st));
-  if (h_tail->sort_err) {  // a bounded wait in a sort ran out (this batch or an earlier call)
-    cudaMemsetAsync(d_sort_err, 0, sizeof(int), st);
+  if (h_tail->sort_err[SORT_FLAG_LISTS]) {  // the depth sort's bounded wait ran out (this batch)
+    cudaMemsetAsync(d_sort_err, 0, 2 * sizeof(int), st);
     cleanup_keep();
     return fail(TS_ERR_TIMEOUT, "ts_render_views: a radix-sort look-back wait ran out");
   }
+  // an earlier call's launch-order sort ran out: its rasteriser took the
+  // tiles in tile order (same result); the word is cleared for this call
+  if (h_tail->sort_err[SORT_FLAG_ORDER]) TS_CUDA_K(cudaMemsetAsync(d_sort_err + SORT_FLAG_ORDER, 0, sizeof(int), st));
   const long long K = (long long)h_tail->tail[0] + h_tail->tail[1];
   if (K > INT32_MAX / 2 || (d_total && h_tail->total > (unsigned long long)(INT32_MAX / 2))) {
     cleanup_keep();
@@ -545,14 +632,14 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   int w2 = 0;
   {
     ProfScope p(st, "sort_pairs");
-    w2 = radix_sort_u32(tk0, pi0, tk1, pi1, (int)K, 0, std::max(1, bits_for(vt.n_tiles)), rtemp2, st);
+    w2 = radix_sort_u32(tk0, pi0, tk1, pi1, (int)K, 0, std::max(1, bits_for(vt.n_tiles)), rtemp2, st, -1);
   }
   uint32_t* tkeys = w2 ? tk1 : tk0;
   uint32_t* pitems = w2 ? pi1 : pi0;
   {
     ProfScope p(st, "tile_ranges");
     TS_CUDA_K(cudaMemsetAsync(ranges, 0, (size_t)vt.n_tiles * sizeof(uint2), st));
-    launch_tile_ranges(tkeys, (int)K, ranges, st);
+    launch_tile_ranges(tkeys, (int)K, vt.n_tiles, ranges, st);
     vt.tile_order = launch_tile_order(ranges, vt.n_tiles, obuf, rtemp2, st);
   }
   TS_CHECK_LAUNCH();
@@ -810,7 +897,7 @@ ts_status ts_upload_indirect(ts_scene* s, int degree, const float* coeffs, int s
   const int K = (degree + 1) * (degree + 1);
   const int stride = (3 * K + 3) & ~3;
   const size_t n = (size_t)std::max<int64_t>(s->n, 1);
-  TS_CUDA(cudaMalloc(&s->sh, n * stride * sizeof(float)));
+  TS_CUDA(dev_malloc((void**)&s->sh, n * stride * sizeof(float)));
   TS_CUDA(cudaMemsetAsync(s->sh, 0, n * stride * sizeof(float), st));
   if (s->n > 0)
     TS_CUDA(cudaMemcpy2DAsync(s->sh, stride * sizeof(float), coeffs, 3 * K * sizeof(float), 3 * K * sizeof(float),
@@ -899,7 +986,7 @@ ts_status ts_scene_build_atlas2d(ts_scene* s, ts_dtype store, int packing, void*
       chart_of = reinterpret_cast<uint32_t*>(b + 256 + 4 * seg);
       void* rtemp = b + 256 + 5 * seg;
       launch_morton_order(s->means, s->n, bbox, k0, v0, st);
-      const int w = radix_sort_u32(k0, v0, k1, v1, (int)s->n, 0, 30, rtemp, st);
+      const int w = radix_sort_u32(k0, v0, k1, v1, (int)s->n, 0, 30, rtemp, st, -1);
       launch_chart_of(w ? v1 : v0, s->n, chart_of, st);
     }
   }
@@ -1019,6 +1106,12 @@ ts_status ts_scene_info(const ts_scene* s, int64_t* n, int* T, int* dtype) {
   if (n) *n = s->n;
   if (T) *T = s->T;
   if (dtype) *dtype = s->tex_dtype;
+  return TS_OK;
+}
+
+ts_status ts_debug_fail_alloc(int64_t after) {
+  if (after < -1) return fail(TS_ERR_ARG, "ts_debug_fail_alloc: after must be >= -1");
+  g_fail_alloc.store(after);
   return TS_OK;
 }
 

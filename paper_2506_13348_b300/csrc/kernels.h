@@ -29,8 +29,11 @@ void launch_preprocess_bwd(const ViewTable& vt, const double* g_items, const Gra
 size_t scan_temp_bytes(int n);
 void launch_exclusive_scan(const uint32_t* in, uint32_t* out, int n, void* temp, cudaStream_t st);
 size_t radix_temp_bytes(int n, int key_bytes);  // temporaries of a sort of n keys of key_bytes (4 or 8)
-// Per-device flag set by a sort pass whose bounded look-back wait ran out
-// (device int, 0 while no sort failed); the host reads and clears it.
+// Per-device flags (two device ints, 0 while no sort failed) set when a
+// bounded look-back wait of a sort ran out: word SORT_FLAG_LISTS for the
+// depth sort (and consumers that found an id out of range), word
+// SORT_FLAG_ORDER for the rasterisers' launch-order sorts.  The host reads
+// and clears them.
 int* sort_error_flag(int device);
 int sort_wait_selftest(cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs over key bits [begin_bit, end_bit).
@@ -38,15 +41,19 @@ int sort_wait_selftest(cudaStream_t st);
 // (k0, v0), 1 if in (k1, v1).
 int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
                    void* temp, cudaStream_t st);
+// flag_word: SORT_FLAG_LISTS / SORT_FLAG_ORDER allow the one-kernel-per-pass
+// sort with a bounded wait for n <= 2^18 (a wait that runs out raises that
+// word); -1 always takes the separate histogram / scan / scatter passes,
+// which wait on nothing (the pair and chart-order sorts).
 int radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
-                   void* temp, cudaStream_t st);
+                   void* temp, cudaStream_t st, int flag_word);
 void launch_sum_counts(const uint32_t* counts, int n, unsigned long long* total, cudaStream_t st);
 void launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t* counts_sorted, int n,
                           cudaStream_t st);
 void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_t* offsets,
                        const uint32_t* counts_sorted, const int4* rects, uint32_t* tile_keys,
                        uint32_t* pair_items, int n, cudaStream_t st);
-void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStream_t st);
+void launch_tile_ranges(const uint32_t* tile_keys, int K, int n_tiles, uint2* ranges, cudaStream_t st);
 // Tile launch order, longest list first: buf holds 4 * n words (keys and ids,
 // twice); returns the n sorted tile ids (inside buf).  temp: radix_temp_bytes(n, 4).
 const uint32_t* launch_tile_order(const uint2* ranges, int n, uint32_t* buf, void* temp, cudaStream_t st);
@@ -83,6 +90,9 @@ void launch_activate_bwd(const float* s, const float* o, const float* gs, const 
                          float* g_log_s, float* g_logit_o, int accumulate, cudaStream_t st);
 void launch_pack_f16(const float* src, __half* dst, long long n, cudaStream_t st);
 void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStream_t st);
+// out: 3 device words, initialised to {0, 0xffffffff, 0} by the caller
+void launch_validate_gaussians(const float4* means, const float4* quats, const float2* scales, const float* opac,
+                               long long n, unsigned* out, cudaStream_t st);
 void launch_l1_loss(const float4* rgba, const float4* target, long long n, float* loss, float4* grad,
                     cudaStream_t st);
 

@@ -1,4 +1,5 @@
 // Upload-time packing and the L1 image loss.
+#include <algorithm>
 #include "kernels.h"
 #include "prof.h"
 
@@ -77,6 +78,42 @@ __global__ void k_pad4(const float* __restrict__ src, int comps, float4* __restr
 void launch_pad4(const float* src, int comps, float4* dst, long long n, cudaStream_t st) {
   if (n > 0) {
     k_pad4<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, comps, dst, n);
+    note_launches(1);
+  }
+}
+
+// Upload check of the splat parameters the renderer divides by or
+// normalises: finite centres, a quaternion with finite components and a
+// squared norm of at least 1e-20 (it is normalised), finite scales > 0
+// (the intersection divides by them), opacity in [0, 1].  out[0] counts the
+// bad splats, out[1] is the smallest bad index, out[2] ORs the reasons
+// (1 centre, 2 quaternion, 4 scale, 8 opacity).
+__global__ void k_validate_gaussians(const float4* __restrict__ means, const float4* __restrict__ quats,
+                                     const float2* __restrict__ scales, const float* __restrict__ opac, long long n,
+                                     unsigned* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float4 p = means[i], q = quats[i];
+    const float2 s = scales[i];
+    const float o = opac[i];
+    unsigned why = 0;
+    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) why |= 1u;
+    const float q2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    if (!(isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w)) || !(q2 >= 1e-20f)) why |= 2u;
+    if (!(isfinite(s.x) && isfinite(s.y) && s.x > 0.f && s.y > 0.f)) why |= 4u;
+    if (!(o >= 0.f && o <= 1.f)) why |= 8u;
+    if (why) {
+      atomicAdd(out, 1u);
+      atomicMin(out + 1, (unsigned)min(i, 0xfffffffell));
+      atomicOr(out + 2, why);
+    }
+  }
+}
+
+void launch_validate_gaussians(const float4* means, const float4* quats, const float2* scales, const float* opac,
+                               long long n, unsigned* out, cudaStream_t st) {
+  if (n > 0) {
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 148 * 8);
+    k_validate_gaussians<<<blocks, 256, 0, st>>>(means, quats, scales, opac, n, out);
     note_launches(1);
   }
 }

@@ -164,13 +164,28 @@ extern "C" ts_status ts_render_noalloc(int64_t n, const float* means, const floa
   uint32_t* order = which ? ids1 : ids0;
   launch_gather_counts(order, counts, cs, (int)n, st);
   launch_exclusive_scan(cs, offs, (int)n, temp, st);
+  // one synchronisation: the pair count and the sort flags (their device
+  // words are module variables too, so reading them allocates nothing)
+  int* d_flags = sort_error_flag(dev);
+  if (!d_flags) return na_fail(TS_ERR_CUDA, "ts_render_noalloc: sort flag lookup failed");
+  vt.sort_err = d_flags;
   uint32_t tail[2] = {0, 0};
+  int flags[2] = {0, 0};
+  e = cudaMemcpyAsync(flags, d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st);
   if (n > 0) {
-    e = cudaMemcpyAsync(&tail[0], offs + (n - 1), 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tail[0], offs + (n - 1), 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&tail[1], cs + (n - 1), 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess)
-      return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: pair count: ") + cudaGetErrorString(e));
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: pair count: ") + cudaGetErrorString(e));
+  if (flags[SORT_FLAG_LISTS]) {  // the depth sort's bounded wait ran out: the lists are not trusted
+    cudaMemsetAsync(d_flags, 0, sizeof(flags), st);
+    return na_fail(TS_ERR_TIMEOUT, "ts_render_noalloc: a radix-sort look-back wait ran out");
+  }
+  if (flags[SORT_FLAG_ORDER]) {  // an earlier call's launch order (same result either way)
+    e = cudaMemsetAsync(d_flags + SORT_FLAG_ORDER, 0, sizeof(int), st);
+    if (e != cudaSuccess) return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: ") + cudaGetErrorString(e));
   }
   const long long K = (long long)tail[0] + tail[1];
   if (K > NA_MAX_PAIRS) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: more than 1048576 (tile, splat) pairs");
@@ -178,12 +193,12 @@ extern "C" ts_status ts_render_noalloc(int64_t n, const float* means, const floa
   launch_emit_pairs(vt, order, offs, cs, rects, tk0, pi0, (int)n, st);
   int tb = 1;
   while ((1ll << tb) < vt.n_tiles) ++tb;
-  const int w2 = radix_sort_u32(tk0, pi0, tk1, pi1, (int)K, 0, tb, temp, st);
+  const int w2 = radix_sort_u32(tk0, pi0, tk1, pi1, (int)K, 0, tb, temp, st, -1);
   uint32_t* tkeys = w2 ? tk1 : tk0;
   uint32_t* pitems = w2 ? pi1 : pi0;
   e = cudaMemsetAsync(ranges, 0, (size_t)vt.n_tiles * sizeof(uint2), st);
   if (e != cudaSuccess) return na_fail(TS_ERR_CUDA, std::string("ts_render_noalloc: ") + cudaGetErrorString(e));
-  launch_tile_ranges(tkeys, (int)K, ranges, st);
+  launch_tile_ranges(tkeys, (int)K, vt.n_tiles, ranges, st);
   // tile launch order in the pair-key buffer the sort left free (4 x tiles <= pairs capacity)
   static_assert(4 * NA_MAX_TILES <= NA_MAX_PAIRS, "tile order buffer");
   if (radix_temp_bytes(vt.n_tiles, 4) > TEMP_BYTES) return na_fail(TS_ERR_CAPACITY, "ts_render_noalloc: sort temporaries");

@@ -250,10 +250,19 @@ __device__ __forceinline__ float3 sh_grad_dir(float3 w, int K, const float s[9])
 constexpr int kRasterWarps = 4;
 constexpr int kCtasPerTile = 8 / kRasterWarps;
 
-// the tile of this CTA (in launch order) and the 8 x 4 block of this warp
+// the tile of this CTA (in launch order) and the 8 x 4 block of this warp;
+// a launch order whose sort's bounded wait ran out is not used (the tiles
+// are then taken in tile order, which changes no result)
 __device__ __forceinline__ int raster_tile(const ViewTable& vt) {
   const int b = (int)blockIdx.x / kCtasPerTile;
-  return vt.tile_order ? (int)vt.tile_order[b] : b;
+  if (!vt.tile_order || (vt.sort_err && __ldcg(vt.sort_err + SORT_FLAG_ORDER))) return b;
+  return (int)vt.tile_order[b];
+}
+// the key lists may be wrong (a bounded wait of the depth sort ran out, or a
+// consumer of its order found an id out of range): the forward then writes
+// NaN to its pixels and the backward adds nothing
+__device__ __forceinline__ bool lists_failed(const ViewTable& vt) {
+  return vt.sort_err && __ldcg(vt.sort_err + SORT_FLAG_LISTS);
 }
 __device__ __forceinline__ int raster_block() {
   return ((int)blockIdx.x % kCtasPerTile) * kRasterWarps + (int)(threadIdx.x >> 5);

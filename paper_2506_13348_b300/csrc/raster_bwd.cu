@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(32 * kRasterWarps, ((FEAT & FEAT_IND) ? 2 : 3)
   const int warp = threadIdx.x >> 5;
   const int tile = raster_tile(vt);
   if ((unsigned)tile >= (unsigned)vt.n_tiles) return;  // an order from a failed sort (flag set)
+  if (lists_failed(vt)) return;                        // the forward marked the image invalid
   const int v = find_view(vt, tile);
   const ViewDesc& V = vt.v[v];
   int px, py;

@@ -43,6 +43,11 @@ __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_
   int px, py;
   pixel_of(tile - V.tile_off, V.tiles_x, raster_block(), px, py);
   const bool inside = px < V.W && py < V.H;
+  if (lists_failed(vt)) {  // reported by the host; the image is marked invalid
+    if (inside) V.rgba[py * V.W + px] = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
+                                                    __int_as_float(0x7fffffff), __int_as_float(0x7fffffff));
+    return;
+  }
   const float xp = (float)px + 0.5f - V.cx;
   const float yp = (float)py + 0.5f - V.cy;
   const uint2 range = ranges[tile];

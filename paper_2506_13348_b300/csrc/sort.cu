@@ -468,10 +468,13 @@ static size_t os_layout(int n, int nbits, size_t* status_off, size_t* ticket_off
   return ghist + status + 256;
 }
 
-// The flag is a module variable (static device memory, one per device
-// context, zero at load): taking it allocates nothing, which the
-// no-allocation render relies on.
-__device__ int g_sort_err_flag;
+// The flags are a module variable (static device memory, one per device
+// context, zero at load): taking them allocates nothing, which the
+// no-allocation render relies on.  Word SORT_FLAG_LISTS: the depth order or
+// a list derived from it may be wrong; word SORT_FLAG_ORDER: a rasteriser
+// launch order may be wrong (the rasterisers then take the tiles in tile
+// order, which changes no result).
+__device__ int g_sort_err_flag[2];
 
 namespace {
 std::mutex g_err_mu;
@@ -483,7 +486,7 @@ int* sort_error_flag(int device) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   if (!g_sort_err[device]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_sort_err_flag) != cudaSuccess) return nullptr;
+    if (cudaGetSymbolAddress(&p, g_sort_err_flag) != cudaSuccess) return nullptr;  // the address of word 0
     g_sort_err[device] = static_cast<int*>(p);
   }
   return g_sort_err[device];
@@ -525,7 +528,7 @@ int sort_wait_selftest(cudaStream_t st) {
 
 template <typename K, int R>
 static int radix_sort_os(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
-                         cudaStream_t st) {
+                         cudaStream_t st, int flag_word) {
   if (n <= 1 || end_bit <= begin_bit) return 0;
   const SortPlan pl = sort_plan(begin_bit, end_bit);
   size_t status_off, ticket_off;
@@ -537,7 +540,7 @@ static int radix_sort_os(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int be
   uint32_t* tickets = reinterpret_cast<uint32_t*>(t + ticket_off);
   int dev = 0;
   cudaGetDevice(&dev);
-  int* err = sort_error_flag(dev);
+  int* err = sort_error_flag(dev) + flag_word;
   cudaMemsetAsync(temp, 0, bytes, st);
   k_os_hist<K, R><<<nb, RS_THREADS, 0, st>>>(k0, n, pl.begin, pl.step, pl.end, pl.passes, ghist);
   note_launches(1);
@@ -596,30 +599,35 @@ static int radix_sort_r(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int beg
   return cur;
 }
 
-template <typename K>
-static int radix_sort(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int n, int begin_bit, int end_bit, void* temp,
-                      cudaStream_t st) {
-  if (n <= RS_SMALL_N) return radix_sort_os<K, 4>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
-  return radix_sort_r<K, 16>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
-}
-
 int radix_sort_u64(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
                    void* temp, cudaStream_t st) {
   // the per-splat depth sort: one kernel per pass at every size (at 12 M keys
   // 1.19 -> 0.98 ms against separate histogram / scan / scatter passes)
-  if (n <= RS_SMALL_N) return radix_sort_os<uint64_t, 4>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
-  return radix_sort_os<uint64_t, 8>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
+  if (n <= RS_SMALL_N)
+    return radix_sort_os<uint64_t, 4>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st, SORT_FLAG_LISTS);
+  return radix_sort_os<uint64_t, 8>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st, SORT_FLAG_LISTS);
 }
 int radix_sort_u32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int n, int begin_bit, int end_bit,
-                   void* temp, cudaStream_t st) {
-  return radix_sort<uint32_t>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
+                   void* temp, cudaStream_t st, int flag_word) {
+  if (flag_word >= 0 && n <= RS_SMALL_N)
+    return radix_sort_os<uint32_t, 4>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st, flag_word);
+  return radix_sort_r<uint32_t, 16>(k0, v0, k1, v1, n, begin_bit, end_bit, temp, st);
 }
 
 // ---------------------------------------------------------------------------
+// counts in depth order; an id out of range (only after a depth sort whose
+// bounded wait ran out, which set the flag the host reads next) counts 0
 __global__ void k_gather_counts(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
-                                uint32_t* __restrict__ out, int n) {
+                                uint32_t* __restrict__ out, int n, int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = counts[order[i]];
+  if (i >= n) return;
+  const uint32_t o = order[i];
+  if (o < (uint32_t)n) {
+    out[i] = counts[o];
+  } else {
+    out[i] = 0u;
+    if (err) atomicExch(err + SORT_FLAG_LISTS, 1);
+  }
 }
 
 // 64-bit total of the per-splat pair counts (the 32-bit scan would wrap past
@@ -653,7 +661,9 @@ void launch_sum_counts(const uint32_t* counts, int n, unsigned long long* total,
 void launch_gather_counts(const uint32_t* order, const uint32_t* counts, uint32_t* counts_sorted, int n,
                           cudaStream_t st) {
   if (n > 0) {
-    k_gather_counts<<<ceil_div(n, 256), 256, 0, st>>>(order, counts, counts_sorted, n);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    k_gather_counts<<<ceil_div(n, 256), 256, 0, st>>>(order, counts, counts_sorted, n, sort_error_flag(dev));
     note_launches(1);
   }
 }
@@ -676,6 +686,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(ViewTable vt, const uint32_t
   uint32_t my_cnt = 0, my_item = 0, my_t0 = 0, my_w = 1, my_base = 0;
   if (my < n) {
     my_cnt = counts_sorted[my];
+    if (my_cnt && order[my] >= (uint32_t)n) my_cnt = 0;  // see k_gather_counts: never, with the flag clear
     if (my_cnt) {
       my_item = order[my];
       const int4 rc = rects[my_item];
@@ -730,7 +741,10 @@ void launch_emit_pairs(const ViewTable& vt, const uint32_t* order, const uint32_
 // Tile ranges from the sorted tile ids: 4 keys per thread (one 16-byte
 // load plus the neighbours at both ends), a range boundary wherever the id
 // changes.
-__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int K, uint2* __restrict__ ranges) {
+// A tile id out of range is skipped and raises the list flag (it cannot occur
+// with the stable pair sort, which has no bounded wait).
+__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int K, int n_tiles, uint2* __restrict__ ranges,
+                              int* __restrict__ err) {
   const long long i0 = 4ll * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
   if (i0 >= K) return;
   uint32_t k[6];
@@ -748,15 +762,21 @@ __global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int K, uint2* _
     const long long i = i0 + j;
     if (i >= K) break;
     const uint32_t t = k[1 + j];
+    if (t >= (uint32_t)n_tiles) {
+      if (err) atomicExch(err + SORT_FLAG_LISTS, 1);
+      continue;
+    }
     if (i == 0 || k[j] != t) ranges[t].x = (uint32_t)i;
     if (i == K - 1 || k[2 + j] != t) ranges[t].y = (uint32_t)(i + 1);
   }
 }
 
-void launch_tile_ranges(const uint32_t* tile_keys, int K, uint2* ranges, cudaStream_t st) {
+void launch_tile_ranges(const uint32_t* tile_keys, int K, int n_tiles, uint2* ranges, cudaStream_t st) {
   if (K > 0) {
     const int threads = (int)((K + 3) / 4);
-    k_tile_ranges<<<ceil_div(threads, 256), 256, 0, st>>>(tile_keys, K, ranges);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    k_tile_ranges<<<ceil_div(threads, 256), 256, 0, st>>>(tile_keys, K, n_tiles, ranges, sort_error_flag(dev));
     note_launches(1);
   }
 }
@@ -817,7 +837,7 @@ const uint32_t* launch_tile_order_walk(const ViewTable& vt, const uint2* ranges,
   if (n <= 0) return buf + n;
   k_tile_walk_keys<<<n, 256, 0, st>>>(vt, ranges, buf, buf + n);
   note_launches(1);
-  const int w = radix_sort_u32(buf, buf + n, buf + 2 * n, buf + 3 * n, n, 0, 8, temp, st);
+  const int w = radix_sort_u32(buf, buf + n, buf + 2 * n, buf + 3 * n, n, 0, 8, temp, st, SORT_FLAG_ORDER);
   return w ? buf + 3 * n : buf + n;
 }
 
@@ -825,7 +845,7 @@ const uint32_t* launch_tile_order(const uint2* ranges, int n, uint32_t* buf, voi
   if (n <= 0) return buf + n;
   k_tile_order_keys<<<ceil_div(n, 256), 256, 0, st>>>(ranges, n, buf, buf + n);
   note_launches(1);
-  const int w = radix_sort_u32(buf, buf + n, buf + 2 * n, buf + 3 * n, n, 0, 8, temp, st);
+  const int w = radix_sort_u32(buf, buf + n, buf + 2 * n, buf + 3 * n, n, 0, 8, temp, st, SORT_FLAG_ORDER);
   return w ? buf + 3 * n : buf + n;
 }
 

@@ -38,6 +38,9 @@ constexpr int kRecGradStride = 14;
 
 enum Dtype : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2 };
 
+// Words of the per-device sort error flags (see sort_error_flag).
+enum SortFlag : int { SORT_FLAG_LISTS = 0, SORT_FLAG_ORDER = 1 };
+
 // Texture sampler of the forward rasteriser.
 //   SMP_SOFTWARE: bilinear filter (Eq. 6) in FP32 from the per-splat chart layout;
 //   SMP_HW_ATLAS: tex2D on 2-D hardware-texture atlases (supplementary Sec. 1);
@@ -115,6 +118,8 @@ struct ViewTable {
   // the rasterisers' tiles in launch order (CTA b takes tile tile_order[b]),
   // or NULL for tile order
   const uint32_t* tile_order;
+  // the sort error flags (two words, see SortFlag), or NULL
+  const int* sort_err;
   ViewDesc v[MAX_VIEWS];
 };
 

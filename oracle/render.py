@@ -246,6 +246,9 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
         out["n_contrib"] = blended.sum(1)
         # index (within the list) of the last blended fragment, -1 if none
         out["last"] = base["last"]
+        # per-fragment local coordinates, unclamped opacity and orientation
+        # (for tests that compare discrete states of two evaluations)
+        out["u"], out["v"], out["oG"], out["flip"] = u.detach(), v.detach(), oG.detach(), flip
         if margins is not None:
             m_uv, m_a, m_t, m_f = margins
             oG_full = op * torch.exp(-(u * u + v * v).clamp(max=1e4) / 2.0)

@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpix/s fwd+bwd at 200k splats 800²; served-view p50/p99 latency vs plain"
 UNIT = "Mpix/s"
 N_SPLATS, T_TEX, RES, N_CAMS = 200_000, 8, 800, 100
+PREC_TILES = 16  # seeded covered 16x16 tiles (4096 px) per error view scored against the FP64 oracle
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 # FP32 operations per fragment of the algorithm (FMA = 2): every evaluated
@@ -384,8 +385,10 @@ def run_ours(args):
         line["serving"] = run_serving(args, local)
     if rank == 0 and not args.no_large:
         line["large_scene"] = run_large_scene(args, local)
+    prec_inputs = None
     if rank == 0 and not args.no_precision:
         line["precision"] = run_precision(args, local)
+        prec_inputs = line["precision"].pop("_oracle_inputs")
     if rank == 0 and not args.no_sampling:
         line["texture_sampling"] = run_sampling(args, local)
     if rank == 0 and not args.no_features:
@@ -396,6 +399,8 @@ def run_ours(args):
                                 "sample": f"{args.cpu_tiles} random non-empty 16x16 tiles ({px} px) of one 800x800 view, "
                                           f"FP64 forward + autograd backward, {dt:.1f} s"}
         line["parity_sample"] = parity_sample(scene, env, my_cams[0], tiles, kl, par_img)
+        if prec_inputs is not None:
+            line["precision"]["vs_fp64_oracle"] = precision_vs_oracle(prec_inputs)
     if rank == 0:
         print(json.dumps(line))
     if pg:
@@ -528,6 +533,12 @@ def run_precision(args, device):
     err_views = (0, 5)
     out = {"workload": "cfg2: 500k splats, 16x16 texels x 8 ch, 1920x1080, 6-level 128 FP16 cube, 10 views",
            "error_reference": "images of views 0 and 5 (RGB, every pixel) rendered from the f32 atlas"}
+    # seeded samples of the error views -- PREC_TILES whole 16x16 tiles among
+    # those the image covers -- scored against the FP64 oracle (fed the
+    # float32 texels) in the CPU-baseline leg
+    srng = np.random.default_rng(7)
+    samp = {}
+    got = {}
     img = torch.empty(H, W, 4, device=dev)
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
@@ -544,6 +555,19 @@ def run_precision(args, device):
         errs = []
         for ci in err_views:
             P.render(sc, cams[ci], out=img)
+            if ci not in samp:
+                tx_n, ty_n = (W + 15) // 16, (H + 15) // 16
+                a = torch.nn.functional.pad(img[..., 3], (0, tx_n * 16 - W, 0, ty_n * 16 - H))
+                cov = (a.reshape(ty_n, 16, tx_n, 16).amax(dim=(1, 3)) > 0).flatten().cpu().numpy()
+                tiles = np.sort(srng.choice(np.nonzero(cov)[0], size=PREC_TILES, replace=False))
+                ys, xs = np.divmod(tiles, tx_n)
+                gy, gx = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+                px_ = (xs[:, None] * 16 + gx.ravel()[None]).ravel()
+                py_ = (ys[:, None] * 16 + gy.ravel()[None]).ravel()
+                keep = (px_ < W) & (py_ < H)
+                samp[ci] = (tiles, px_[keep], py_[keep])
+            _, px_, py_ = samp[ci]
+            got[(store, ci)] = img[torch.from_numpy(py_).to(dev), torch.from_numpy(px_).to(dev)].cpu().numpy()
             if store == "f32":
                 ref_imgs[ci] = img[..., :3].clone()
             else:
@@ -571,9 +595,50 @@ def run_precision(args, device):
                        psnr_db=float(10 * np.log10(1.0 / mse)) if mse > 0 else None)
         out[store] = res
         sc.close()
+    out["_oracle_inputs"] = dict(geo=geo, tex=tex.cpu().numpy(), env=env, cams=[cams[ci] for ci in err_views],
+                                 views=list(err_views), samples=samp, got=got)
     del tex, ref_imgs
     torch.cuda.empty_cache()
     return out
+
+
+def precision_vs_oracle(inp):
+    """Each reduced-precision image's error against the FP64 oracle fed the
+    float32 texels (the storage error), on PREC_TILES seeded whole tiles of
+    each error view: max-abs, mean-abs and PSNR over RGB.  The f32 row is
+    the renderer's own error against the oracle.  Pixels with several
+    threshold decisions within FP32 error are left out (counted); where one
+    decision is, the nearer admissible oracle result is used."""
+    import numpy as np
+
+    from oracle import keys as K
+    from oracle import render as R
+    geo, tex, env = inp["geo"], inp["tex"], inp["env"]
+    env16 = dict(env, spec=[m.astype(np.float16).astype(np.float32) for m in env["spec"]],
+                 irr=env["irr"].astype(np.float16).astype(np.float32))
+    scene = dict(geo, texels=tex, T=tex.shape[1])
+    res = {"tiles_per_view": PREC_TILES, "reference": "FP64 oracle, float32 texels, the FP16 cube the renderer reads; "
+                                                       "RGB of every pixel of seeded covered 16x16 tiles"}
+    t0 = time.perf_counter()
+    params, envp = R.to_params(scene), R.env_params(env16)
+    for ci, cam in zip(inp["views"], inp["cams"]):
+        kl = K.build_keys(scene, cam)
+        tiles, px, py = inp["samples"][ci]
+        ref = R.render(scene, cam, env16, params=params, envp=envp, tiles=tiles, keylist=kl)
+        r, a = ref["rgba"].detach().numpy()[py, px], ref["alt"]["rgba"].numpy()[py, px]
+        amb = ref["ambiguous"].numpy()[py, px]
+        row = {"pixels": int(px.size), "masked": int(amb.sum())}
+        for store in ("f32", "bf16", "f16"):
+            g = inp["got"][(store, ci)].astype(np.float64)
+            e0, e1 = (g - r)[..., :3], (g - a)[..., :3]
+            pick = (np.abs(e0).max(-1) <= np.abs(e1).max(-1))[:, None]
+            e = np.where(pick, e0, e1)[~amb]
+            mse = float((e * e).mean())
+            row[store] = {"max_abs_err": float(np.abs(e).max()), "mean_abs_err": float(np.abs(e).mean()),
+                          "psnr_db": float(10 * np.log10(1.0 / mse)) if mse > 0 else None}
+        res[f"view{ci}"] = row
+    res["oracle_seconds"] = time.perf_counter() - t0
+    return res
 
 
 def run_large_scene(args, device):
@@ -1033,6 +1098,9 @@ def main():
             res["large_scene"] = run_large_scene(args, dist_env()[2])
         if args.precision_only:
             res["precision"] = run_precision(args, dist_env()[2])
+            inp = res["precision"].pop("_oracle_inputs")
+            if not args.no_cpu_baseline:
+                res["precision"]["vs_fp64_oracle"] = precision_vs_oracle(inp)
         if args.sampling_only:
             res["texture_sampling"] = run_sampling(args, dist_env()[2])
         if args.features_only:

@@ -372,13 +372,25 @@ typedef struct ts_serve_stats {
   double mean_ms;
   double fps;             /* completed views / (last completion - first submission) */
   double mpix_per_s;
+  int64_t true_ups;       /* batches whose counted pairs needed more memory than their estimate */
+  int64_t over_budget;    /* of those, batches that went past the budget because waiting could not end */
+  double peak_reserved_bytes;  /* largest memory reservation held at once (outputs + render buffers) */
 } ts_serve_stats;
 
 /* Starts a view server on `device` with n_streams worker threads (one CUDA
  * stream each, 1..16), batches of at most max_batch views (1..32), and a
- * device-memory budget of arena_bytes for requests in flight (outputs plus
- * estimated binning memory).  Scenes stay resident: requests name a scene
- * created and uploaded beforehand; it must outlive its requests. */
+ * device-memory budget of arena_bytes (> 0) for requests in flight.  A
+ * request is admitted with its output, the render's exact per-splat
+ * buffers and an estimate of its (tile, splat) pair buffers -- pairs per
+ * pixel learned per scene as the largest value its renders showed, 32
+ * before the first.  When the batch has counted its pairs (the render's one
+ * synchronisation) its reservation is trued up to the exact bytes it still
+ * allocates: a surplus is returned at once, a deficit waits for running
+ * batches to free memory (if every running batch is waiting, it proceeds and
+ * is counted in over_budget, since memory held by uncollected results can
+ * only come back through ts_server_wait); a batch that alone exceeds the
+ * budget fails with TS_ERR_CAPACITY.  Scenes stay resident: requests name a
+ * scene created and uploaded beforehand; it must outlive its requests. */
 ts_status ts_server_create(ts_server** out, int device, size_t arena_bytes, int n_streams, int max_batch);
 
 /* Stops the workers (queued requests are dropped) and frees everything. */
@@ -401,6 +413,20 @@ ts_status ts_server_wait(ts_server* server, uint64_t ticket, float* out_rgba, in
 
 /* Latency / throughput counters since creation or the last reset. */
 ts_status ts_server_stats(ts_server* server, ts_serve_stats* out);
+
+/* The bytes a request for `scene` and `cam` would be admitted with now
+ * (output, the render's per-splat buffers, the current pair estimate). */
+ts_status ts_server_request_bytes(ts_server* server, ts_scene* scene, const ts_camera* cam, size_t* bytes);
+
+/* The device-time interval of each of the last batches (at most
+ * max_entries, oldest first, up to 4096 kept since the last reset): the
+ * worker that ran it, its view count and its start / end in ms on the GPU
+ * clock, measured by CUDA events on the worker's stream against an event
+ * recorded when the server was created.  Intervals of different workers
+ * that intersect ran on the device at the same time.  *n_out receives the
+ * count.  TS_ERR_ARG for NULL outputs. */
+ts_status ts_server_batch_log(ts_server* server, int32_t max_entries, int32_t* n_out, int32_t* worker,
+                              int32_t* views, double* t0_ms, double* t1_ms);
 ts_status ts_server_reset_stats(ts_server* server);
 
 /* ---- training helpers --------------------------------------------------------- */

@@ -28,7 +28,8 @@ EXPORTED = [
     "ts_adam_update", "ts_measure_fp32_peak", "ts_scene_build_atlas2d", "ts_scene_set_sampler",
     "ts_image_loss", "ts_saved_copy_depth", "ts_normal_loss", "ts_upload_indirect",
     "ts_scene_set_normal_encoding", "ts_scene_envmap", "ts_activate", "ts_activate_backward",
-    "ts_selftest_sort_wait", "ts_debug_fail_alloc",
+    "ts_selftest_sort_wait", "ts_debug_fail_alloc", "ts_server_batch_log",
+    "ts_server_request_bytes",
 ]
 
 
@@ -51,7 +52,8 @@ class TsServeStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
                 ("failed", C.c_int64), ("batches", C.c_int64), ("mean_batch", C.c_double),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double), ("fps", C.c_double),
-                ("mpix_per_s", C.c_double)]
+                ("mpix_per_s", C.c_double), ("true_ups", C.c_int64), ("over_budget", C.c_int64),
+                ("peak_reserved_bytes", C.c_double)]
 
 
 class TsAdam(C.Structure):
@@ -113,6 +115,8 @@ def lib() -> C.CDLL:
         "ts_activate_backward": [i64, vp, vp, vp, vp, vp, vp, i32, vp],
         "ts_selftest_sort_wait": [i32, vp],
         "ts_debug_fail_alloc": [i64],
+        "ts_server_batch_log": [vp, i32, C.POINTER(i32), vp, vp, vp, vp],
+        "ts_server_request_bytes": [vp, vp, C.POINTER(TsCamera), C.POINTER(C.c_size_t)],
         "ts_image_loss": [vp, vp, i32, i32, C.c_float, vp, vp, vp],
         "ts_saved_copy_depth": [vp, i32, vp, vp, vp],
         "ts_normal_loss": [vp, i32, C.c_float, vp, vp],

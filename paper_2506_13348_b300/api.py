@@ -396,6 +396,27 @@ class Server:
     def reset_stats(self):
         check(lib().ts_server_reset_stats(self.handle), "ts_server_reset_stats")
 
+    def request_bytes(self, scene: Scene, cam: dict) -> int:
+        """The bytes a request would be admitted with now."""
+        c = make_camera(cam)
+        b = C.c_size_t()
+        check(lib().ts_server_request_bytes(self.handle, scene.handle, C.byref(c), C.byref(b)),
+              "ts_server_request_bytes")
+        return b.value
+
+    def batch_log(self, max_entries: int = 4096) -> list:
+        """[(worker, views, t0_ms, t1_ms)] of the last batches, oldest first
+        (device-time intervals, see ts_server_batch_log)."""
+        import numpy as np
+        w = np.zeros(max_entries, np.int32)
+        v = np.zeros(max_entries, np.int32)
+        t0 = np.zeros(max_entries, np.float64)
+        t1 = np.zeros(max_entries, np.float64)
+        n = C.c_int32()
+        check(lib().ts_server_batch_log(self.handle, max_entries, C.byref(n), w.ctypes.data, v.ctypes.data,
+                                        t0.ctypes.data, t1.ctypes.data), "ts_server_batch_log")
+        return [(int(w[i]), int(v[i]), float(t0[i]), float(t1[i])) for i in range(n.value)]
+
 
 def adam_update(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int,
                 lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, shadow_ptr: int = 0,

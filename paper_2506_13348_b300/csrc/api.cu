@@ -427,8 +427,19 @@ static ts_status check_cam(const ts_camera* c) {
   return TS_OK;
 }
 
-ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_views, float* const* out_rgba,
-                          ts_saved** saved_out, void* stream) {
+}  // extern "C"
+
+// Device bytes ts_render_views allocates before its synchronisation for a
+// batch of n_items (view, splat) items: records, counts, ids, offsets,
+// depth keys, tile rectangles and the sort / scan temporaries.
+size_t ts::render_views_fixed_bytes(long long n_items) {
+  const size_t ni = (size_t)std::max<long long>(n_items, 1);
+  const size_t rt = std::max(radix_temp_bytes((int)ni, 8), scan_temp_bytes((int)ni));
+  return ni * (sizeof(Record) + 5 * 4 + 2 * 8 + sizeof(int4)) + rt + 8 * 256;
+}
+
+ts_status ts::render_views_hooked(ts_scene* const* scenes, const ts_camera* cams, int n_views, float* const* out_rgba,
+                                  ts_saved** saved_out, void* stream, ReserveFn reserve, void* ctx) {
   if (!scenes || !cams || !out_rgba) return fail(TS_ERR_ARG, "ts_render_views: NULL argument");
   if (n_views < 1 || n_views > MAX_VIEWS) return fail(TS_ERR_ARG, "ts_render_views: n_views out of [1, 32]");
   const int device = scenes[0] ? scenes[0]->device : 0;
@@ -484,6 +495,7 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     V.n_splats = (int)s->n;
     V.means = s->means; V.quats = s->quats; V.scales = s->scales; V.opacity = s->opacity;
     V.texels = s->texels; V.T = s->T; V.tex_dtype = s->tex_dtype;
+    V.tex_v8 = s->tex_dtype == DT_F32 && (reinterpret_cast<uintptr_t>(s->texels) & 31) == 0;
     V.atlas2d[0] = s->a2d_tex[0];
     V.atlas2d[1] = s->a2d_tex[1];
     V.chart = s->chart;
@@ -611,6 +623,16 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
     cleanup_keep();
     return fail(TS_ERR_CAPACITY, "ts_render_views: too many (tile, splat) pairs");
   }
+  if (reserve) {  // the caller admits the rest of the call's memory now that K is known
+    size_t rest = (size_t)std::max<long long>(K, 1) * 16 + (size_t)vt.n_tiles * (8 + 16) +
+                  std::max(radix_temp_bytes((int)K, 4), radix_temp_bytes(vt.n_tiles, 4)) + 8 * 256;
+    if (saved_out) rest += (size_t)pixels * (32 + 4 + 4 + 4 + 4 + (indirect ? 16 : 0));
+    const ts_status r = reserve(ctx, rest, K);
+    if (r != TS_OK) {
+      cleanup_keep();
+      return r;
+    }
+  }
 
   // ---- pairs: emit in depth order, stable sort by tile --------------------------
   uint32_t *tk0 = nullptr, *tk1 = nullptr, *pi0 = nullptr, *pi1 = nullptr;
@@ -686,6 +708,13 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
   }
   return TS_OK;
 #undef TS_CUDA_K
+}
+
+extern "C" {
+
+ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_views, float* const* out_rgba,
+                          ts_saved** saved_out, void* stream) {
+  return ts::render_views_hooked(scenes, cams, n_views, out_rgba, saved_out, stream, nullptr, nullptr);
 }
 
 ts_status ts_render(ts_scene* scene, const ts_camera* cam, float* out_rgba, ts_saved** saved, void* stream) {

@@ -19,6 +19,24 @@ struct GradTable {
 
 // api.cu: records the message returned by ts_last_error() and returns code
 int set_error(int code, const std::string& msg);
+}  // namespace ts
+
+struct ts_scene;
+struct ts_camera;
+struct ts_saved;
+
+namespace ts {
+// api.cu: ts_render_views with an admission hook.  After its one
+// synchronisation, once the batch's pair count K is known and before any
+// per-pair buffer is allocated, reserve(ctx, bytes, K) is called with the
+// device bytes the rest of the call allocates; a status other than TS_OK
+// ends the call with that status (nothing of the batch is left allocated).
+typedef int (*ReserveFn)(void* ctx, size_t bytes, long long pairs);
+int render_views_hooked(ts_scene* const* scenes, const ts_camera* cams, int n_views, float* const* out_rgba,
+                        ts_saved** saved_out, void* stream, ReserveFn reserve, void* ctx);
+// Device bytes ts_render_views allocates before that synchronisation for
+// n_items (view, splat) items.
+size_t render_views_fixed_bytes(long long n_items);
 
 // preprocess.cu
 void launch_preprocess(const ViewTable& vt, Record* rec, uint32_t* counts, uint64_t* depth_keys,

@@ -124,6 +124,7 @@ extern "C" ts_status ts_render_noalloc(int64_t n, const float* means, const floa
   V.texels = texels;
   V.T = T;
   V.tex_dtype = DT_F32;
+  V.tex_v8 = (reinterpret_cast<uintptr_t>(texels) & 31) == 0;
   size_t off = 0;
   for (int l = 0; l < levels; ++l) {
     const int r = base_res >> l > 0 ? base_res >> l : 1;

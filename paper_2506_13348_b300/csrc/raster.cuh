@@ -73,6 +73,10 @@ struct TexSample {
 };
 
 // Eq. 5: s = (u + 3)/6, t = (v + 3)/6; texel-centre coordinates x = s T - 1/2.
+// A fragment has |u|, |v| <= 3, so x lies in [-1/2, T - 1/2] and floor(x) in
+// [-1, T - 1] (the float32 rounding of (u + 3) T/6 stays within the same
+// integer parts): clamping the lower corner from below and the upper one
+// from above is the whole clamp-to-edge.
 __device__ __forceinline__ TexSample tex_setup(float u, float v, int T) {
   TexSample s;
   float Ts6 = (float)T * (1.0f / 6.0f);
@@ -82,23 +86,40 @@ __device__ __forceinline__ TexSample tex_setup(float u, float v, int T) {
   s.fx = xs - fi;
   s.fy = ys - fj;
   int i0 = (int)fi, j0 = (int)fj;
-  s.ia = min(max(i0, 0), T - 1);
-  s.ib = min(max(i0 + 1, 0), T - 1);
-  s.ja = min(max(j0, 0), T - 1);
-  s.jb = min(max(j0 + 1, 0), T - 1);
+  s.ia = max(i0, 0);
+  s.ib = min(i0 + 1, T - 1);
+  s.ja = max(j0, 0);
+  s.jb = min(j0 + 1, T - 1);
   return s;
+}
+
+// The four bilinear corners' 8 channels: t0 (ia, ja), t1 (ib, ja), t2 (ia, jb),
+// t3 (ib, jb) of the splat's chart.
+template <int DT>
+__device__ __forceinline__ void tex_corners(const ViewDesc& V, long long splat, int T, const TexSample& s, float t0[8],
+                                            float t1[8], float t2[8], float t3[8]) {
+  const unsigned ra = (unsigned)(s.ja * T), rb = (unsigned)(s.jb * T);
+  if (DT == DT_F32 && V.tex_v8) {
+    const float* c = reinterpret_cast<const float*>(V.texels) + splat * (long long)(T * T * 8);
+    load_texel_v8(c + (ra + s.ia) * 8u, t0);
+    load_texel_v8(c + (ra + s.ib) * 8u, t1);
+    load_texel_v8(c + (rb + s.ia) * 8u, t2);
+    load_texel_v8(c + (rb + s.ib) * 8u, t3);
+  } else {
+    const long long base = splat * (long long)T * T;
+    load_texel(V.texels, DT, base + ra + s.ia, t0);
+    load_texel(V.texels, DT, base + ra + s.ib, t1);
+    load_texel(V.texels, DT, base + rb + s.ia, t2);
+    load_texel(V.texels, DT, base + rb + s.ib, t3);
+  }
 }
 
 // Bilinear texel fetch (Eq. 6) of the 8 channels, as 4 channel pairs.
 template <int DT>
-__device__ __forceinline__ void tex_fetch(const void* texels, long long splat, int T, const TexSample& s,
+__device__ __forceinline__ void tex_fetch(const ViewDesc& V, long long splat, int T, const TexSample& s,
                                           float out[8]) {
-  long long base = splat * (long long)T * T;
   float t0[8], t1[8], t2[8], t3[8];
-  load_texel(texels, DT, base + s.ja * T + s.ia, t0);
-  load_texel(texels, DT, base + s.ja * T + s.ib, t1);
-  load_texel(texels, DT, base + s.jb * T + s.ia, t2);
-  load_texel(texels, DT, base + s.jb * T + s.ib, t3);
+  tex_corners<DT>(V, splat, T, s, t0, t1, t2, t3);
   const float gx = 1.f - s.fx, gy = 1.f - s.fy;
   const float2 FX = f2(s.fx, s.fx), GX = f2(gx, gx), FY = f2(s.fy, s.fy), GY = f2(gy, gy);
 #pragma unroll

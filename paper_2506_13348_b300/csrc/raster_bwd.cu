@@ -183,6 +183,8 @@ __global__ void __launch_bounds__(32 * kRasterWarps, ((FEAT & FEAT_IND) ? 2 : 3)
         // channels)/d(texel-space u, v)
         float dnu[3] = {0.f, 0.f, 0.f}, dnv[3] = {0.f, 0.f, 0.f};
         const float2 g01 = f2(g8[0], g8[1]), g23 = f2(g8[2], g8[3]), g45 = f2(g8[4], g8[5]), g67 = f2(g8[6], g8[7]);
+        // (two 16-byte loads per float32 texel: one 32-byte load holds eight
+        // more registers live and spills here)
         const long long base = splat * (long long)T * T;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_
             float x[8];
             if (SMP == SMP_SOFTWARE) {
               const TexSample ts_ = tex_setup(f.u, f.v, T);
-              tex_fetch<DT>(V.texels, splat, T, ts_, x);
+              tex_fetch<DT>(V, splat, T, ts_, x);
             } else if (SMP == SMP_HW_ATLAS) {
               tex_fetch_hw(V, splat, T, f.u, f.v, x);
             } else {

@@ -86,6 +86,7 @@ struct ViewDesc {
   const void* texels;
   int T;
   int tex_dtype;
+  int tex_v8;     // float32 texels at a 32-byte aligned base: one 32-byte load per texel
   // 2-D atlases for SMP_HW_ATLAS: channels 0-3 and 4-7, and each splat's
   // chart origin (texels) -- the indirection buffer of supplementary Sec. 1
   cudaTextureObject_t atlas2d[2];
@@ -163,6 +164,15 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // ---- texel loads (stored dtype -> float32) ----------------------------------
+// One float32 texel (8 channels, 32 bytes) in a single 256-bit load; p must
+// be 32-byte aligned (callers check the atlas base once per view).
+__device__ __forceinline__ void load_texel_v8(const float* p, float out[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(out[0]), "=f"(out[1]), "=f"(out[2]), "=f"(out[3]), "=f"(out[4]), "=f"(out[5]), "=f"(out[6]),
+        "=f"(out[7])
+      : "l"(p));
+}
+
 __device__ __forceinline__ void load_texel(const void* base, int dtype, long long idx, float out[8]) {
   if (dtype == DT_F32) {
     const float4* p = reinterpret_cast<const float4*>(base) + idx * 2;

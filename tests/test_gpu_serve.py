@@ -89,7 +89,9 @@ def test_admission_rejection_and_timeout(P, scenes):
     # budget fits one 64x64 request but not one plus another's uncollected
     # output: the second waits until the first result is collected, so a
     # short wait on it times out
-    one = 64 * 64 * 16 + 64 * 64 * 32 * 16 + 9000 * 160
+    probe = P.Server(arena_bytes=1 << 30, n_streams=1, max_batch=1)
+    one = probe.request_bytes(scenes[2], c)
+    probe.close()
     srv = P.Server(arena_bytes=one + 1000, n_streams=1, max_batch=4)
     t1 = srv.submit(scenes[2], c)
     t2 = srv.submit(scenes[2], c)
@@ -106,3 +108,79 @@ def test_admission_rejection_and_timeout(P, scenes):
     with pytest.raises(TexSplatError, match="ARG"):
         srv.wait(987654, None)
     srv.close()
+
+
+def dense_scene(P, n=20000):
+    """n large fronto splats stacked in front of the camera: every one covers
+    all 256 tiles of a 256x256 view, about n / 256 pairs per pixel -- far
+    more than the server's initial estimate of 32."""
+    rng = np.random.default_rng(5)
+    means = np.zeros((n, 3), np.float32)
+    means[:, 2] = 5.0 + rng.uniform(0.0, 1.0, n).astype(np.float32)
+    scene = dict(means=means, quats=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                 scales=np.full((n, 2), 20.0, np.float32), opacity=np.full(n, 0.9, np.float32),
+                 texels=np.tile(np.linspace(0.1, 0.9, 8, dtype=np.float32), (n, 1, 1, 1)).reshape(n, 1, 1, 8), T=1)
+    cam = dict(R=np.eye(3, dtype=np.float32), t=np.zeros(3, np.float32), fx=np.float32(256.0),
+               fy=np.float32(256.0), cx=np.float32(128.0), cy=np.float32(128.0), W=256, H=256)
+    return P.Scene.from_arrays(scene, sg.make_env(0, cube_res=8, irr_res=4, lut_res=16)), cam
+
+
+def test_admission_trues_up_to_the_counted_pairs(P):
+    """Requests whose real pair count is 2.5x the initial estimate: the
+    reservation is trued up once the batch has counted its pairs, so two
+    workers that were both admitted on the estimate do not hold more than
+    the budget at once (the second waits for the first), and the learned
+    estimate then admits such requests one at a time.  Every image equals
+    the alone render."""
+    sc, cam = dense_scene(P)
+    ref, saved = P.render(sc, cam, save=True)
+    pairs = saved.sizes()[0]
+    saved.release()
+    torch.cuda.synchronize()
+    assert pairs / (256 * 256) > 70
+    probe = P.Server(arena_bytes=1 << 30, n_streams=1, max_batch=1)
+    est = probe.request_bytes(sc, cam)
+    probe.close()
+    real = est + (pairs / (256 * 256) - 32.0) * 256 * 256 * 16
+    arena = int(1.6 * real)  # two estimates fit, two real requests do not
+    assert 2 * est < arena < 2 * real
+    srv = P.Server(arena_bytes=arena, n_streams=2, max_batch=1)
+    try:
+        ts = [srv.submit(sc, cam) for _ in range(6)]
+        for t in ts:
+            out = torch.empty(256, 256, 4, dtype=torch.float32, device="cuda")
+            srv.wait(t, out)
+            assert torch.equal(out, ref)
+        st = srv.stats()
+        print(f"[serve] arena {arena / 1e6:.1f} MB, peak reserved {st['peak_reserved_bytes'] / 1e6:.1f} MB, "
+              f"true-ups {st['true_ups']}, over budget {st['over_budget']}")
+        assert st["completed"] == 6 and st["failed"] == 0
+        assert st["true_ups"] >= 1 and st["over_budget"] == 0
+        assert st["peak_reserved_bytes"] <= arena
+        assert srv.request_bytes(sc, cam) > real - 4096  # the learned estimate covers the real pairs
+    finally:
+        srv.close()
+
+
+def test_two_workers_batches_overlap_on_the_device(P):
+    """With two workers, batches of different workers run on the device at
+    the same time: their device-time intervals (CUDA events on each
+    worker's stream) intersect."""
+    scene = sg.make_scene(1, n=200_000, T=8, seed=7)
+    sc = P.Scene.from_arrays(scene, sg.make_env(1, cube_res=32, levels=1, irr_res=8, lut_res=128), store="bf16")
+    cams = sg.fibonacci_cameras(16, 4.0, 800, 800)
+    srv = P.Server(arena_bytes=8 << 30, n_streams=2, max_batch=1)
+    try:
+        ts = [srv.submit(sc, c) for c in cams]
+        for t in ts:
+            srv.wait(t, None)
+        log = srv.batch_log()
+        assert len(log) == 16 and {w for w, _, _, _ in log} == {0, 1}
+        overlaps = sum(1 for i, a in enumerate(log) for b in log[i + 1:]
+                       if a[0] != b[0] and a[2] < b[3] and b[2] < a[3])
+        busy = sum(t1 - t0 for _, _, t0, t1 in log)
+        span = max(t1 for *_, t1 in log) - min(t0 for _, _, t0, _ in log)
+        print(f"[serve] {overlaps} overlapping pairs of batches, device-busy sum {busy:.2f} ms over a {span:.2f} ms span")
+        assert overlaps >= 1
+    finally:
+        srv.close()

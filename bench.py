@@ -34,7 +34,7 @@ METRIC = "Mpix/s fwd+bwd at 200k splats 800²; served-view p50/p99 latency vs pl
 UNIT = "Mpix/s"
 N_SPLATS, T_TEX, RES, N_CAMS = 200_000, 8, 800, 100
 PREC_TILES = 16  # seeded covered 16x16 tiles (4096 px) per error view scored against the FP64 oracle
-FP32_LANES_PER_SM, N_SM = 128, 148
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM on this architecture (sm_100 family)
 
 # FP32 operations per fragment of the algorithm (FMA = 2): every evaluated
 # (pixel, splat) pair costs the homography (6 FMA, a reciprocal, 2 mul) and the
@@ -339,7 +339,8 @@ def run_ours(args):
     flops_bwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_BWD * fr["n_blended"]
     peaks, peak_kind = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     stage_ms = {k: v[1] / max(1, v[0]) for k, v in stages.items()}
     dom = max(("raster_fwd", "raster_bwd"), key=lambda k: stages.get(k, (0, 0.0))[1])
     dom_ms = stage_ms.get(dom, float("nan"))
@@ -360,7 +361,7 @@ def run_ours(args):
             "config": workload_config(world),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                         "peak_note": f"FP32 FMA peak {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                         "peak_note": f"FP32 FMA peak {n_sm} SMs (device) x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                       f"(clock from {peak_kind} peaks)",
                          "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
                          "peak_measured": None if args.no_fp32_probe else {

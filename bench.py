@@ -367,6 +367,7 @@ def run_ours(args):
                          "peak_measured": None if args.no_fp32_probe else {
                              "scalar_fma_tflops": round(meas_scalar, 2), "paired_fma_tflops": round(meas_paired, 2),
                              "frac_of_measured_scalar": achieved / meas_scalar}},
+            "roofline_fwd": roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar),
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_hbm_frac": stage_fracs,
             "fragments_per_view": {k: int(v) for k, v in fr.items()},
@@ -408,6 +409,20 @@ def run_ours(args):
         pg.barrier()
         pg.destroy_process_group()
     return 0
+
+
+def roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar):
+    """The roofline of the rasteriser that is not the dominant kernel (the
+    forward, normally), on the same FLOP model, peak and per-stage event
+    timing as the dominant one."""
+    other = "raster_fwd" if dom == "raster_bwd" else "raster_bwd"
+    ms = stage_ms.get(other, float("nan"))
+    flops = flops_fwd if other == "raster_fwd" else flops_bwd
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": other, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": read_traffic(other), "flops_per_launch": flops,
+            "ms_per_launch": ms,
+            "frac_of_measured_scalar": achieved / meas_scalar if meas_scalar == meas_scalar else None}
 
 
 def run_serving(args, device):
@@ -702,6 +717,17 @@ def run_large_scene(args, device):
            "stages_ms_per_step": stage_ms,
            "adam": {"ms_per_step": adam_ms, "bytes_per_step": adam_bytes, "gb_per_s": adam_gbs,
                     "frac_of_hbm": adam_gbs / float(peaks.get("hbm_gbs", 6400.0)), "peak": peak_kind}}
+    # the HBM-side stages of a step against their algorithmic bytes (the
+    # pair count of one untimed batch of the step's views)
+    _, saved = P.render_views([sc] * V, cams[:V], outs=outs, save=True)
+    K = saved.sizes()[0]
+    saved.release()
+    tiles = V * ((W + 15) // 16) * ((H + 15) // 16)
+    sb = stage_bytes(V * n, K, V * W * H, tiles)
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    out["pairs_per_step"] = K
+    out["stage_hbm_frac"] = {k: round(b / (stage_ms[k] / 1e3) / 1e9 / hbm, 3) for k, b in sb.items()
+                             if stage_ms.get(k, 0) > 0}
     sc.close()
     del tr
     torch.cuda.empty_cache()

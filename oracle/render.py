@@ -299,7 +299,7 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
                 near = (fr_ <= m_k) | (fr_ >= 1.0 - m_k)
                 kink |= near & (coord >= -m_k) & (coord <= T - 1 + m_k)
             kink |= (oG - ALPHA_MAX).abs() <= m_a * ALPHA_MAX
-            # nearly edge-on splats (|n . d| <= 0.03 |d|, within ~1.7 deg):
+            # nearly edge-on splats (|n . d| <= EDGE_ON_COS |d|):
             # d(u,v)/d(params) grows like 1/cos^2 and an FP32 evaluation
             # keeps only a few correct digits of those gradients
             kink |= den.abs() <= EDGE_ON_COS * dnorm
@@ -315,10 +315,16 @@ def fragments(params: dict, cam: dict, px, py, cand: torch.Tensor, margins=None)
 # beyond (the texel coordinate scales u by T / 6).
 KINK_TEX = 1e-5
 # |cos| between view ray and splat normal below which gradients are excluded
-# (~1.7 deg from edge-on; isolated splats match to ~1e-6 up to 85 deg tilt,
-# but inside deep pixels the FP32 error of the 1/cos^2-amplified geometry
-# gradients of near-edge-on splats exceeds 1e-3 of the group maximum)
-EDGE_ON_COS = 0.03
+# (~1.15 deg from edge-on).  The local coordinates (u, v) of a hit carry an
+# FP32 error that grows like 1/|cos| whichever way they are evaluated (an
+# FP32 homography and an FP32 ray-plane evaluation of the same fragments
+# measure the same error in every |cos| band: median 4e-5 at |cos| in
+# [0.01, 0.03) against 2e-6 above 0.3), and their derivatives grow like
+# 1/cos^2, so geometry gradients of fragments this close to edge-on keep only
+# a few correct digits.  The band is the narrowest of {0, 0.005, 0.01, 0.02,
+# 0.03} at which the 200k-splat scene's 1k-splat slice keeps every gradient
+# group within 1e-3 of its maximum (quaternions 6.5e-4 at 0.02, 1.7e-3 at 0.01).
+EDGE_ON_COS = 0.02
 
 
 def tile_candidates(keylist: dict, tile: int) -> np.ndarray:

@@ -187,13 +187,15 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter_local(const uin
     vr[r] = idx < n ? vin[idx] : 0u;
   }
   const unsigned lt_mask = (1u << lane) - 1u;
+  // the lanes sharing each element's digit, kept for the placement below
+  unsigned pr[RS_ROUNDS];
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS; ++r) {
     const int idx = wbase + r * 32 + lane;
     const bool ok = idx < n;
     const uint32_t d = digit_of(kr[r], shift, mask);
-    const unsigned peers = digit_peers(d, bits, ok);
-    if (ok && (peers & lt_mask) == 0) whist[warp][d] += __popc(peers);
+    pr[r] = digit_peers(d, bits, ok);
+    if (ok && (pr[r] & lt_mask) == 0) whist[warp][d] += __popc(pr[r]);
     __syncwarp();
   }
   __syncthreads();
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter_local(const uin
     const int idx = wbase + r * 32 + lane;
     const bool ok = idx < n;
     const uint32_t d = digit_of(kr[r], shift, mask);
-    const unsigned peers = digit_peers(d, bits, ok);
+    const unsigned peers = pr[r];
     if (ok) {
       const uint32_t slot = s_dstart[d] + whist[warp][d] + __popc(peers & lt_mask);
       s_key[slot] = kr[r];

@@ -859,13 +859,13 @@ def read_traffic(kernel: str):
 #   tile_ranges: 4 B / pair in, 8 B / tile out; the forward's tile order:
 #     ranges 8 in, key + id 8 out, one sort pass 20      ->  36 B / tile
 #   shade_bwd: G-buffer 32 + coverage 4 + dL/drgba 16 in, 48 out -> 100 B / pixel
-#   preprocess_bwd: record gradients 112 + record 80 + parameters 40 in,
-#     gradients 40 out                                      -> 272 B / splat
+#   preprocess_bwd: record gradients 112 in (every item); parameters 40 in,
+#     gradients 40 out (items with a gradient)              -> 192 B / splat at most
 #   l1_loss: image 16 + target 16 in, gradient 16 out       ->  48 B / pixel
 def stage_bytes(N, K, P, tiles):
     return {"preprocess": 152 * N, "sort_splats": 128 * N, "scan_counts": 20 * N,
             "emit_pairs": 8 * K + 28 * N, "sort_pairs": 40 * K, "tile_ranges": 4 * K + 44 * tiles,
-            "shade_bwd": 100 * P, "preprocess_bwd": 272 * N, "l1_loss": 48 * P}
+            "shade_bwd": 100 * P, "preprocess_bwd": 192 * N, "l1_loss": 48 * P}
 
 
 def run_features(args, device):

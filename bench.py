@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--cpu-tiles", type=int, default=6, help="tiles of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="one stream: each view's forward waits for the previous view's backward")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-view latency measurement")
     ap.add_argument("--serve-only", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -117,11 +119,13 @@ def aggregate_value(world: int, steps: int, ms_max: float) -> float:
     return world * steps * RES * RES / 1e6 / (ms_max / 1e3)
 
 
-def workload_config(world: int) -> dict:
+def workload_config(world: int, pipelined: bool = True) -> dict:
     return {"workload": "cfg1: 200k textured splats (160k sphere + 40k box), 8x8 texels x 8 ch, "
                         "800x800, forward + L1 loss + backward per view",
             "splats": N_SPLATS, "texels": f"{T_TEX}x{T_TEX}x8 f32", "resolution": f"{RES}x{RES}",
             "views_per_step": 1, "parallelism": f"replicas x{world}",
+            "streams": ("2: view i+1's binning and forward overlap view i's backward" if pipelined
+                        else "1: views in sequence"),
             "l2": "inputs larger than L2 (texel atlas 410 MB, records+pairs ~90 MB per view)"}
 
 
@@ -287,16 +291,37 @@ def run_ours(args):
     my_cams = [cams[i] for i in views]
     targets = [torch.from_numpy(sg.make_target(i, RES, RES)).to(dev) for i in views]
     out = torch.empty(RES, RES, 4, dtype=torch.float32, device=dev)
-    dl = torch.empty_like(out)
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
     grads = P.zero_grads(sc)
     stream = torch.cuda.current_stream()
+    # views alternate between two streams: view i+1's binning and forward
+    # overlap view i's backward (gradients accumulate with atomics, so the
+    # two backwards may also overlap); each stream has its own image, loss
+    # and gradient-image buffers
+    streams = [stream] + ([torch.cuda.Stream(device=dev)] if not args.no_pipeline else [])
+    bufs = [(torch.empty_like(out), torch.empty_like(out), torch.zeros(1, dtype=torch.float32, device=dev))
+            for _ in streams]
 
-    def step(i):
-        _, saved = P.render(sc, my_cams[i % n_needed], out=out, save=True)
-        P.l1_loss(out, targets[i % n_needed], loss, dl)
-        P.render_backward(saved, dl, grads)
+    def step(i, serial=False):
+        k = 0 if serial else i % len(streams)
+        st, (o, d, l) = streams[k], bufs[k]
+        _, saved = P.render(sc, my_cams[i % n_needed], out=o, save=True, stream=st)
+        P.l1_loss(o, targets[i % n_needed], l, d, stream=st)
+        P.render_backward(saved, d, grads, stream=st)
         saved.release()
+
+    def timed(steps, serial):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s2 in streams[1:]:
+            s2.wait_event(e0)
+        for i in range(steps):
+            step(args.warmup + i, serial)
+        for s2 in streams[1:]:
+            stream.wait_stream(s2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
 
     for i in range(args.warmup):
         step(i)
@@ -304,23 +329,20 @@ def run_ours(args):
     if pg:
         pg.barrier()
     sampler = ClockSampler(local)
+    l0 = _lib.launch_count()
+    ms = timed(args.steps, serial=False)
+    launches = _lib.launch_count() - l0
+    if pg:
+        pg.barrier()
+    # the same steps once more on one stream with per-stage CUDA events: the
+    # kernels' own durations (the roofline) without the other view's work
+    # sharing the SMs
     _lib.profile_enable(True)
     _lib.profile_report()
-    l0 = _lib.launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    launches = _lib.launch_count() - l0
+    ms_serial = timed(args.steps, serial=True)
     stages = _lib.profile_report()
     _lib.profile_enable(False)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        pg.barrier()
     ms_max = max_over_ranks(ms, pg, dev)
     value = aggregate_value(world, args.steps, ms_max)
 
@@ -358,8 +380,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(world),
+            "config": workload_config(world, not args.no_pipeline),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
+                         "timing": "kernel's own CUDA events in a second timed pass of the same steps on one stream",
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                          "peak_note": f"FP32 FMA peak {n_sm} SMs (device) x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                       f"(clock from {peak_kind} peaks)",
@@ -368,6 +391,7 @@ def run_ours(args):
                              "scalar_fma_tflops": round(meas_scalar, 2), "paired_fma_tflops": round(meas_paired, 2),
                              "frac_of_measured_scalar": achieved / meas_scalar}},
             "roofline_fwd": roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar),
+            "serial_ms_per_step": ms_serial / args.steps,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_hbm_frac": stage_fracs,
             "fragments_per_view": {k: int(v) for k, v in fr.items()},
@@ -772,30 +796,36 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
 
     import scenegen as sg
     host_t = [torch.from_numpy(sg.make_target(i, RES, RES)).pin_memory() for i in range(min(8, n_needed))]
-    dev_t = [torch.empty(RES, RES, 4, dtype=torch.float32, device=dev) for _ in range(2)]
-    out = torch.empty_like(dev_t[0])
-    dl = torch.empty_like(dev_t[0])
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    loss_h = torch.zeros(1, dtype=torch.float32).pin_memory()
-    grads = P.zero_grads(sc)
     stream = torch.cuda.current_stream()
+    # as the timed loop: views alternate between the compute streams; per
+    # stream a device target, image, gradient image, loss and pinned loss
+    streams = [stream] + ([torch.cuda.Stream(device=dev)] if not args.no_pipeline else [])
+    ns = len(streams)
+    dev_t = [torch.empty(RES, RES, 4, dtype=torch.float32, device=dev) for _ in range(ns)]
+    outs = [torch.empty_like(dev_t[0]) for _ in range(ns)]
+    dls = [torch.empty_like(dev_t[0]) for _ in range(ns)]
+    losses = [torch.zeros(1, dtype=torch.float32, device=dev) for _ in range(ns)]
+    loss_h = [torch.zeros(1, dtype=torch.float32).pin_memory() for _ in range(ns)]
+    grads = P.zero_grads(sc)
     copy_stream = torch.cuda.Stream(device=dev)
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    used = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [torch.cuda.Event() for _ in range(ns)]
+    used = [torch.cuda.Event() for _ in range(ns)]
 
     def step(i):
-        b = i % 2
+        b = i % ns
+        st = streams[b]
         with torch.cuda.stream(copy_stream):
             copy_stream.wait_event(used[b])  # the buffer's previous loss read is done
             dev_t[b].copy_(host_t[i % len(host_t)], non_blocking=True)
             copied[b].record(copy_stream)
-        _, saved = P.render(sc, cams[i % n_needed], out=out, save=True)
-        stream.wait_event(copied[b])
-        P.l1_loss(out, dev_t[b], loss, dl)
-        used[b].record(stream)
-        P.render_backward(saved, dl, grads)
+        _, saved = P.render(sc, cams[i % n_needed], out=outs[b], save=True, stream=st)
+        st.wait_event(copied[b])
+        P.l1_loss(outs[b], dev_t[b], losses[b], dls[b], stream=st)
+        used[b].record(st)
+        P.render_backward(saved, dls[b], grads, stream=st)
         saved.release()
-        loss_h.copy_(loss, non_blocking=True)
+        with torch.cuda.stream(st):
+            loss_h[b].copy_(losses[b], non_blocking=True)
 
     for i in range(args.warmup):
         step(i)
@@ -805,14 +835,19 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     copy_stream.wait_event(e0)
+    for s2 in streams[1:]:
+        s2.wait_event(e0)
     for i in range(args.steps):
         step(args.warmup + i)
+    for s2 in streams[1:]:
+        stream.wait_stream(s2)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
     return {"value": aggregate_value(world, args.steps, ms), "unit": UNIT,
             "h2d_bytes_per_step": RES * RES * 4 * 4, "d2h_bytes_per_step": 4,
-            "note": "target H2D on a side stream overlapping the render (double-buffered)"}
+            "note": "target H2D on a side stream overlapping the render; views on "
+                    f"{'two streams as the timed loop' if not args.no_pipeline else 'one stream'}"}
 
 
 # Source files each profiled kernel is built from: a committed DRAM-traffic

@@ -347,7 +347,7 @@ def run_ours(args):
     value = aggregate_value(world, args.steps, ms_max)
 
     # fragment statistics of a few of the timed views (untimed pass)
-    fr = {"n_pairs": 0, "n_evaluated": 0, "n_blended": 0, "n_visible": 0}
+    fr = {"n_pairs": 0, "n_evaluated": 0, "n_blended": 0, "n_visible": 0, "n_texels_read": 0, "n_items_blended": 0}
     nstat = 4
     for i in range(nstat):
         _, saved = P.render(sc, my_cams[(args.warmup + i) % n_needed], out=out, save=True)
@@ -369,6 +369,7 @@ def run_ours(args):
     dom_flops = flops_bwd if dom == "raster_bwd" else flops_fwd
     achieved = dom_flops / (dom_ms / 1e3) / 1e12
     traffic = read_traffic(dom)
+    rbytes = raster_bytes(fr, npix)
     # measured FP32 FMA rate of this GPU (after the timed region): context for
     # the derived peak above
     meas_scalar, meas_paired = (float("nan"), float("nan")) if args.no_fp32_probe else _lib.measure_fp32_peak(local)
@@ -387,10 +388,12 @@ def run_ours(args):
                          "peak_note": f"FP32 FMA peak {n_sm} SMs (device) x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                       f"(clock from {peak_kind} peaks)",
                          "flops_per_launch": dom_flops, "ms_per_launch": dom_ms,
+                         "alg_bytes_per_launch": rbytes[dom],
+                         "traffic_over_alg_bytes": traffic / rbytes[dom] if traffic else None,
                          "peak_measured": None if args.no_fp32_probe else {
                              "scalar_fma_tflops": round(meas_scalar, 2), "paired_fma_tflops": round(meas_paired, 2),
                              "frac_of_measured_scalar": achieved / meas_scalar}},
-            "roofline_fwd": roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar),
+            "roofline_fwd": roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar, rbytes),
             "serial_ms_per_step": ms_serial / args.steps,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_hbm_frac": stage_fracs,
@@ -435,7 +438,7 @@ def run_ours(args):
     return 0
 
 
-def roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar):
+def roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar, rbytes):
     """The roofline of the rasteriser that is not the dominant kernel (the
     forward, normally), on the same FLOP model, peak and per-stage event
     timing as the dominant one."""
@@ -443,9 +446,11 @@ def roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar):
     ms = stage_ms.get(other, float("nan"))
     flops = flops_fwd if other == "raster_fwd" else flops_bwd
     achieved = flops / (ms / 1e3) / 1e12
+    traffic = read_traffic(other)
     return {"bound": "alu", "kernel": other, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": read_traffic(other), "flops_per_launch": flops,
-            "ms_per_launch": ms,
+            "frac": achieved / fp32_peak, "traffic": traffic, "flops_per_launch": flops,
+            "ms_per_launch": ms, "alg_bytes_per_launch": rbytes[other],
+            "traffic_over_alg_bytes": traffic / rbytes[other] if traffic else None,
             "frac_of_measured_scalar": achieved / meas_scalar if meas_scalar == meas_scalar else None}
 
 
@@ -897,6 +902,21 @@ def read_traffic(kernel: str):
 #   preprocess_bwd: record gradients 112 in (every item); parameters 40 in,
 #     gradients 40 out (items with a gradient)              -> 192 B / splat at most
 #   l1_loss: image 16 + target 16 in, gradient 16 out       ->  48 B / pixel
+# Algorithmic bytes of the two rasterisers (per view): what each must move
+# at least once.  Both read the pair list (4 B per pair), the first 48 B of
+# every visible splat's record (block test and fragment), the last 32 B of
+# each splat blended at some pixel, and every distinct texel a blended
+# fragment reads (32 B at float32: n_texels_read from the statistics pass).
+#   forward: + per pixel rgba 16 and saved state 48 out      -> 64 B / pixel
+#   backward: + per pixel dL/dX, dL/dA 48, T and last index 8 in -> 56 B / pixel;
+#     texel gradients read and written once per distinct texel (2 x 32 B),
+#     record gradients (14 doubles) read and written per blended splat
+def raster_bytes(fr, P, texel_bytes=32):
+    common = 4 * fr["n_pairs"] + 48 * fr["n_visible"] + 32 * fr["n_items_blended"] + texel_bytes * fr["n_texels_read"]
+    return {"raster_fwd": common + 64 * P,
+            "raster_bwd": common + 56 * P + 2 * texel_bytes * fr["n_texels_read"] + 2 * 112 * fr["n_items_blended"]}
+
+
 def stage_bytes(N, K, P, tiles):
     return {"preprocess": 152 * N, "sort_splats": 128 * N, "scan_counts": 20 * N,
             "emit_pairs": 8 * K + 28 * N, "sort_pairs": 40 * K, "tile_ranges": 4 * K + 44 * tiles,

@@ -89,6 +89,9 @@ typedef struct ts_frag_stats {
   int64_t n_evaluated;  /* (pixel, splat) fragments tested before each pixel terminated */
   int64_t n_blended;    /* fragments that passed the support and alpha tests and were blended */
   int64_t n_visible;    /* splats that survived culling */
+  int64_t n_texels_read;   /* distinct (list item, texel) pairs read by blended fragments: each blended
+                              fragment reads its four bilinear corners (Eq. 6), clamped to the chart */
+  int64_t n_items_blended; /* distinct list items (splats of a view) blended at some pixel */
 } ts_frag_stats;
 
 /* ---- scenes --------------------------------------------------------------- */
@@ -203,7 +206,8 @@ ts_status ts_saved_copy_pixels(const ts_saved* saved, int view, float* gbuf, flo
                                int32_t* last, void* stream);
 
 /* Fragment counts of a saved forward (counted by a separate, untimed pass
- * over the same lists).  Synchronises the stream. */
+ * over the same lists; the texel counts use a temporary bitmap of one bit
+ * per texel of every list item's chart).  Synchronises the stream. */
 ts_status ts_saved_frag_stats(const ts_saved* saved, ts_frag_stats* out, void* stream);
 
 /* Geometry size, texture resolution and stored atlas dtype of a scene (any

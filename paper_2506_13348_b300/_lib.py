@@ -45,7 +45,7 @@ class TsGrads(C.Structure):
 
 class TsFragStats(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_evaluated", C.c_int64), ("n_blended", C.c_int64),
-                ("n_visible", C.c_int64)]
+                ("n_visible", C.c_int64), ("n_texels_read", C.c_int64), ("n_items_blended", C.c_int64)]
 
 
 class TsServeStats(C.Structure):

@@ -214,7 +214,7 @@ class Saved:
         st = TsFragStats()
         check(lib().ts_saved_frag_stats(self.handle, C.byref(st), _stream(stream)), "ts_saved_frag_stats")
         return dict(n_pairs=st.n_pairs, n_evaluated=st.n_evaluated, n_blended=st.n_blended,
-                    n_visible=st.n_visible)
+                    n_visible=st.n_visible, n_texels_read=st.n_texels_read, n_items_blended=st.n_items_blended)
 
 
 def render(scene: Scene, cam: dict, out: torch.Tensor | None = None, save: bool = False, stream=None):

@@ -877,11 +877,23 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
     TS_CUDA(tmp.alloc((void**)&V.rgba, (size_t)V.W * V.H * sizeof(float4)));
   }
   unsigned long long* d = nullptr;
-  TS_CUDA(tmp.alloc((void**)&d, 2 * sizeof(unsigned long long)));
-  TS_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st));
-  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, d, SMP_SOFTWARE, 0, st);
+  TS_CUDA(tmp.alloc((void**)&d, 4 * sizeof(unsigned long long)));
+  TS_CUDA(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), st));
+  // texel bitmap: one bit per texel of each list item's chart
+  int t2max = 1;
+  for (int i = 0; i < vt.n_views; ++i) t2max = std::max(t2max, vt.v[i].T * vt.v[i].T);
+  const int wpi = (t2max + 31) / 32;
+  const size_t bm_bytes = (size_t)std::max<long long>(vt.n_items, 1) * wpi * 4;
+  uint32_t* bm = nullptr;
+  TS_CUDA(tmp.alloc((void**)&bm, bm_bytes));
+  TS_CUDA(cudaMemsetAsync(bm, 0, bm_bytes, st));
+  const FragCounters fc{d, bm, wpi};
+  launch_raster_fwd(vt, sv->rec, sv->pair_items, sv->ranges, sv->scenes[0]->tex_dtype, false, &fc, SMP_SOFTWARE, 0,
+                    st);
   TS_CHECK_LAUNCH();
-  unsigned long long h[2] = {0, 0};
+  launch_touch_counts(bm, vt.n_items, wpi, d, st);
+  TS_CHECK_LAUNCH();
+  unsigned long long h[4] = {0, 0, 0, 0};
   TS_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
   // visible splats: items with a finite depth
   uint32_t* db = sv->depth_bits;
@@ -892,6 +904,8 @@ ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stre
   out->n_pairs = sv->K;
   out->n_evaluated = (int64_t)h[0];
   out->n_blended = (int64_t)h[1];
+  out->n_texels_read = (int64_t)h[2];
+  out->n_items_blended = (int64_t)h[3];
   int64_t vis = 0;
   for (uint32_t b : hb) vis += (b != 0xffffffffu);
   out->n_visible = vis;

@@ -82,9 +82,21 @@ const uint32_t* launch_tile_order_walk(const ViewTable& vt, const uint2* ranges,
 void launch_depth_bits(const uint64_t* depth_keys_unsorted, uint32_t* out, int n, cudaStream_t st);
 
 // raster_fwd.cu / raster_bwd.cu
+// Counters of the statistics pass (a forward that writes only these):
+// counts[0] evaluated, counts[1] blended fragments; touched is a bitmap with
+// words_per_item 32-bit words per list item, bit j T + i set when a blended
+// fragment of the item reads texel (i, j) (its four bilinear corners).
+struct FragCounters {
+  unsigned long long* counts;
+  uint32_t* touched;
+  int words_per_item;
+};
 void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
+                       const uint2* ranges, int tex_dtype, bool save, const FragCounters* stats, int sampler,
                        int feat, cudaStream_t st);
+// counts[2] += set bits of the bitmap, counts[3] += items with any bit set
+void launch_touch_counts(const uint32_t* touched, long long n_items, int words_per_item, unsigned long long* counts,
+                         cudaStream_t st);
 void launch_pack_atlas2d(const void* texels, int dtype, long long n, int T, int charts_x, cudaSurfaceObject_t s0,
                          cudaSurfaceObject_t s1, uint2* chart, const uint32_t* chart_of, int half_store,
                          cudaStream_t st);

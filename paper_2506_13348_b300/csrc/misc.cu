@@ -118,6 +118,37 @@ void launch_validate_gaussians(const float4* means, const float4* quats, const f
   }
 }
 
+// Totals of the statistics pass's texel bitmap: set bits (distinct texels
+// read by blended fragments) and items with any bit set (distinct splats
+// blended at some pixel).  One warp per item, grid-stride.
+__global__ void k_touch_counts(const uint32_t* __restrict__ touched, long long n_items, int wpi,
+                               unsigned long long* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bits = 0, items = 0;
+  for (long long i = w0; i < n_items; i += nw) {
+    unsigned c = 0;
+    for (int k = lane; k < wpi; k += 32) c += __popc(touched[i * wpi + k]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    bits += c;
+    items += c != 0;
+  }
+  if (lane == 0 && (bits | items)) {
+    atomicAdd(counts + 2, bits);
+    atomicAdd(counts + 3, items);
+  }
+}
+
+void launch_touch_counts(const uint32_t* touched, long long n_items, int words_per_item, unsigned long long* counts,
+                         cudaStream_t st) {
+  if (n_items > 0) {
+    const unsigned blocks = (unsigned)std::min<long long>((n_items + 7) / 8, 148 * 8);
+    k_touch_counts<<<blocks, 256, 0, st>>>(touched, n_items, words_per_item, counts);
+    note_launches(1);
+  }
+}
+
 // Activations of the raw optimisation variables: s = exp(log s) per scale
 // component, o = sigmoid(logit o) (the 3DGS / 2DGS parameterisation the
 // optimisation of Sec. 3.6 runs on).  Element i < 2n is a scale component,

@@ -32,8 +32,7 @@ namespace ts {
 template <int DT, bool SAVE, bool STATS, int SMP, int FEAT = 0>
 __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
                                                      const uint32_t* __restrict__ pair_items,
-                                                     const uint2* __restrict__ ranges,
-                                                     unsigned long long* __restrict__ stats) {
+                                                     const uint2* __restrict__ ranges, FragCounters stats) {
   constexpr unsigned FULL = 0xffffffffu;
   constexpr bool IND = (FEAT & FEAT_IND) != 0, N2 = (FEAT & FEAT_N2) != 0;
   const int tile = raster_tile(vt);
@@ -136,6 +135,15 @@ __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_
             if (SMP == SMP_SOFTWARE) {
               const TexSample ts_ = tex_setup(f.u, f.v, T);
               tex_fetch<DT>(V, splat, T, ts_, x);
+              if (STATS) {  // the four texels this fragment reads
+                uint32_t* w = stats.touched + (size_t)s_it[warp][b][t] * stats.words_per_item;
+                const int q0 = ts_.ja * T + ts_.ia, q1 = ts_.ja * T + ts_.ib;
+                const int q2 = ts_.jb * T + ts_.ia, q3 = ts_.jb * T + ts_.ib;
+                atomicOr(w + (q0 >> 5), 1u << (q0 & 31));
+                atomicOr(w + (q1 >> 5), 1u << (q1 & 31));
+                atomicOr(w + (q2 >> 5), 1u << (q2 & 31));
+                atomicOr(w + (q3 >> 5), 1u << (q3 & 31));
+              }
             } else if (SMP == SMP_HW_ATLAS) {
               tex_fetch_hw(V, splat, T, f.u, f.v, x);
             } else {
@@ -206,8 +214,8 @@ __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_
       b += __shfl_xor_sync(FULL, b, o);
     }
     if ((threadIdx.x & 31) == 0) {
-      atomicAdd(stats + 0, e);
-      atomicAdd(stats + 1, b);
+      atomicAdd(stats.counts + 0, e);
+      atomicAdd(stats.counts + 1, b);
     }
   }
 }
@@ -216,7 +224,7 @@ namespace {
 
 template <int DT, bool SAVE, bool STATS, int SMP>
 void launch_feat(int feat, dim3 grid, dim3 block, cudaStream_t st, const ViewTable& vt, const Record* rec,
-                 const uint32_t* pair_items, const uint2* ranges, unsigned long long* stats) {
+                 const uint32_t* pair_items, const uint2* ranges, FragCounters stats) {
   switch (feat & (FEAT_IND | FEAT_N2)) {
     case 0: k_raster_fwd<DT, SAVE, STATS, SMP, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); break;
     case FEAT_N2:
@@ -236,29 +244,29 @@ template <int DT, int SMP>
 void launch_feat_n2(int feat, dim3 grid, dim3 block, cudaStream_t st, const ViewTable& vt, const Record* rec,
                     const uint32_t* pair_items, const uint2* ranges) {
   if (feat & FEAT_N2)
-    k_raster_fwd<DT, false, false, SMP, FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, nullptr);
+    k_raster_fwd<DT, false, false, SMP, FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, FragCounters{});
   else
-    k_raster_fwd<DT, false, false, SMP, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, nullptr);
+    k_raster_fwd<DT, false, false, SMP, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, FragCounters{});
 }
 
 template <int DT>
 void launch_dt(const ViewTable& vt, const Record* rec, const uint32_t* pair_items, const uint2* ranges, bool save,
-               unsigned long long* stats, int sampler, int feat, cudaStream_t st) {
+               const FragCounters* stats, int sampler, int feat, cudaStream_t st) {
   dim3 grid(vt.n_tiles * kCtasPerTile), block(32 * kRasterWarps);
   if (sampler == SMP_FLAT)
     launch_feat_n2<DT, SMP_FLAT>(feat, grid, block, st, vt, rec, pair_items, ranges);
   else if (stats)  // fragment statistics: the features change no fragment
-    k_raster_fwd<DT, false, true, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+    k_raster_fwd<DT, false, true, SMP_SOFTWARE><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, *stats);
   else if (save)
-    launch_feat<DT, true, false, SMP_SOFTWARE>(feat, grid, block, st, vt, rec, pair_items, ranges, nullptr);
+    launch_feat<DT, true, false, SMP_SOFTWARE>(feat, grid, block, st, vt, rec, pair_items, ranges, FragCounters{});
   else
-    launch_feat<DT, false, false, SMP_SOFTWARE>(feat, grid, block, st, vt, rec, pair_items, ranges, nullptr);
+    launch_feat<DT, false, false, SMP_SOFTWARE>(feat, grid, block, st, vt, rec, pair_items, ranges, FragCounters{});
 }
 
 }  // namespace
 
 void launch_raster_fwd(const ViewTable& vt, const Record* rec, const uint32_t* pair_items,
-                       const uint2* ranges, int tex_dtype, bool save, unsigned long long* stats, int sampler,
+                       const uint2* ranges, int tex_dtype, bool save, const FragCounters* stats, int sampler,
                        int feat, cudaStream_t st) {
   if (sampler == SMP_HW_ATLAS) {  // inference only; the atlas dtype is the texture's
     launch_feat_n2<DT_F32, SMP_HW_ATLAS>(feat, dim3(vt.n_tiles * kCtasPerTile), dim3(32 * kRasterWarps), st, vt, rec, pair_items, ranges);

@@ -161,6 +161,77 @@ def test_fragment_counts_match_oracle(P):
     assert e_ok <= st["n_evaluated"] <= e_ok + slack
 
 
+def oracle_texels_read(scene, cam, kl, cell_band=1e-4):
+    """Sets of (splat, texel) pairs the definition's blended fragments read
+    (each reads the four clamped bilinear corners of Eq. 6): 'sure' from
+    unmasked pixels and fragments clear of a bilinear cell boundary, 'maybe'
+    adding the corners of both sides of a near-boundary floor and of every
+    fragment in reach of a masked pixel; and the splats blended likewise."""
+    params = R.to_params(scene)
+    T = params["texels"].shape[1]
+    W, H = int(cam["W"]), int(cam["H"])
+    tiles_x, tiles_y = kl["view"]["tiles_x"], kl["view"]["tiles_y"]
+    sure, maybe, items_sure, items_maybe = set(), set(), set(), set()
+
+    def corners(sid, x, y):
+        out = []
+        for i0 in {int(np.floor(x - cell_band)), int(np.floor(x)), int(np.floor(x + cell_band))}:
+            for j0 in {int(np.floor(y - cell_band)), int(np.floor(y)), int(np.floor(y + cell_band))}:
+                for jj in (max(j0, 0), min(j0 + 1, T - 1)):
+                    for ii in (max(i0, 0), min(i0 + 1, T - 1)):
+                        out.append((sid, jj * T + ii))
+        return out
+
+    for tl in range(tiles_x * tiles_y):
+        c = R.tile_candidates(kl, tl)
+        if c.size == 0:
+            continue
+        tx, ty = tl % tiles_x, tl // tiles_x
+        xs = np.arange(tx * K.TILE, min(W, (tx + 1) * K.TILE))
+        ys = np.arange(ty * K.TILE, min(H, (ty + 1) * K.TILE))
+        gy, gx = np.meshgrid(ys, xs, indexing="ij")
+        cand = torch.from_numpy(np.ascontiguousarray(np.broadcast_to(c, (gx.size, c.size))).astype(np.int64))
+        fr = R.fragments(params, cam, gx.ravel(), gy.ravel(), cand, R.DEFAULT_MARGINS)
+        masked = (fr["ambiguous"] | fr["alt_mask"]).numpy()
+        bl = fr["blended"].numpy()
+        u, v = fr["u"].numpy(), fr["v"].numpy()
+        reach = (np.abs(u) <= 3.001) & (np.abs(v) <= 3.001)
+        xt = (u + 3.0) / 6.0 * T - 0.5
+        yt = (v + 3.0) / 6.0 * T - 0.5
+        cn = cand.numpy()
+        for p_, l_ in zip(*np.nonzero(bl | (masked[:, None] & reach))):
+            sid = int(cn[p_, l_])
+            cs = corners(sid, xt[p_, l_], yt[p_, l_])
+            maybe.update(cs)
+            items_maybe.add(sid)
+            if bl[p_, l_] and not masked[p_]:
+                items_sure.add(sid)
+                fx, fy = xt[p_, l_] - np.floor(xt[p_, l_]), yt[p_, l_] - np.floor(yt[p_, l_])
+                if min(fx, 1 - fx, fy, 1 - fy) > cell_band:
+                    sure.update(cs)
+    return sure, maybe, items_sure, items_maybe
+
+
+def test_texels_read_match_oracle(P):
+    """The statistics pass's distinct texels read by blended fragments (the
+    algorithmic texel bytes of the bench's traffic ratio) and distinct
+    splats blended lie between what the definition certainly reads and what
+    an admissible FP32 evaluation may read."""
+    scene = sg.make_scene(0)
+    env = sg.make_env(0)
+    cam = sg.look_at_camera((4.0, 0.0, 0.0), 128, 128)
+    kl = K.build_keys(scene, cam)
+    sc, out, saved = gpu_render(P, scene, env, cam)
+    st = saved.frag_stats()
+    sure, maybe, items_sure, items_maybe = oracle_texels_read(scene, cam, kl)
+    print(f"[texels] gpu {st['n_texels_read']} oracle sure {len(sure)} maybe {len(maybe)}; "
+          f"items gpu {st['n_items_blended']} sure {len(items_sure)} maybe {len(items_maybe)}")
+    assert len(sure) > 1000
+    assert len(sure) <= st["n_texels_read"] <= len(maybe)
+    assert len(items_sure) <= st["n_items_blended"] <= len(items_maybe)
+    assert st["n_items_blended"] <= st["n_visible"]
+
+
 def test_fp32_rate_probe(P):
     """The measured FP32 FMA rate (roofline denominator) is plausible for one
     B300-class GPU: 128 FP32 lanes x 148 SMs x ~2 GHz ~ 77 TFLOP/s."""

@@ -393,7 +393,9 @@ typedef struct ts_serve_stats {
  * batches to free memory (if every running batch is waiting, it proceeds and
  * is counted in over_budget, since memory held by uncollected results can
  * only come back through ts_server_wait); a batch that alone exceeds the
- * budget fails with TS_ERR_CAPACITY.  Scenes stay resident: requests name a
+ * budget fails with TS_ERR_CAPACITY, and so does a queued request that its
+ * scene's learned pair count puts above the whole budget (reported by
+ * ts_server_wait, counted as failed).  Scenes stay resident: requests name a
  * scene created and uploaded beforehand; it must outlive its requests. */
 ts_status ts_server_create(ts_server** out, int device, size_t arena_bytes, int n_streams, int max_batch);
 

@@ -19,7 +19,8 @@
 // waits until running batches free enough, unless every running batch is
 // waiting too (then it proceeds and is counted as over budget, since waiting
 // could not end).  A batch whose own memory exceeds the budget fails with
-// TS_ERR_CAPACITY.
+// TS_ERR_CAPACITY, and so does a queued request once its scene's learned
+// pair count puts it above the whole budget.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -52,6 +53,7 @@ struct Request {
   float* out = nullptr;
   double t_submit = 0.0, t_done = 0.0;
   int state = 0;     // 0 queued, 1 running, 2 done, 3 failed
+  bool admitted = false;  // its cost was added to the server's reserved bytes
   ts_status status = TS_OK;
   std::string err;
 };
@@ -104,6 +106,14 @@ size_t pair_estimate(const ts_camera& c, double ppp) {
 }
 
 void note_inflight(ts_server* sv) { sv->peak_reserved = std::max(sv->peak_reserved, sv->inflight); }
+
+// A request's admission bytes under the pairs per pixel its scene has shown
+// so far (at least the initial estimate).  Caller holds sv->mu.
+void refresh_cost(ts_server* sv, Request* r) {
+  auto it = sv->ppp.find(r->scene);
+  r->pairs = pair_estimate(r->cam, std::max(kInitialPairsPerPixel, it == sv->ppp.end() ? 0.0 : it->second));
+  r->cost = r->out_bytes + r->fixed + r->pairs;
+}
 
 // True-up of a batch's reservation once its pair count is known (called by
 // the render between its synchronisation and its pair-buffer allocations).
@@ -168,23 +178,42 @@ void worker_loop(ts_server* sv, int w) {
     batch.clear();
     {
       std::unique_lock<std::mutex> lk(sv->mu);
+      // wake for a front request that fits, or that no longer can fit
       sv->cv_work.wait(lk, [&] {
-        return sv->stop || (!sv->queue.empty() && sv->inflight + sv->queue.front()->cost <= sv->arena);
+        if (sv->stop) return true;
+        if (sv->queue.empty()) return false;
+        refresh_cost(sv, sv->queue.front());
+        return sv->queue.front()->cost > sv->arena || sv->inflight + sv->queue.front()->cost <= sv->arena;
       });
-      if (sv->stop && sv->queue.empty()) break;
       if (sv->stop) break;
+      // requests that their scene's learned pair count puts above the whole
+      // budget (admitted to the queue on a smaller estimate) fail here
+      // instead of blocking the queue
+      bool failed_any = false;
+      while (!sv->queue.empty()) {
+        Request* r = sv->queue.front();
+        refresh_cost(sv, r);
+        if (r->cost <= sv->arena) break;
+        sv->queue.pop_front();
+        r->state = 3;
+        r->status = TS_ERR_CAPACITY;
+        r->err = "server: the scene's pair count puts the request above the memory budget";
+        r->t_done = now_s();
+        ++sv->failed;
+        failed_any = true;
+      }
+      if (failed_any) sv->cv_done.notify_all();
+      if (sv->queue.empty()) continue;
       const int dtype = sv->queue.front()->dtype;
       while (!sv->queue.empty() && (int)batch.size() < sv->max_batch) {
         Request* r = sv->queue.front();
         if (r->dtype != dtype) break;
-        // the pair estimate from what this scene's renders have shown so far
-        auto it = sv->ppp.find(r->scene);
-        r->pairs = pair_estimate(r->cam, std::max(kInitialPairsPerPixel, it == sv->ppp.end() ? 0.0 : it->second));
-        r->cost = r->out_bytes + r->fixed + r->pairs;
+        refresh_cost(sv, r);  // the pair estimate from what this scene's renders have shown so far
         if (sv->inflight + r->cost > sv->arena) break;
         sv->queue.pop_front();
         sv->inflight += r->cost;
         r->state = 1;
+        r->admitted = true;
         batch.push_back(r);
       }
       if (!batch.empty()) {
@@ -350,9 +379,7 @@ ts_status ts_server_submit(ts_server* sv, ts_scene* scene, const ts_camera* cam,
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
-    auto it = sv->ppp.find(scene);
-    r->pairs = pair_estimate(*cam, std::max(kInitialPairsPerPixel, it == sv->ppp.end() ? 0.0 : it->second));
-    r->cost = r->out_bytes + r->fixed + r->pairs;
+    refresh_cost(sv, r);
     if (r->cost > sv->arena) {
       ++sv->rejected;
       delete r;
@@ -399,7 +426,7 @@ ts_status ts_server_wait(ts_server* sv, uint64_t ticket, float* out_rgba, int ou
     }
   }
   if (r->out) cudaFreeAsync(r->out, sv->copy_stream);
-  {
+  if (r->admitted) {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->inflight -= r->out_bytes;
   }

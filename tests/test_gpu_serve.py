@@ -162,6 +162,40 @@ def test_admission_trues_up_to_the_counted_pairs(P):
         srv.close()
 
 
+def test_request_that_outgrows_the_budget_fails_instead_of_blocking(P):
+    """Two requests admitted to the queue on the initial estimate, whose real
+    pairs do not fit the budget: the first fails at its true-up, and the
+    second, now estimated above the whole budget, fails with TS_ERR_CAPACITY
+    instead of waiting forever at the head of the queue; a small request
+    queued behind them is still served."""
+    from paper_2506_13348_b300._lib import TexSplatError
+    sc, cam = dense_scene(P)
+    probe = P.Server(arena_bytes=1 << 30, n_streams=1, max_batch=1)
+    est = probe.request_bytes(sc, cam)
+    probe.close()
+    ref, saved = P.render(sc, cam, save=True)
+    pairs = saved.sizes()[0]
+    saved.release()
+    real = est + (pairs / (256 * 256) - 32.0) * 256 * 256 * 16
+    arena = int((est + real) / 2)
+    small = dict(cam, W=16, H=16, cx=np.float32(8.0), cy=np.float32(8.0))
+    srv = P.Server(arena_bytes=arena, n_streams=1, max_batch=1)
+    try:
+        ta, tb, tc = srv.submit(sc, cam), srv.submit(sc, cam), srv.submit(sc, small)
+        for t in (ta, tb):
+            with pytest.raises(TexSplatError, match="CAPACITY"):
+                srv.wait(t, None, timeout_s=30.0)
+        out = torch.empty(16, 16, 4, dtype=torch.float32, device="cuda")
+        srv.wait(tc, out, timeout_s=30.0)
+        ref_small, _ = P.render(sc, small)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref_small)
+        st = srv.stats()
+        assert st["failed"] == 2 and st["completed"] == 1
+    finally:
+        srv.close()
+
+
 def test_two_workers_batches_overlap_on_the_device(P):
     """With two workers, batches of different workers run on the device at
     the same time: their device-time intervals (CUDA events on each

@@ -138,46 +138,68 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms around the
+    timed region; samples carry nvidia-smi's timestamp, and the summary is
+    taken over those inside the timed window [t0, t1] (host wall clock,
+    both ends after a device synchronisation)."""
 
     def __init__(self, gpu_index: int):
         self.path = tempfile.mktemp(suffix=".csv")
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # the timed region starts only once the sampler is producing
+        deadline = time.time() + 5.0
+        while self.proc is not None and time.time() < deadline:
+            if os.path.exists(self.path) and os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
-    def stop(self) -> dict:
+    def stop(self, t0: float, t1: float) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.05)  # one more sample past the end of the window
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for nm, val in zip(names, parts[5:9]):
-                    if val.lower() == "active":
-                        reasons.add(nm)
+            lines = f.readlines()
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarise_clocks(lines, t0, t1)
+
+
+def summarise_clocks(lines, t0: float, t1: float, interval_ms: int = 20) -> dict:
+    """Median SM clock, maximum clock and active slowdown reasons of the
+    nvidia-smi samples (timestamp first) inside [t0, t1] (all samples if
+    none fell inside)."""
+    import datetime
+    rows = []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            rows.append((ts, float(parts[2]), float(parts[3]),
+                         {nm for nm, val in zip(names, parts[6:10]) if val.lower() == "active"}))
+        except ValueError:
+            continue
+    inside = [r for r in rows if t0 <= r[0] <= t1]
+    use = inside if inside else rows
+    reasons = set().union(*[r[3] for r in use]) if use else set()
+    return {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
+            "sm_max_mhz": max(r[2] for r in use) if use else None,
+            "reasons": sorted(reasons), "samples": len(inside), "samples_total": len(rows),
+            "window_s": round(t1 - t0, 4), "interval_ms": interval_ms}
 
 
 def build_workload(seed_cams=0):
@@ -329,9 +351,12 @@ def run_ours(args):
     if pg:
         pg.barrier()
     sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    t_w0 = time.time()
     l0 = _lib.launch_count()
     ms = timed(args.steps, serial=False)
     launches = _lib.launch_count() - l0
+    t_w1 = time.time()  # timed() ends with a device synchronisation
     if pg:
         pg.barrier()
     # the same steps once more on one stream with per-stage CUDA events: the
@@ -342,7 +367,7 @@ def run_ours(args):
     ms_serial = timed(args.steps, serial=True)
     stages = _lib.profile_report()
     _lib.profile_enable(False)
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_w0, t_w1)
     ms_max = max_over_ranks(ms, pg, dev)
     value = aggregate_value(world, args.steps, ms_max)
 

@@ -23,3 +23,27 @@ def test_reference_arm_prints_one_contract_line(capsys, monkeypatch):
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["config"]["workload"] == bench.workload_config(1)["workload"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_clock_summary_keeps_the_samples_inside_the_timed_window():
+    """The bench's clock record is taken over the nvidia-smi samples whose
+    timestamps fall inside the timed window; a slowdown reason seen only
+    outside it is not attributed to the measurement."""
+    import datetime
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(ms, mhz, hw="Not Active", cap="Not Active"):
+        ts = (base + datetime.timedelta(milliseconds=ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2032, 700.00, 0x0, {hw}, Not Active, Not Active, {cap}\n"
+
+    lines = [line(0, 1200, hw="Active"), line(20, 2032), line(40, 2000, cap="Active"), line(60, 2032),
+             line(80, 900, hw="Active"), "garbage\n"]
+    t0 = (base + datetime.timedelta(milliseconds=10)).timestamp()
+    t1 = (base + datetime.timedelta(milliseconds=70)).timestamp()
+    c = bench.summarise_clocks(lines, t0, t1)
+    assert c["samples"] == 3 and c["samples_total"] == 5
+    assert c["sm_mhz"] == 2032.0 and c["sm_max_mhz"] == 2032.0
+    assert c["reasons"] == ["sw_power_cap"]
+    # no sample inside a window shorter than the interval: all samples count
+    c = bench.summarise_clocks(lines, t0, t0 + 0.001)
+    assert c["samples"] == 0 and "hw_slowdown" in c["reasons"]

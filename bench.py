@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpix/s fwd+bwd at 200k splats 800²; served-view p50/p99 latency vs plain"
 UNIT = "Mpix/s"
 N_SPLATS, T_TEX, RES, N_CAMS = 200_000, 8, 800, 100
+VIEWS_PER_STEP = 4  # views rendered and differentiated per launch sequence (one step)
 PREC_TILES = 16  # seeded covered 16x16 tiles (4096 px) per error view scored against the FP64 oracle
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM on this architecture (sm_100 family)
 
@@ -61,6 +62,8 @@ def parse():
     ap.add_argument("--cpu-tiles", type=int, default=6, help="tiles of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--views-per-step", type=int, default=VIEWS_PER_STEP,
+                    help="views batched into one launch sequence per step")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="one stream: each view's forward waits for the previous view's backward")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-view latency measurement")
@@ -114,18 +117,21 @@ def max_over_ranks(ms: float, pg, device) -> float:
     return float(t.item())
 
 
-def aggregate_value(world: int, steps: int, ms_max: float) -> float:
-    """Whole-job Mpix/s: every rank renders `steps` views of RES x RES."""
-    return world * steps * RES * RES / 1e6 / (ms_max / 1e3)
+def aggregate_value(world: int, steps: int, ms_max: float, views: int = 1) -> float:
+    """Whole-job Mpix/s: every rank renders `steps` steps of `views` views of RES x RES."""
+    return world * steps * views * RES * RES / 1e6 / (ms_max / 1e3)
 
 
-def workload_config(world: int, pipelined: bool = True) -> dict:
+def workload_config(world: int, pipelined: bool = True, views: int = VIEWS_PER_STEP) -> dict:
     return {"workload": "cfg1: 200k textured splats (160k sphere + 40k box), 8x8 texels x 8 ch, "
                         "800x800, forward + L1 loss + backward per view",
             "splats": N_SPLATS, "texels": f"{T_TEX}x{T_TEX}x8 f32", "resolution": f"{RES}x{RES}",
-            "views_per_step": 1, "parallelism": f"replicas x{world}",
-            "streams": ("2: view i+1's binning and forward overlap view i's backward" if pipelined
-                        else "1: views in sequence"),
+            "views_per_step": views,
+            "batching": (f"{views} views (cameras i..i+{views - 1} of the 100) per launch sequence: one binning, "
+                         "forward, loss and backward pass over all their tiles" if views > 1 else "one view per step"),
+            "parallelism": f"replicas x{world}",
+            "streams": ("2: step i+1's binning and forward overlap step i's backward" if pipelined
+                        else "1: steps in sequence"),
             "l2": "inputs larger than L2 (texel atlas 410 MB, records+pairs ~90 MB per view)"}
 
 
@@ -308,26 +314,33 @@ def run_ours(args):
 
     scene, env, cams = build_workload()
     sc = P.Scene.from_arrays(scene, env, device=local)
-    n_needed = min(N_CAMS, args.warmup + args.steps)
+    B = max(1, args.views_per_step)
+    n_needed = min(N_CAMS, (args.warmup + args.steps) * B)
     views = rank_views(rank, n_needed)
     my_cams = [cams[i] for i in views]
     targets = [torch.from_numpy(sg.make_target(i, RES, RES)).to(dev) for i in views]
     out = torch.empty(RES, RES, 4, dtype=torch.float32, device=dev)
     grads = P.zero_grads(sc)
     stream = torch.cuda.current_stream()
-    # views alternate between two streams: view i+1's binning and forward
-    # overlap view i's backward (gradients accumulate with atomics, so the
-    # two backwards may also overlap); each stream has its own image, loss
-    # and gradient-image buffers
+    # a step renders B views in one launch sequence (their tiles form one
+    # grid per kernel); steps alternate between two streams: step i+1's
+    # binning and forward overlap step i's backward (gradients accumulate
+    # with atomics, so the two backwards may also overlap); each stream has
+    # its own images, losses and gradient images
     streams = [stream] + ([torch.cuda.Stream(device=dev)] if not args.no_pipeline else [])
-    bufs = [(torch.empty_like(out), torch.empty_like(out), torch.zeros(1, dtype=torch.float32, device=dev))
-            for _ in streams]
+    bufs = [([torch.empty_like(out) for _ in range(B)], [torch.empty_like(out) for _ in range(B)],
+             torch.zeros(B, dtype=torch.float32, device=dev)) for _ in streams]
 
     def step(i, serial=False):
         k = 0 if serial else i % len(streams)
         st, (o, d, l) = streams[k], bufs[k]
-        _, saved = P.render(sc, my_cams[i % n_needed], out=o, save=True, stream=st)
-        P.l1_loss(o, targets[i % n_needed], l, d, stream=st)
+        vi = [(i * B + j) % n_needed for j in range(B)]
+        if B == 1:
+            _, saved = P.render(sc, my_cams[vi[0]], out=o[0], save=True, stream=st)
+        else:
+            _, saved = P.render_views([sc] * B, [my_cams[v] for v in vi], outs=o, save=True, stream=st)
+        for j, v in enumerate(vi):
+            P.l1_loss(o[j], targets[v], l[j:j + 1], d[j], stream=st)
         P.render_backward(saved, d, grads, stream=st)
         saved.release()
 
@@ -369,7 +382,7 @@ def run_ours(args):
     _lib.profile_enable(False)
     clocks = sampler.stop(t_w0, t_w1)
     ms_max = max_over_ranks(ms, pg, dev)
-    value = aggregate_value(world, args.steps, ms_max)
+    value = aggregate_value(world, args.steps, ms_max, B)
 
     # fragment statistics of a few of the timed views (untimed pass)
     fr = {"n_pairs": 0, "n_evaluated": 0, "n_blended": 0, "n_visible": 0, "n_texels_read": 0, "n_items_blended": 0}
@@ -381,9 +394,10 @@ def run_ours(args):
         for k in fr:
             fr[k] += s[k] / nstat
     npix = RES * RES
-    flops_fwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_FWD * fr["n_blended"] + FLOP_SHADE_FWD * npix
+    # per launch: each rasteriser launch covers the step's B views
+    flops_fwd = B * (FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_FWD * fr["n_blended"] + FLOP_SHADE_FWD * npix)
     # the shading adjoint (FLOP_SHADE_BWD per pixel) runs in k_shade_bwd, not in the rasteriser
-    flops_bwd = FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_BWD * fr["n_blended"]
+    flops_bwd = B * (FLOP_EVAL * fr["n_evaluated"] + FLOP_BLEND_BWD * fr["n_blended"])
     peaks, peak_kind = load_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -393,20 +407,22 @@ def run_ours(args):
     dom_ms = stage_ms.get(dom, float("nan"))
     dom_flops = flops_bwd if dom == "raster_bwd" else flops_fwd
     achieved = dom_flops / (dom_ms / 1e3) / 1e12
-    traffic = read_traffic(dom)
-    rbytes = raster_bytes(fr, npix)
+    traffic = read_traffic(dom, B)
+    rbytes = {k: B * v for k, v in raster_bytes(fr, npix).items()}
     # measured FP32 FMA rate of this GPU (after the timed region): context for
     # the derived peak above
     meas_scalar, meas_paired = (float("nan"), float("nan")) if args.no_fp32_probe else _lib.measure_fp32_peak(local)
 
     # HBM-side stages against the measured copy rate (algorithmic bytes / time)
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
-    sb = stage_bytes(len(scene["opacity"]), fr["n_pairs"], npix, ((RES + 15) // 16) ** 2)
+    # per launch: every stage covers the step's B views except the loss (one launch per view)
+    sb = {k: (v if k == "l1_loss" else B * v)
+          for k, v in stage_bytes(len(scene["opacity"]), fr["n_pairs"], npix, ((RES + 15) // 16) ** 2).items()}
     stage_fracs = {k: round(b / (stage_ms[k] / 1e3) / 1e9 / hbm_peak, 3) for k, b in sb.items() if k in stage_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(world, not args.no_pipeline),
+            "config": workload_config(world, not args.no_pipeline, B),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak,
                          "timing": "kernel's own CUDA events in a second timed pass of the same steps on one stream",
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
@@ -418,7 +434,7 @@ def run_ours(args):
                          "peak_measured": None if args.no_fp32_probe else {
                              "scalar_fma_tflops": round(meas_scalar, 2), "paired_fma_tflops": round(meas_paired, 2),
                              "frac_of_measured_scalar": achieved / meas_scalar}},
-            "roofline_fwd": roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar, rbytes),
+            "roofline_fwd": roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar, rbytes, B),
             "serial_ms_per_step": ms_serial / args.steps,
             "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
             "stage_hbm_frac": stage_fracs,
@@ -463,7 +479,7 @@ def run_ours(args):
     return 0
 
 
-def roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar, rbytes):
+def roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar, rbytes, views):
     """The roofline of the rasteriser that is not the dominant kernel (the
     forward, normally), on the same FLOP model, peak and per-stage event
     timing as the dominant one."""
@@ -471,7 +487,7 @@ def roofline_other(dom, stage_ms, flops_fwd, flops_bwd, fp32_peak, meas_scalar, 
     ms = stage_ms.get(other, float("nan"))
     flops = flops_fwd if other == "raster_fwd" else flops_bwd
     achieved = flops / (ms / 1e3) / 1e12
-    traffic = read_traffic(other)
+    traffic = read_traffic(other, views)
     return {"bound": "alu", "kernel": other, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic, "flops_per_launch": flops,
             "ms_per_launch": ms, "alg_bytes_per_launch": rbytes[other],
@@ -816,26 +832,28 @@ def time_image_loss(P, img, target, dev, reps=50):
 
 
 def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
-    """Same step through the public API with host buffers: each step's target
-    image goes host->device from pinned memory and its loss comes back.  The
-    copy runs on a side stream into one of two device buffers and overlaps the
-    render; the loss kernel waits for it.  Every copy is issued after the
-    start event and consumed before the end event, so all of them are inside
-    the timed region."""
+    """Same step through the public API with host buffers: each step's B
+    target images go host->device from pinned memory and their B losses come
+    back.  The copies run on a side stream into one of two sets of device
+    buffers and overlap the render; the loss kernels wait for them.  Every
+    copy is issued after the start event and consumed before the end event,
+    so all of them are inside the timed region."""
     import torch
 
     import scenegen as sg
+    B = max(1, args.views_per_step)
     host_t = [torch.from_numpy(sg.make_target(i, RES, RES)).pin_memory() for i in range(min(8, n_needed))]
     stream = torch.cuda.current_stream()
-    # as the timed loop: views alternate between the compute streams; per
-    # stream a device target, image, gradient image, loss and pinned loss
+    # as the timed loop: steps alternate between the compute streams; per
+    # stream B device targets, images and gradient images, B losses and
+    # their pinned host copy
     streams = [stream] + ([torch.cuda.Stream(device=dev)] if not args.no_pipeline else [])
     ns = len(streams)
-    dev_t = [torch.empty(RES, RES, 4, dtype=torch.float32, device=dev) for _ in range(ns)]
-    outs = [torch.empty_like(dev_t[0]) for _ in range(ns)]
-    dls = [torch.empty_like(dev_t[0]) for _ in range(ns)]
-    losses = [torch.zeros(1, dtype=torch.float32, device=dev) for _ in range(ns)]
-    loss_h = [torch.zeros(1, dtype=torch.float32).pin_memory() for _ in range(ns)]
+    dev_t = [[torch.empty(RES, RES, 4, dtype=torch.float32, device=dev) for _ in range(B)] for _ in range(ns)]
+    outs = [[torch.empty_like(dev_t[0][0]) for _ in range(B)] for _ in range(ns)]
+    dls = [[torch.empty_like(dev_t[0][0]) for _ in range(B)] for _ in range(ns)]
+    losses = [torch.zeros(B, dtype=torch.float32, device=dev) for _ in range(ns)]
+    loss_h = [torch.zeros(B, dtype=torch.float32).pin_memory() for _ in range(ns)]
     grads = P.zero_grads(sc)
     copy_stream = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event() for _ in range(ns)]
@@ -844,13 +862,19 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
     def step(i):
         b = i % ns
         st = streams[b]
+        vi = [(i * B + j) % n_needed for j in range(B)]
         with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(used[b])  # the buffer's previous loss read is done
-            dev_t[b].copy_(host_t[i % len(host_t)], non_blocking=True)
+            copy_stream.wait_event(used[b])  # the buffers' previous loss reads are done
+            for j, v in enumerate(vi):
+                dev_t[b][j].copy_(host_t[v % len(host_t)], non_blocking=True)
             copied[b].record(copy_stream)
-        _, saved = P.render(sc, cams[i % n_needed], out=outs[b], save=True, stream=st)
+        if B == 1:
+            _, saved = P.render(sc, cams[vi[0]], out=outs[b][0], save=True, stream=st)
+        else:
+            _, saved = P.render_views([sc] * B, [cams[v] for v in vi], outs=outs[b], save=True, stream=st)
         st.wait_event(copied[b])
-        P.l1_loss(outs[b], dev_t[b], losses[b], dls[b], stream=st)
+        for j in range(B):
+            P.l1_loss(outs[b][j], dev_t[b][j], losses[b][j:j + 1], dls[b][j], stream=st)
         used[b].record(st)
         P.render_backward(saved, dls[b], grads, stream=st)
         saved.release()
@@ -874,9 +898,9 @@ def run_e2e(P, sc, cams, n_needed, args, dev, pg, world):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
-    return {"value": aggregate_value(world, args.steps, ms), "unit": UNIT,
-            "h2d_bytes_per_step": RES * RES * 4 * 4, "d2h_bytes_per_step": 4,
-            "note": "target H2D on a side stream overlapping the render; views on "
+    return {"value": aggregate_value(world, args.steps, ms, B), "unit": UNIT,
+            "h2d_bytes_per_step": B * RES * RES * 4 * 4, "d2h_bytes_per_step": 4 * B,
+            "note": f"{B} targets H2D per step on a side stream overlapping the render; steps on "
                     f"{'two streams as the timed loop' if not args.no_pipeline else 'one stream'}"}
 
 
@@ -898,35 +922,20 @@ def kernel_source_hash(kernel: str) -> str:
     return h.hexdigest()
 
 
-def read_traffic(kernel: str):
+def read_traffic(kernel: str, views: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current source of that kernel; else None."""
+    was taken on the current source of that kernel and on launches covering
+    `views` views (the bench's views per step); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     with open(path) as f:
-        rec = json.load(f)
-    ent = rec.get(kernel)
-    if not ent or ent.get("source_sha256") != kernel_source_hash(kernel):
+        ent = json.load(f).get(kernel)
+    if not ent or ent.get("source_sha256") != kernel_source_hash(kernel) or ent.get("views_per_launch") != views:
         return None
     return ent.get("dram_bytes_per_launch")
 
 
-# Algorithmic bytes of the HBM-side stages (per splat N, pair K, pixel P of
-# the view): what each stage must read and write once.
-#   preprocess: parameters 40 B in; record 80 + count 4 + depth key 8 + id 4 +
-#     tile rect 16 B out                                    -> 152 B / splat
-#   sort_splats: 4 passes x (key 8 + id 4 in, 12 out, 8 histogram read)
-#                                                           -> 128 B / splat
-#   scan_counts: gather 12 B + scan 8 B                     ->  20 B / splat
-#   emit_pairs: 8 B out per pair; order, offset, count, rect in (28 B / splat)
-#   sort_pairs: 2 passes x (4 histogram + 8 in + 8 out)     ->  40 B / pair
-#   tile_ranges: 4 B / pair in, 8 B / tile out; the forward's tile order:
-#     ranges 8 in, key + id 8 out, one sort pass 20      ->  36 B / tile
-#   shade_bwd: G-buffer 32 + coverage 4 + dL/drgba 16 in, 48 out -> 100 B / pixel
-#   preprocess_bwd: record gradients 112 in (every item); parameters 40 in,
-#     gradients 40 out (items with a gradient)              -> 192 B / splat at most
-#   l1_loss: image 16 + target 16 in, gradient 16 out       ->  48 B / pixel
 # Algorithmic bytes of the two rasterisers (per view): what each must move
 # at least once.  Both read the pair list (4 B per pair), the first 48 B of
 # every visible splat's record (block test and fragment), the last 32 B of

@@ -111,3 +111,35 @@ def test_batch_of_the_maximum_view_count_equals_alone_renders(P):
         assert torch.equal(a, o)
     with pytest.raises(P.TexSplatError, match="TS_ERR_ARG"):
         P.render_views([sc] * 33, cams + cams[:1])
+
+
+def test_batched_backward_equals_the_sum_of_view_backwards(P):
+    """One launch sequence over four views (the training bench's step):
+    images bit-identical to the views rendered alone, and the accumulated
+    gradients equal the sum of the four single-view backwards up to the
+    order of the atomic additions (1e-4 of each group's maximum)."""
+    scene = sg.make_scene(1, n=20000, T=8, seed=21)
+    env = sg.make_env(1, cube_res=16, levels=1, irr_res=8, lut_res=32)
+    cams = sg.fibonacci_cameras(4, 4.0, 192, 160)
+    sc = P.Scene.from_arrays(scene, env)
+    rng = np.random.default_rng(3)
+    dls = [torch.from_numpy(rng.normal(size=(160, 192, 4)).astype(np.float32)).cuda() for _ in cams]
+    outs, saved = P.render_views([sc] * 4, cams, save=True)
+    g_batch = P.zero_grads(sc)
+    P.render_backward(saved, dls, g_batch)
+    saved.release()
+    g_sum = P.zero_grads(sc)
+    for c, d, o in zip(cams, dls, outs):
+        a, sv = P.render(sc, c, save=True)
+        P.render_backward(sv, d, g_sum)
+        sv.release()
+        torch.cuda.synchronize()
+        assert torch.equal(a, o)
+    torch.cuda.synchronize()
+    for k in g_batch:
+        a, b = g_batch[k].double(), g_sum[k].double()
+        scale = float(b.abs().max())
+        assert scale > 0.0, k
+        err = float((a - b).abs().max())
+        print(f"[batch] {k}: max |batched - summed| {err:.3g} of max {scale:.3g}")
+        assert err <= 1e-4 * scale + 1e-9, (k, err, scale)

@@ -120,14 +120,17 @@ __device__ __forceinline__ void tex_fetch(const ViewDesc& V, long long splat, in
                                           float out[8]) {
   float t0[8], t1[8], t2[8], t3[8];
   tex_corners<DT>(V, splat, T, s, t0, t1, t2, t3);
+  // the four corner weights (the same products the backward uses)
   const float gx = 1.f - s.fx, gy = 1.f - s.fy;
-  const float2 FX = f2(s.fx, s.fx), GX = f2(gx, gx), FY = f2(s.fy, s.fy), GY = f2(gy, gy);
+  const float2 w01 = mul2(f2(gx, s.fx), f2(gy, gy)), w23 = mul2(f2(gx, s.fx), f2(s.fy, s.fy));
+  const float2 W0 = f2(w01.x, w01.x), W1 = f2(w01.y, w01.y), W2 = f2(w23.x, w23.x), W3 = f2(w23.y, w23.y);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int c = 2 * q;
-    const float2 top = fma2(FX, f2(t1[c], t1[c + 1]), mul2(GX, f2(t0[c], t0[c + 1])));
-    const float2 bot = fma2(FX, f2(t3[c], t3[c + 1]), mul2(GX, f2(t2[c], t2[c + 1])));
-    const float2 o = fma2(FY, bot, mul2(GY, top));
+    float2 o = mul2(W0, f2(t0[c], t0[c + 1]));
+    o = fma2(W1, f2(t1[c], t1[c + 1]), o);
+    o = fma2(W2, f2(t2[c], t2[c + 1]), o);
+    o = fma2(W3, f2(t3[c], t3[c + 1]), o);
     out[c] = o.x;
     out[c + 1] = o.y;
   }

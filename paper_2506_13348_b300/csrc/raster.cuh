@@ -115,15 +115,44 @@ __device__ __forceinline__ void tex_corners(const ViewDesc& V, long long splat, 
 }
 
 // Bilinear texel fetch (Eq. 6) of the 8 channels, as 4 channel pairs.
-template <int DT>
+// PHASED (float32 texels in 32-byte loads): the two corners of the upper row
+// are loaded and summed before those of the lower row, so 16 texel registers
+// are live instead of 32 (the forward instances with indirect light or
+// two-component normals, whose other state would otherwise spill); the sums
+// are the same operations in the same order either way.
+template <int DT, bool PHASED = false>
 __device__ __forceinline__ void tex_fetch(const ViewDesc& V, long long splat, int T, const TexSample& s,
                                           float out[8]) {
-  float t0[8], t1[8], t2[8], t3[8];
-  tex_corners<DT>(V, splat, T, s, t0, t1, t2, t3);
   // the four corner weights (the same products the backward uses)
   const float gx = 1.f - s.fx, gy = 1.f - s.fy;
   const float2 w01 = mul2(f2(gx, s.fx), f2(gy, gy)), w23 = mul2(f2(gx, s.fx), f2(s.fy, s.fy));
   const float2 W0 = f2(w01.x, w01.x), W1 = f2(w01.y, w01.y), W2 = f2(w23.x, w23.x), W3 = f2(w23.y, w23.y);
+  if (PHASED && DT == DT_F32 && V.tex_v8) {
+    const float* c = reinterpret_cast<const float*>(V.texels) + splat * (long long)(T * T * 8);
+    const unsigned ra = (unsigned)(s.ja * T), rb = (unsigned)(s.jb * T);
+    float ta[8], tb[8];
+    load_texel_v8_ordered(c + (ra + s.ia) * 8u, ta);
+    load_texel_v8_ordered(c + (ra + s.ib) * 8u, tb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 2 * q;
+      const float2 o = fma2(W1, f2(tb[k], tb[k + 1]), mul2(W0, f2(ta[k], ta[k + 1])));
+      out[k] = o.x;
+      out[k + 1] = o.y;
+    }
+    load_texel_v8_ordered(c + (rb + s.ia) * 8u, ta);
+    load_texel_v8_ordered(c + (rb + s.ib) * 8u, tb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 2 * q;
+      const float2 o = fma2(W3, f2(tb[k], tb[k + 1]), fma2(W2, f2(ta[k], ta[k + 1]), f2(out[k], out[k + 1])));
+      out[k] = o.x;
+      out[k + 1] = o.y;
+    }
+    return;
+  }
+  float t0[8], t1[8], t2[8], t3[8];
+  tex_corners<DT>(V, splat, T, s, t0, t1, t2, t3);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int c = 2 * q;

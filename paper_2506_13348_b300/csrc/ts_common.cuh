@@ -173,6 +173,15 @@ __device__ __forceinline__ void load_texel_v8(const float* p, float out[8]) {
       : "l"(p));
 }
 
+// The same, kept in program order relative to the other ordered loads
+// (volatile): callers that consume texels in phases keep fewer live.
+__device__ __forceinline__ void load_texel_v8_ordered(const float* p, float out[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(out[0]), "=f"(out[1]), "=f"(out[2]), "=f"(out[3]), "=f"(out[4]), "=f"(out[5]), "=f"(out[6]),
+                 "=f"(out[7])
+               : "l"(p));
+}
+
 __device__ __forceinline__ void load_texel(const void* base, int dtype, long long idx, float out[8]) {
   if (dtype == DT_F32) {
     const float4* p = reinterpret_cast<const float4*>(base) + idx * 2;

@@ -118,8 +118,10 @@ __device__ __forceinline__ void tex_corners(const ViewDesc& V, long long splat, 
 // PHASED (float32 texels in 32-byte loads): the two corners of the upper row
 // are loaded and summed before those of the lower row, so 16 texel registers
 // are live instead of 32 (the forward instances with indirect light or
-// two-component normals, whose other state would otherwise spill); the sums
-// are the same operations in the same order either way.
+// two-component normals, whose other state would otherwise spill, and the
+// non-saving ones, where it measured faster); the sums are the same
+// operations in the same order either way, so saving and non-saving renders
+// give the same image.
 template <int DT, bool PHASED = false>
 __device__ __forceinline__ void tex_fetch(const ViewDesc& V, long long splat, int T, const TexSample& s,
                                           float out[8]) {

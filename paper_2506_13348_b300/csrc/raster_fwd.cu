@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_
             float x[8];
             if (SMP == SMP_SOFTWARE) {
               const TexSample ts_ = tex_setup(f.u, f.v, T);
-              tex_fetch<DT, FEAT != 0>(V, splat, T, ts_, x);
+              tex_fetch<DT, FEAT != 0 || !SAVE>(V, splat, T, ts_, x);
               if (STATS) {  // the four texels this fragment reads
                 uint32_t* w = stats.touched + (size_t)s_it[warp][b][t] * stats.words_per_item;
                 const int q0 = ts_.ja * T + ts_.ia, q1 = ts_.ja * T + ts_.ib;

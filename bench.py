@@ -922,11 +922,14 @@ def kernel_source_hash(kernel: str) -> str:
     return h.hexdigest()
 
 
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+
+
 def read_traffic(kernel: str, views: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current source of that kernel and on launches covering
     `views` views (the bench's views per step); else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = TRAFFIC_PATH
     if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     with open(path) as f:

@@ -47,3 +47,21 @@ def test_clock_summary_keeps_the_samples_inside_the_timed_window():
     # no sample inside a window shorter than the interval: all samples count
     c = bench.summarise_clocks(lines, t0, t0 + 0.001)
     assert c["samples"] == 0 and "hw_slowdown" in c["reasons"]
+
+
+def test_committed_traffic_is_used_only_for_the_profiled_source_and_launch(monkeypatch, tmp_path):
+    """A DRAM-traffic figure from the committed ncu summary is reported only
+    while the kernel's sources hash to the profiled value and the bench
+    launches as many views per launch as the profiled launch covered."""
+    import json
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = bench.kernel_source_hash("raster_bwd")
+    (prof / "traffic.json").write_text(json.dumps(
+        {"raster_bwd": {"dram_bytes_per_launch": 123, "views_per_launch": 4, "source_sha256": h},
+         "raster_fwd": {"dram_bytes_per_launch": 456, "views_per_launch": 4, "source_sha256": "0" * 64}}))
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(prof / "traffic.json"))
+    assert bench.read_traffic("raster_bwd", 4) == 123
+    assert bench.read_traffic("raster_bwd", 1) is None      # another launch size
+    assert bench.read_traffic("raster_fwd", 4) is None      # sources changed since the capture
+    assert bench.read_traffic("sort_pairs", 4) is None      # not a profiled kernel

@@ -3,7 +3,8 @@ by one), the 1k-splat gradient slice, and GPU central differences.
 
 * 200k splats, 800x800 (the benchmarked training view): the whole tile/sort
   list bit-exact, 4096 sampled pixels within 1e-4 of an admissible oracle
-  result (at most 0.1 % masked, the fraction printed);
+  result (at most 0.1 % masked, the fraction printed); the same for the
+  benchmarked launch of four such views;
 * 500k splats, 16x16 texels, 1920x1080, 6-level FP16 cube, BF16 / FP16
   atlases: sampled pixels within 1e-4 of an oracle fed the same rounded
   texels and cube;
@@ -49,6 +50,42 @@ def oracle_pixels(scene, cam, env, px, py, kl, chunk=256, **kw):
 def check_sampled(out, ref, px, py, tol=IMG_TOL, max_masked=1e-3, label=""):
     g = out.cpu().numpy()[py, px].astype(np.float64)
     return check_admissible(g, ref, tol, max_masked, label)["max_err"]
+
+
+def test_cfg1_four_view_launch_keys_and_sampled_pixels(P):
+    """The benchmarked launch: four 800x800 views of the 200k-splat scene in
+    one launch sequence.  Each view's tile/sort lists are bit-exact (items
+    offset by v x n, list positions by the earlier views' pairs), and 1024
+    sampled pixels per view (4096 in all) are within 1e-4 of an admissible
+    oracle result, at most 0.1 % masked."""
+    scene = sg.make_scene(1)
+    env = sg.make_env(1, cube_res=32, levels=1, irr_res=8, lut_res=128)
+    cams = sg.fibonacci_cameras(100, 4.0, 800, 800)[40:44]
+    n = len(scene["opacity"])
+    sc = P.Scene.from_arrays(scene, env)
+    outs, saved = P.render_views([sc] * 4, cams, save=True)
+    torch.cuda.synchronize()
+    ids, rng_t, _ = saved.lists(4 * n)
+    rng = np.random.default_rng(11)
+    k_off = t_off = 0
+    gs, refs = [], []
+    for v, cam in enumerate(cams):
+        kl = K.build_keys(scene, cam)
+        kv = kl["ids"].size
+        assert kv > 5_000_000
+        np.testing.assert_array_equal(ids[k_off:k_off + kv], kl["ids"].astype(np.int64) + v * n)
+        nt = kl["tile_ranges"].shape[0]
+        ne = kl["tile_ranges"][:, 1] > kl["tile_ranges"][:, 0]
+        np.testing.assert_array_equal(rng_t[t_off:t_off + nt][ne], kl["tile_ranges"][ne] + k_off)
+        k_off += kv
+        t_off += nt
+        px, py = sample_pixels(rng, 800, 800, N_SAMPLES // 4)
+        refs.append(oracle_pixels(scene, cam, env, px, py, kl))
+        gs.append(outs[v].cpu().numpy()[py, px].astype(np.float64))
+    saved.release()
+    ref = {k: torch.cat([r[k] for r in refs]) for k in ("rgba", "ambiguous", "alt_mask")}
+    ref["alt"] = {"rgba": torch.cat([r["alt"]["rgba"] for r in refs])}
+    check_admissible(np.concatenate(gs), ref, IMG_TOL, 1e-3, "cfg1 4-view launch")
 
 
 def test_cfg1_full_size_keys_and_sampled_pixels(P):

@@ -4,7 +4,8 @@ by one), the 1k-splat gradient slice, and GPU central differences.
 * 200k splats, 800x800 (the benchmarked training view): the whole tile/sort
   list bit-exact, 4096 sampled pixels within 1e-4 of an admissible oracle
   result (at most 0.1 % masked, the fraction printed); the same for the
-  benchmarked launch of four such views;
+  benchmarked launch of four such views, whose backward equals the sum of
+  the four single-view backwards;
 * 500k splats, 16x16 texels, 1920x1080, 6-level FP16 cube, BF16 / FP16
   atlases: sampled pixels within 1e-4 of an oracle fed the same rounded
   texels and cube;
@@ -86,6 +87,43 @@ def test_cfg1_four_view_launch_keys_and_sampled_pixels(P):
     ref = {k: torch.cat([r[k] for r in refs]) for k in ("rgba", "ambiguous", "alt_mask")}
     ref["alt"] = {"rgba": torch.cat([r["alt"]["rgba"] for r in refs])}
     check_admissible(np.concatenate(gs), ref, IMG_TOL, 1e-3, "cfg1 4-view launch")
+
+
+def test_cfg1_four_view_backward_equals_single_view_backwards(P):
+    """The benchmarked step's backward (four 800x800 views of the 200k-splat
+    scene in one launch, L1 gradients against the seeded targets) equals the
+    sum of the four views' single-view backwards up to the order of the
+    atomic additions (1e-4 of each group's maximum); with the single-view
+    backward checked against the oracle on the 1k-splat slice below, this
+    carries the gradient parity to the benchmarked launch."""
+    scene = sg.make_scene(1)
+    env = sg.make_env(1, cube_res=32, levels=1, irr_res=8, lut_res=128)
+    cams = sg.fibonacci_cameras(100, 4.0, 800, 800)[40:44]
+    sc = P.Scene.from_arrays(scene, env)
+    targets = [torch.from_numpy(sg.make_target(40 + i, 800, 800)).cuda() for i in range(4)]
+    loss = torch.zeros(4, device="cuda")
+    outs, saved = P.render_views([sc] * 4, cams, save=True)
+    dls = [torch.empty_like(o) for o in outs]
+    for j in range(4):
+        P.l1_loss(outs[j], targets[j], loss[j:j + 1], dls[j])
+    g_batch = P.zero_grads(sc)
+    P.render_backward(saved, dls, g_batch)
+    saved.release()
+    g_sum = P.zero_grads(sc)
+    for j, c in enumerate(cams):
+        o, sv = P.render(sc, c, save=True)
+        d = torch.empty_like(o)
+        P.l1_loss(o, targets[j], loss[j:j + 1], d)
+        P.render_backward(sv, d, g_sum)
+        sv.release()
+    torch.cuda.synchronize()
+    for k in g_batch:
+        a, b = g_batch[k].double(), g_sum[k].double()
+        scale = float(b.abs().max())
+        err = float((a - b).abs().max())
+        print(f"[batch] cfg1 {k}: max |batched - summed| {err:.3g} of max {scale:.3g}")
+        assert scale > 0.0, k
+        assert err <= 1e-4 * scale, (k, err, scale)
 
 
 def test_cfg1_full_size_keys_and_sampled_pixels(P):

@@ -178,9 +178,13 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
  * batched form, in view order).  Gradients are accumulated into `grads`
  * (one set per scene; for the batched form all views must share one scene).
  * The saved handle stays valid (backward may be repeated).  The backward
- * rasteriser takes the tiles by the list entries it walks (up to each
- * pixel's last blended entry), longest first; temporaries are allocated with
- * cudaMallocAsync on `stream`. */
+ * recomputes each fragment from the scene's current splats, texels and
+ * environment (only the lists and per-pixel state are saved), so the scene
+ * must not change between the forward and its backward: update parameters
+ * after the backward (as api.Trainer and the autograd wrapper do).  The
+ * backward rasteriser takes the tiles by the list entries it walks (up to
+ * each pixel's last blended entry), longest first; temporaries are allocated
+ * with cudaMallocAsync on `stream`. */
 ts_status ts_render_backward(const ts_saved* saved, const float* const* dL_drgba,
                              const ts_grads* grads, void* stream);
 

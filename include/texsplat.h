@@ -181,7 +181,11 @@ ts_status ts_render_views(ts_scene* const* scenes, const ts_camera* cams, int n_
  * recomputes each fragment from the scene's current splats, texels and
  * environment (only the lists and per-pixel state are saved), so the scene
  * must not change between the forward and its backward: update parameters
- * after the backward (as api.Trainer and the autograd wrapper do).  The
+ * after the backward (as api.Trainer and the autograd wrapper do).  An upload
+ * that replaced a scene's buffers since the forward (ts_upload_gaussians,
+ * ts_upload_atlas, ts_upload_envmap, a new SH degree or count) makes this
+ * call return TS_ERR_STATE instead of reading the freed buffers; a scene must
+ * outlive its saved states.  The
  * backward rasteriser takes the tiles by the list entries it walks (up to
  * each pixel's last blended entry), longest first; temporaries are allocated
  * with cudaMallocAsync on `stream`. */

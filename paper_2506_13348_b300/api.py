@@ -312,7 +312,10 @@ class TexSplatRender(torch.autograd.Function):
     logit_opacity, texels, spec (flat, all levels), irr.  The activations run
     in the library (ts_activate), the parameters are copied into ``scene``
     on each forward (device to device) and the backward is the library's
-    hand-written adjoint followed by the activations' chain rule."""
+    hand-written adjoint followed by the activations' chain rule.  Because
+    each forward re-uploads the scene, a second forward on the same scene
+    before the first one's backward invalidates the first (its backward then
+    raises TS_ERR_STATE): use one scene per pending forward."""
 
     @staticmethod
     def forward(ctx, scene: Scene, cam: dict, env_lut, means, quats, log_scales, logit_opacity, texels, spec_flat,

@@ -127,6 +127,7 @@ struct ts_scene {
   float* lut = nullptr;
   int lut_res = 0;
   int64_t tex_version = 0;  // bumped by every ts_upload_atlas
+  int64_t gen = 0;          // bumped whenever an upload replaces (and frees) device buffers
   // 2-D hardware-texture atlases (supplementary Sec. 1) and the indirection buffer
   cudaArray_t a2d[2] = {nullptr, nullptr};
   cudaTextureObject_t a2d_tex[2] = {0, 0};
@@ -155,7 +156,18 @@ struct ts_saved {
   uint32_t* depth_bits = nullptr;
   std::vector<void*> bufs;  // owned, cudaMallocAsync'ed on `stream`
   int64_t K = 0;
+  std::vector<int64_t> gens;  // each view's scene generation at the forward
 };
+
+namespace {
+// The saved state keeps pointers into its scenes' buffers: a backward (or a
+// recount) after an upload replaced them would read freed memory.
+bool scenes_unchanged(const ts_saved* sv) {
+  for (size_t i = 0; i < sv->scenes.size(); ++i)
+    if (i >= sv->gens.size() || sv->scenes[i]->gen != sv->gens[i]) return false;
+  return true;
+}
+}  // namespace
 
 int ts::set_error(int code, const std::string& msg) { return fail(code, msg); }
 
@@ -280,6 +292,7 @@ ts_status ts_upload_gaussians(ts_scene* s, int64_t n, const float* means, const 
   }
   for (void* p : {(void*)s->means, (void*)s->quats, (void*)s->scales, (void*)s->opacity})
     if (p) cudaFree(p);
+  s->gen += 1;
   s->means = m4;
   s->quats = q4;
   s->scales = s2;
@@ -327,6 +340,7 @@ ts_status ts_upload_atlas(ts_scene* s, int T, int C, ts_dtype store, const float
   }
   TS_UP(cudaStreamSynchronize(st));
   if (s->texels) cudaFree(s->texels);
+  s->gen += 1;
   s->texels = tex;
   s->tex_version += 1;  // any 2-D atlas built from the old texels is stale
   s->T = T;
@@ -380,6 +394,7 @@ ts_status ts_upload_envmap(ts_scene* s, int levels, int base_res, const float* s
   TS_UP(cudaStreamSynchronize(st));
   for (void* p : {s->spec, s->irr, (void*)s->lut})
     if (p) cudaFree(p);
+  s->gen += 1;
   s->spec = d_spec;
   s->irr = d_irr;
   s->lut = d_lut;
@@ -697,6 +712,7 @@ ts_status ts::render_views_hooked(ts_scene* const* scenes, const ts_camera* cams
     sv->indirect = indirect;
     sv->feat = feat;
     sv->scenes.assign(scenes, scenes + n_views);
+    for (int i = 0; i < n_views; ++i) sv->gens.push_back(scenes[i]->gen);
     sv->rec = rec;
     sv->pair_items = pitems;
     sv->tile_keys = tkeys;
@@ -733,6 +749,8 @@ ts_status ts_release_saved(ts_saved* sv) {
 
 ts_status ts_render_backward(const ts_saved* sv, const float* const* dL_drgba, const ts_grads* grads, void* stream) {
   if (!sv || !dL_drgba || !grads) return fail(TS_ERR_ARG, "ts_render_backward: NULL argument");
+  if (!scenes_unchanged(sv))
+    return fail(TS_ERR_STATE, "ts_render_backward: a scene was re-uploaded since the forward (render again)");
   const ts_scene* s = sv->scenes[0];
   for (ts_scene* o : sv->scenes)
     if (o != s) return fail(TS_ERR_ARG, "ts_render_backward: views of one backward must share one scene");
@@ -868,6 +886,8 @@ ts_status ts_normal_loss(ts_saved* sv, int view, float weight, float* loss, void
 
 ts_status ts_saved_frag_stats(const ts_saved* sv, ts_frag_stats* out, void* stream) {
   if (!sv || !out) return fail(TS_ERR_ARG, "ts_saved_frag_stats: NULL argument");
+  if (!scenes_unchanged(sv))
+    return fail(TS_ERR_STATE, "ts_saved_frag_stats: a scene was re-uploaded since the forward (render again)");
   cudaStream_t st = (cudaStream_t)stream;
   TS_CUDA(cudaSetDevice(sv->device));
   ViewTable vt = sv->vt;
@@ -930,6 +950,7 @@ ts_status ts_upload_indirect(ts_scene* s, int degree, const float* coeffs, int s
   }
   TS_CUDA(cudaStreamSynchronize(st));
   if (s->sh) cudaFree(s->sh);
+  s->gen += 1;
   s->sh = nullptr;
   s->sh_deg = -1;
   s->sh_stride = 0;

@@ -125,6 +125,34 @@ def test_injected_allocation_failures_leave_state_intact(P):
         L.ts_debug_fail_alloc(-1)
 
 
+def test_backward_after_a_reupload_is_refused(P):
+    """A saved forward keeps pointers into its scene's buffers; after an
+    upload replaced them (new texels, geometry or environment), the backward
+    and the fragment recount return TS_ERR_STATE instead of reading freed
+    memory, and a fresh render's backward works again."""
+    scene = sg.make_scene(0, n=300, T=4, seed=3)
+    env = sg.make_env(0, cube_res=8, levels=1, irr_res=4, lut_res=16)
+    cam = sg.look_at_camera((3.5, 0.5, 0.5), 64, 48)
+    sc = P.Scene.from_arrays(scene, env)
+    dl = torch.ones(48, 64, 4, device="cuda")
+    for redo in (lambda: sc.upload_atlas(scene["texels"], "f32"),
+                 lambda: sc.upload_gaussians(scene["means"], scene["quats"], scene["scales"], scene["opacity"]),
+                 lambda: sc.upload_envmap(env, "f32")):
+        _, saved = P.render(sc, cam, save=True)
+        redo()
+        with pytest.raises(P.TexSplatError, match="TS_ERR_STATE"):
+            P.render_backward(saved, dl, P.zero_grads(sc))
+        with pytest.raises(P.TexSplatError, match="TS_ERR_STATE"):
+            saved.frag_stats()
+        saved.release()
+        _, saved = P.render(sc, cam, save=True)
+        g = P.zero_grads(sc)
+        P.render_backward(saved, dl, g)
+        torch.cuda.synchronize()
+        assert float(g["texels"].abs().sum()) > 0.0
+        saved.release()
+
+
 def test_server_budget_limits(P):
     """A zero-byte arena is refused at creation; a request larger than the
     arena is rejected at submission (TS_ERR_CAPACITY, counted), and a

@@ -6,9 +6,11 @@ Workload (synthetic, seeded; stands in for the paper's Shiny Blender
 object captures): 160k splats on a unit sphere + 40k in a [-1,1]^3 box,
 8x8 texels x 8 channels, 100 cameras on a radius-4 Fibonacci sphere, 800x800,
 L1 loss to seeded U[0,1] targets, 32x32 cube + 8x8 irradiance + 128x128 BRDF
-table.  One step = one view: render (with saved state), loss, backward.
-Gradients accumulate over the steps (a multi-view gradient accumulation), so
-every step does the full forward and backward.
+table.  One step = four views (--views-per-step) in one launch sequence:
+binning, render (with saved state), the four losses, backward.  Gradients
+accumulate over the views and steps (a multi-view gradient accumulation), so
+every view gets the full forward and backward; consecutive steps alternate
+between two CUDA streams (--no-pipeline: one).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 

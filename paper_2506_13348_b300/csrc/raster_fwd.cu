@@ -29,8 +29,14 @@
 
 namespace ts {
 
-template <int DT, bool SAVE, bool STATS, int SMP, int FEAT = 0>
-__global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
+// WIDE: the instance for large grids (kWideTiles tiles or more): 8 CTAs per
+// SM at 64 registers instead of 6 at 80, the texel corners loaded in two
+// phases to fit; it pays once the grid is many waves deep (4 views of 800x800:
+// 2.021 -> 1.968 ms) and loses on a single view's grid (0.614 -> 0.674 ms),
+// where the longer per-CTA time stretches the last wave.  Same arithmetic,
+// same image.
+template <int DT, bool SAVE, bool STATS, int SMP, int FEAT = 0, bool WIDE = false>
+__global__ void __launch_bounds__(32 * kRasterWarps, WIDE ? 8 : 3 * kCtasPerTile) k_raster_fwd(ViewTable vt, const Record* __restrict__ rec,
                                                      const uint32_t* __restrict__ pair_items,
                                                      const uint2* __restrict__ ranges, FragCounters stats) {
   constexpr unsigned FULL = 0xffffffffu;
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_
             float x[8];
             if (SMP == SMP_SOFTWARE) {
               const TexSample ts_ = tex_setup(f.u, f.v, T);
-              tex_fetch<DT, FEAT != 0 || !SAVE>(V, splat, T, ts_, x);
+              tex_fetch<DT, FEAT != 0 || !SAVE || WIDE>(V, splat, T, ts_, x);
               if (STATS) {  // the four texels this fragment reads
                 uint32_t* w = stats.touched + (size_t)s_it[warp][b][t] * stats.words_per_item;
                 const int q0 = ts_.ja * T + ts_.ia, q1 = ts_.ja * T + ts_.ib;
@@ -222,11 +228,23 @@ __global__ void __launch_bounds__(32 * kRasterWarps, 3 * kCtasPerTile) k_raster_
 
 namespace {
 
+// grids of at least this many tiles take the WIDE instance of the saving
+// forward (4 views of 800x800: 10 000 tiles; one view: 2 500)
+constexpr int kWideTiles = 8192;
+
 template <int DT, bool SAVE, bool STATS, int SMP>
 void launch_feat(int feat, dim3 grid, dim3 block, cudaStream_t st, const ViewTable& vt, const Record* rec,
                  const uint32_t* pair_items, const uint2* ranges, FragCounters stats) {
   switch (feat & (FEAT_IND | FEAT_N2)) {
-    case 0: k_raster_fwd<DT, SAVE, STATS, SMP, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats); break;
+    case 0:
+      if constexpr (SAVE && !STATS && SMP == SMP_SOFTWARE) {
+        if (vt.n_tiles >= kWideTiles) {
+          k_raster_fwd<DT, SAVE, STATS, SMP, 0, true><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+          break;
+        }
+      }
+      k_raster_fwd<DT, SAVE, STATS, SMP, 0><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
+      break;
     case FEAT_N2:
       k_raster_fwd<DT, SAVE, STATS, SMP, FEAT_N2><<<grid, block, 0, st>>>(vt, rec, pair_items, ranges, stats);
       break;

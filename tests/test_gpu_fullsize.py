@@ -90,7 +90,8 @@ def test_cfg1_four_view_launch_keys_and_sampled_pixels(P):
 
 
 def test_cfg1_four_view_backward_equals_single_view_backwards(P):
-    """The benchmarked step's backward (four 800x800 views of the 200k-splat
+    """The benchmarked step's images equal the single-view renders bit for
+    bit, and its backward (four 800x800 views of the 200k-splat
     scene in one launch, L1 gradients against the seeded targets) equals the
     sum of the four views' single-view backwards up to the order of the
     atomic additions (1e-4 of each group's maximum); with the single-view
@@ -112,6 +113,10 @@ def test_cfg1_four_view_backward_equals_single_view_backwards(P):
     g_sum = P.zero_grads(sc)
     for j, c in enumerate(cams):
         o, sv = P.render(sc, c, save=True)
+        # the four-view grid (10 000 tiles) takes the wide-grid forward
+        # instance, one view the default one: the same image bit for bit
+        torch.cuda.synchronize()
+        assert torch.equal(o, outs[j]), j
         d = torch.empty_like(o)
         P.l1_loss(o, targets[j], loss[j:j + 1], d)
         P.render_backward(sv, d, g_sum)
